@@ -1,0 +1,228 @@
+"""Homomorphic training and inference of the oracle.  TEST INFRASTRUCTURE ONLY.
+
+Thin Python orchestration over the C routines of oracle.c, following
+Algorithm 6 (training) and Algorithm 7 (inference, PD-act) item by item.
+Decryption rounds with Python integers: the phase residues are combined by
+the Chinese remainder theorem into phi in [0, Q) and the message is
+round(p * phi / Q) mod p = floor((p * phi + floor(Q/2)) / Q) mod p
+(DecRLWE/DecLWE, Section 2.4; Q is odd and p a power of two, so no ties).
+
+Encrypted-bit streams: bit slot b of sample i (slot l < L is label bit l,
+slot L + d is data bit d) is encrypted under stream index i * n_slots + b.
+"""
+import ctypes
+
+import numpy as np
+
+from . import wisard
+from ._lib import lib, u64p, i8p, u8p
+from .cdt import cdt_table
+from .params import derive
+
+
+def _p64(a: np.ndarray):
+    assert a.dtype == np.uint64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(u64p)
+
+
+class Oracle:
+    def __init__(self, cfg):
+        self.cfg = cfg
+        self.P = P = derive(cfg)
+        q = (ctypes.c_uint64 * P.r)(*P.q)
+        psi = (ctypes.c_uint64 * P.r)(*P.psi)
+        cdt = (ctypes.c_uint64 * 38)(*cdt_table())
+        self.ctx = lib().or_ctx_new(P.log_n, P.r, ctypes.cast(q, u64p), ctypes.cast(psi, u64p),
+                                    cfg.log_beta, P.dpp, ctypes.cast(cdt, u64p))
+        self.rlwe_words = int(lib().or_rlwe_words(self.ctx))
+        self.rgsw_words = int(lib().or_rgsw_words(self.ctx))
+        self.ram_bits = wisard.ram_bits(P)
+
+    def __del__(self):
+        try:
+            lib().or_ctx_free(self.ctx)
+        except Exception:
+            pass
+
+    # ---------------------------------------------------------------- keys
+    def keygen(self, seed: int) -> np.ndarray:
+        s = np.zeros(self.P.n, dtype=np.int8)
+        lib().or_keygen(self.ctx, seed, s.ctypes.data_as(i8p))
+        return s
+
+    # ---------------------------------------------------------- encryption
+    def encrypt_bit(self, s, seed, stream_idx, value, trivial=False) -> np.ndarray:
+        out = np.zeros(self.rgsw_words, dtype=np.uint64)
+        lib().or_encrypt_rgsw(self.ctx, s.ctypes.data_as(i8p), seed, stream_idx, int(value),
+                              int(trivial), _p64(out))
+        return out
+
+    def export_rgsw(self, rgsw) -> np.ndarray:
+        out = np.zeros(self.rgsw_words, dtype=np.uint64)
+        lib().or_rgsw_export(self.ctx, _p64(rgsw), _p64(out))
+        return out
+
+    def encrypt_slots(self, s, seed, sample_idx, data_bits_row, label, slots, trivial=False):
+        """RGSW of the requested bit slots of one sample, keyed by slot."""
+        P = self.P
+        out = {}
+        for b in slots:
+            if b < P.L:
+                val = (int(label) >> b) & 1
+            else:
+                val = int(data_bits_row[b - P.L])
+            out[b] = self.encrypt_bit(s, seed, sample_idx * P.n_slots + b, val, trivial)
+        return out
+
+    def slots_for_rams(self, rams, with_labels=True):
+        P = self.P
+        sl = set(range(P.L)) if with_labels else set()
+        for j in rams:
+            for d in self.ram_bits[j]:
+                if d >= 0:
+                    sl.add(P.L + int(d))
+        return sorted(sl)
+
+    def trivial_one(self) -> np.ndarray:
+        """(0, Delta * 1): the trivial RLWE of the constant 1."""
+        P = self.P
+        ct = np.zeros(self.rlwe_words, dtype=np.uint64)
+        for j in range(P.r):
+            ct[(P.r + j) * P.n] = P.delta % P.q[j]
+        return ct
+
+    # ------------------------------------------------------------ training
+    def ivp_item(self, rgsw_by_slot, j) -> np.ndarray:
+        """IVP(b, (0,1)) for RAM j with b = [label bits, tuple bits of RAM j]
+        (Algorithm 6); returns the 2^z RLWE outputs."""
+        P = self.P
+        k = P.L + P.a
+        ptrs = (u64p * k)()
+        clear = (ctypes.c_int * k)()
+        keep = []
+        for t in range(P.L):
+            ptrs[t] = _p64(rgsw_by_slot[t])
+        for i in range(P.a):
+            d = int(self.ram_bits[j][i])
+            if d >= 0:
+                ptrs[P.L + i] = _p64(rgsw_by_slot[P.L + d])
+            else:
+                ptrs[P.L + i] = ctypes.cast(None, u64p)
+                clear[P.L + i] = 0
+        lhat = self.trivial_one()
+        L = np.zeros((1 << P.z) * self.rlwe_words, dtype=np.uint64)
+        keep.append(lhat)
+        lib().or_ivp(self.ctx, _p64(lhat), ptrs, clear, k, P.z, P.gate.ctypes.data_as(u8p), _p64(L))
+        return L.reshape(1 << P.z, self.rlwe_words)
+
+    def new_model(self) -> np.ndarray:
+        P = self.P
+        return np.zeros((P.k0, P.k1, self.rlwe_words), dtype=np.uint64)
+
+    def train(self, H, s, seed, data_bits, labels, rams=None, sample_offset=0, trivial=False):
+        """Algorithm 6 over the given samples; only the listed RAMs are
+        updated (rows of H are independent).  H is modified in place."""
+        P = self.P
+        rams = list(range(P.k0)) if rams is None else list(rams)
+        slots = self.slots_for_rams(rams)
+        for i in range(data_bits.shape[0]):
+            rg = self.encrypt_slots(s, seed, sample_offset + i, data_bits[i], labels[i], slots,
+                                    trivial)
+            for j in rams:
+                L = self.ivp_item(rg, j)
+                for v in P.V:
+                    lib().or_rlwe_add(self.ctx, _p64(H[j, P.slot[v]]), _p64(np.ascontiguousarray(L[v])))
+        return H
+
+    # ----------------------------------------------------------- inference
+    def vp_item(self, H, rgsw_by_slot, j, c) -> np.ndarray:
+        """VP(b, H[j]) with clear label bits of class c (Algorithm 7)."""
+        P = self.P
+        k = P.L + P.a
+        ptrs = (u64p * k)()
+        clear = (ctypes.c_int * k)()
+        for t in range(P.L):
+            ptrs[t] = ctypes.cast(None, u64p)
+            clear[t] = (c >> t) & 1
+        for i in range(P.a):
+            d = int(self.ram_bits[j][i])
+            if d >= 0:
+                ptrs[P.L + i] = _p64(rgsw_by_slot[P.L + d])
+            else:
+                ptrs[P.L + i] = ctypes.cast(None, u64p)
+                clear[P.L + i] = 0
+        nl = 1 << P.z
+        Lin = (u64p * nl)()
+        rows = []
+        for v in range(nl):
+            if v in P.slot:
+                row = np.ascontiguousarray(H[j, P.slot[v]])
+                rows.append(row)
+                Lin[v] = _p64(row)
+            else:
+                Lin[v] = ctypes.cast(None, u64p)
+        lwe = np.zeros(P.r * (P.n + 1), dtype=np.uint64)
+        lib().or_vp(self.ctx, Lin, ptrs, clear, k, P.z, _p64(lwe))
+        return lwe
+
+    def infer(self, H, s, seed, data_bits, rams=None, sample_offset=0, trivial=False):
+        """Algorithm 7 (PD-act): responses u[i][c][j] as LWE ciphertexts and
+        the per-class sums over the listed RAMs."""
+        P = self.P
+        l = self.cfg.n_classes
+        rams = list(range(P.k0)) if rams is None else list(rams)
+        slots = self.slots_for_rams(rams, with_labels=False)
+        n = data_bits.shape[0]
+        lw = P.r * (P.n + 1)
+        resp = np.zeros((n, l, len(rams), lw), dtype=np.uint64)
+        sums = np.zeros((n, l, lw), dtype=np.uint64)
+        for i in range(n):
+            rg = self.encrypt_slots(s, seed, sample_offset + i, data_bits[i], 0, slots, trivial)
+            for jj, j in enumerate(rams):
+                for c in range(l):
+                    resp[i, c, jj] = self.vp_item(H, rg, j, c)
+                    lib().or_lwe_add(self.ctx, _p64(sums[i, c]), _p64(resp[i, c, jj]))
+        return resp, sums
+
+    # ---------------------------------------------------------- decryption
+    def crt(self, residues):
+        P = self.P
+        phi = 0
+        for j in range(P.r):
+            Mj = P.Q // P.q[j]
+            phi += int(residues[j]) * Mj * pow(Mj % P.q[j], -1, P.q[j])
+        return phi % P.Q
+
+    def decode(self, residues) -> int:
+        P = self.P
+        phi = self.crt(residues)
+        return ((P.p * phi + P.Q // 2) // P.Q) % P.p
+
+    def rlwe_phase(self, s, ct) -> np.ndarray:
+        P = self.P
+        ph = np.zeros(P.r * P.n, dtype=np.uint64)
+        lib().or_rlwe_phase(self.ctx, s.ctypes.data_as(i8p), _p64(np.ascontiguousarray(ct)), _p64(ph))
+        return ph.reshape(P.r, P.n)
+
+    def decrypt_rlwe(self, s, ct) -> np.ndarray:
+        ph = self.rlwe_phase(s, ct)
+        return np.array([self.decode(ph[:, k]) for k in range(self.P.n)], dtype=np.int64)
+
+    def decrypt_lwe(self, s, lwe) -> int:
+        P = self.P
+        ph = np.zeros(P.r, dtype=np.uint64)
+        lib().or_lwe_phase(self.ctx, s.ctypes.data_as(i8p), _p64(np.ascontiguousarray(lwe)), _p64(ph))
+        return self.decode(ph)
+
+    def decrypt_model(self, s, H, rams=None) -> np.ndarray:
+        """Counters W[c][j][addr] from H, for the listed RAMs (others 0)."""
+        P = self.P
+        rams = list(range(P.k0)) if rams is None else list(rams)
+        W = np.zeros((self.cfg.n_classes, P.k0, 1 << P.a), dtype=np.int64)
+        for j in rams:
+            dec = {v: self.decrypt_rlwe(s, H[j, P.slot[v]]) for v in P.V}
+            for c in range(self.cfg.n_classes):
+                for addr in range(1 << P.a):
+                    m = c + (addr << P.L)
+                    W[c, j, addr] = dec[m % (1 << P.z)][m >> P.z]
+        return W
