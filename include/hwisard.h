@@ -1,0 +1,176 @@
+/*
+ * hwisard.h -- C ABI of the GB300 (sm_103a) homomorphic WiSARD hot path.
+ *
+ * The library implements encrypted training and inference of an Integer
+ * WiSARD (Neumann, Guimaraes, Aranha, Borin, "Homomorphic WiSARDs",
+ * PoPETs 2024) over RLWE/RGSW ciphertexts with an RNS modulus
+ * Q = q_0 ... q_{r-1}.  Every step runs in CUDA kernels on one GPU; there is
+ * no CPU fallback.
+ *
+ * Conventions
+ * -----------
+ * - All calls return HW_OK (0) or a negative HW_E* code; the message of the
+ *   last failure of the calling thread is in hw_last_error().  The library
+ *   never aborts the process.
+ * - Arrays passed as "device" pointers live in device memory of the context's
+ *   GPU and are owned by the caller; the library never frees them.  "host"
+ *   pointers are ordinary host memory (pinned memory makes copies faster).
+ * - Calls that take a `stream` (a cudaStream_t, NULL = default stream) only
+ *   enqueue work and return; the caller synchronises.  Calls without a stream
+ *   are synchronous.
+ * - Word = 64-bit unsigned residue.  Polynomials have N = 2^log_n
+ *   coefficients; an RNS polynomial is [prime 0..r-1][coefficient 0..N-1].
+ * - Canonical (coefficient-domain) layouts:
+ *     RLWE   (a, b)       [component a=0,b=1][prime][N], residues in [0, q_i)
+ *     LWE    (a', b')     [prime][N a-coefficients, then b]   (r*(N+1) words)
+ *     model  H            [RAM k0][ciphertext k1][RLWE]       (Definition 2)
+ *   RGSW ciphertexts and the secret key are kept in an internal evaluation
+ *   form; hw_export_rgsw() returns the canonical coefficient form
+ *   [row 0..2*dnum-1][RLWE].
+ */
+#ifndef HWISARD_H
+#define HWISARD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HW_OK 0
+#define HW_EINVAL (-1)    /* bad argument, size or parameter */
+#define HW_ENOMEM (-2)    /* a caller buffer is too small */
+#define HW_ECUDA (-3)     /* a CUDA call failed; see hw_last_error() */
+#define HW_EMISMATCH (-5) /* object made for other parameters */
+
+/* PD-act activations (Section 3.2): floor(log2(x+1)), min(floor(log2(x+1)),
+ * act_arg), and [x > act_arg]. */
+#define HW_ACT_LOG 0
+#define HW_ACT_BLOG 1
+#define HW_ACT_BIN 2
+
+/* What hw_decrypt decrypts. */
+#define HW_DEC_RLWE 0 /* count RLWE ciphertexts -> count*N values */
+#define HW_DEC_LWE 1  /* count LWE ciphertexts  -> count values */
+
+typedef struct hw_params {
+    int32_t log_n;      /* ring dimension N = 2^log_n, 10 <= log_n <= 13 */
+    int32_t n_primes;   /* r, 1..3 */
+    int32_t prime_bits; /* q_i < 2^prime_bits, q_i = 1 mod 2N, 20 <= bits <= 55 */
+    int32_t log_beta;   /* gadget base 2^log_beta; 0 = one digit per prime */
+    int32_t log_p;      /* plaintext modulus p = 2^log_p, 1..30 */
+    int32_t n_classes;  /* l, 2..64 */
+    int32_t n_values;   /* uint8 input values per sample */
+    int32_t therm_bits; /* thermometer width T, 1..16 */
+    int32_t tuple_bits; /* bits per tuple before hashing (= addr_bits if not hashed) */
+    int32_t addr_bits;  /* a, RAM address bits, 1..20 */
+    int32_t hash_h3;    /* 1: client hashes each tuple to addr_bits with H3 */
+    int32_t act;        /* HW_ACT_* for hw_pdact */
+    int32_t act_arg;    /* bound (blog) or threshold (bin) */
+    int32_t reserved;
+    uint64_t model_seed; /* seeds the bit permutation pi_r and the H3 matrix */
+} hw_params;
+
+typedef struct hw_ctx hw_ctx;
+
+/* Derived sizes (words are 64-bit). */
+typedef struct hw_sizes {
+    int32_t n, r, L, a, s, k0, k1, z, dpp, dnum, n_data, n_slots;
+    uint64_t q[4];          /* the RNS primes, descending */
+    size_t rlwe_words;      /* 2 r N */
+    size_t lwe_words;       /* r (N + 1) */
+    size_t rgsw_words;      /* 2 dnum rlwe_words */
+    size_t key_words;       /* device secret key buffer */
+    size_t model_words;     /* k0 k1 rlwe_words */
+    size_t sample_words;    /* n_slots rgsw_words: one encrypted sample */
+    size_t resp_words;      /* l k0 lwe_words: responses of one test sample */
+    size_t sums_words;      /* l lwe_words: class sums of one test sample */
+} hw_sizes;
+
+/* Create a context on `cuda_device` for the given parameters: finds the
+ * primes, roots of unity, transform tables, pi_r and (if hashed) the H3
+ * matrix, and uploads them.  The RNS modulus and noise distribution are the
+ * readings of Section 2.4 (Setup) listed with the project's design notes. */
+int hw_create(const hw_params* params, int cuda_device, hw_ctx** out);
+int hw_destroy(hw_ctx* ctx);
+int hw_get_sizes(const hw_ctx* ctx, hw_sizes* out);
+/* Host copy of the server's index tables: ram_slot[k0*a] gives, for RAM j and
+ * address bit i, the encrypted bit slot it reads (-1: constant 0). */
+int hw_get_ram_slots(const hw_ctx* ctx, int32_t* ram_slot_host, size_t n);
+
+/* Scratch words hw_train_accumulate / hw_infer need for a batch of n samples. */
+size_t hw_train_scratch_words(const hw_ctx* ctx, size_t n);
+size_t hw_infer_scratch_words(const hw_ctx* ctx, size_t n);
+
+/* SecretKeyGen (Section 2.4): a ternary RLWE key S_1 drawn from `seed`
+ * (coefficient k from word k of the KEY stream, w mod 3 -> 0,+1,-1).
+ * key_dev: key_words device words, written. */
+int hw_keygen(hw_ctx* ctx, uint64_t seed, uint64_t* key_dev, void* stream);
+
+/* Client pre-processing (Sections 2.3.1-2.3.2, 3.4): quantise each uint8
+ * value to level (v*(T+1))>>8, thermometer-encode it; hashed contexts also
+ * apply pi_r and H3 per tuple.  values_dev: n*n_values bytes; bits_dev:
+ * n*n_data bytes (0/1), written. */
+int hw_encode(hw_ctx* ctx, const uint8_t* values_dev, size_t n, uint8_t* bits_dev, void* stream);
+
+/* EncRGSW of every bit of n samples (Section 3.4: samples and labels are
+ * encrypted bit by bit).  Slot b < L is label bit b (LSB first), slot L+d is
+ * data bit d.  labels_dev: n uint32 labels, or NULL to skip the label slots
+ * (inference).  Sample i uses stream index (first_sample+i)*n_slots+slot of
+ * the RGSW_A / RGSW_E streams keyed by `seed`.  rgsw_dev: n*sample_words
+ * device words, written (label slots untouched when labels_dev is NULL). */
+int hw_encrypt_sample(hw_ctx* ctx, const uint64_t* key_dev, const uint8_t* bits_dev,
+                      const uint32_t* labels_dev, size_t n, uint64_t seed, uint64_t first_sample,
+                      uint64_t* rgsw_dev, void* stream);
+
+/* Homomorphic training (Algorithm 6): for each sample and RAM j, the Inverse
+ * Vertical Packing (Algorithm 5) of b = [label bits, tuple bits of RAM j] and
+ * the trivial RLWE (0, Delta) is added into H[j] (mod q_i).  model_dev:
+ * model_words device words, updated in place.  scratch_dev: at least
+ * hw_train_scratch_words(ctx, n) device words. */
+int hw_train_accumulate(hw_ctx* ctx, uint64_t* model_dev, const uint64_t* rgsw_dev, size_t n,
+                        uint64_t* scratch_dev, size_t scratch_words, void* stream);
+
+/* Homomorphic inference with PD-act (Algorithm 7): for each sample, RAM j and
+ * class c, the Vertical Packing (Algorithm 3) of H[j] with the label bits of c
+ * in clear, then ExtractLWE(., 0).  resp_dev: n*resp_words words, laid out
+ * [sample][class][RAM][LWE]; sums_dev: n*sums_words words, [sample][class][LWE],
+ * the per-class sums over RAMs (mod q_i).  Both written. */
+int hw_infer(hw_ctx* ctx, const uint64_t* model_dev, const uint64_t* rgsw_dev, size_t n,
+             uint64_t* resp_dev, uint64_t* sums_dev, uint64_t* scratch_dev, size_t scratch_words,
+             void* stream);
+
+/* DecRLWE / DecLWE (Section 2.4): phase b - a*s combined over the primes by
+ * the CRT and rounded, m = floor((p*phi + floor(Q/2)) / Q) mod p.  what =
+ * HW_DEC_RLWE: obj_dev holds count RLWEs, out_dev gets count*N values;
+ * HW_DEC_LWE: count LWEs, count values.  out_dev: int64 device array. */
+int hw_decrypt(hw_ctx* ctx, const uint64_t* key_dev, int what, const uint64_t* obj_dev,
+               size_t count, int64_t* out_dev, void* stream);
+
+/* PD-act (Section 3.5.1): counts_dev [n][l][k0] decrypted responses ->
+ * scores_dev [n][l] (sum of activated counts) and labels_dev [n] (arg-max,
+ * ties to the lowest class). */
+int hw_pdact(hw_ctx* ctx, const int64_t* counts_dev, size_t n, int64_t* scores_dev,
+             int32_t* labels_dev, void* stream);
+
+/* Canonical coefficient form of count RGSW ciphertexts (for checks). */
+int hw_export_rgsw(hw_ctx* ctx, const uint64_t* rgsw_dev, size_t count, uint64_t* out_dev,
+                   void* stream);
+
+/* Batched forward / inverse negacyclic transform of count polynomials in
+ * place, polynomial t using prime (t mod r).  The forward output is in the
+ * library's evaluation order; inverse(forward(x)) = x. */
+int hw_ntt_forward(hw_ctx* ctx, uint64_t* poly_dev, size_t count, void* stream);
+int hw_ntt_inverse(hw_ctx* ctx, uint64_t* poly_dev, size_t count, void* stream);
+
+/* Number of kernel launches the library has issued since the context was
+ * created (all calls). */
+uint64_t hw_launch_count(const hw_ctx* ctx);
+
+const char* hw_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HWISARD_H */

@@ -1,0 +1,217 @@
+"""Thin Python binding of the C ABI in include/hwisard.h.
+
+Functions keep the C names and only marshal arguments: device buffers are
+torch CUDA tensors (int64 storage holding the 64-bit residues bit for bit),
+streams are torch CUDA streams.  Every computation runs in libhwisard.so;
+there is no Python or CPU fallback, and a missing library is an error.
+"""
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+_lib = None
+
+HW_OK = 0
+HW_ACT = {"log": 0, "blog": 1, "bin": 2}
+HW_DEC_RLWE = 0
+HW_DEC_LWE = 1
+
+
+class HwParams(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_int32) for name in (
+        "log_n", "n_primes", "prime_bits", "log_beta", "log_p", "n_classes", "n_values",
+        "therm_bits", "tuple_bits", "addr_bits", "hash_h3", "act", "act_arg", "reserved")] + [
+        ("model_seed", ctypes.c_uint64)]
+
+
+class HwSizes(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_int32) for name in (
+        "n", "r", "L", "a", "s", "k0", "k1", "z", "dpp", "dnum", "n_data", "n_slots")] + [
+        ("q", ctypes.c_uint64 * 4)] + [(name, ctypes.c_size_t) for name in (
+            "rlwe_words", "lwe_words", "rgsw_words", "key_words", "model_words", "sample_words",
+            "resp_words", "sums_words")]
+
+
+class HwError(RuntimeError):
+    pass
+
+
+_VP = ctypes.c_void_p
+_SZ = ctypes.c_size_t
+_U64 = ctypes.c_uint64
+_SIGS = {
+    "hw_create": (ctypes.c_int, [ctypes.POINTER(HwParams), ctypes.c_int, ctypes.POINTER(_VP)]),
+    "hw_destroy": (ctypes.c_int, [_VP]),
+    "hw_get_sizes": (ctypes.c_int, [_VP, ctypes.POINTER(HwSizes)]),
+    "hw_get_ram_slots": (ctypes.c_int, [_VP, _VP, _SZ]),
+    "hw_train_scratch_words": (_SZ, [_VP, _SZ]),
+    "hw_infer_scratch_words": (_SZ, [_VP, _SZ]),
+    "hw_keygen": (ctypes.c_int, [_VP, _U64, _VP, _VP]),
+    "hw_encode": (ctypes.c_int, [_VP, _VP, _SZ, _VP, _VP]),
+    "hw_encrypt_sample": (ctypes.c_int, [_VP, _VP, _VP, _VP, _SZ, _U64, _U64, _VP, _VP]),
+    "hw_train_accumulate": (ctypes.c_int, [_VP, _VP, _VP, _SZ, _VP, _SZ, _VP]),
+    "hw_infer": (ctypes.c_int, [_VP, _VP, _VP, _SZ, _VP, _VP, _VP, _SZ, _VP]),
+    "hw_decrypt": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, _SZ, _VP, _VP]),
+    "hw_pdact": (ctypes.c_int, [_VP, _VP, _SZ, _VP, _VP, _VP]),
+    "hw_export_rgsw": (ctypes.c_int, [_VP, _VP, _SZ, _VP, _VP]),
+    "hw_ntt_forward": (ctypes.c_int, [_VP, _VP, _SZ, _VP]),
+    "hw_ntt_inverse": (ctypes.c_int, [_VP, _VP, _SZ, _VP]),
+    "hw_launch_count": (_U64, [_VP]),
+    "hw_last_error": (ctypes.c_char_p, []),
+}
+EXPORTS = tuple(_SIGS)
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False) -> ctypes.CDLL:
+    """Load libhwisard.so (built by paper_2403_20190_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise HwError(f"libhwisard.so is not built ({path}); run paper_2403_20190_gb300.build")
+        _build.build()
+    L = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(rc, what):
+    if rc != HW_OK:
+        msg = load().hw_last_error().decode(errors="replace")
+        raise HwError(f"{what} failed ({rc}): {msg}")
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, torch.Tensor):
+        if not t.is_contiguous():
+            raise HwError("buffers must be contiguous")
+        return ctypes.c_void_p(t.data_ptr())
+    return ctypes.c_void_p(t)
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Ctx:
+    """An hw_ctx handle; destroyed with hw_destroy when collected."""
+
+    def __init__(self, handle, device):
+        self.handle = handle
+        self.device = device
+
+    def __del__(self):
+        if self.handle and _lib is not None:
+            _lib.hw_destroy(self.handle)
+            self.handle = None
+
+
+def params_from_config(cfg) -> HwParams:
+    p = HwParams()
+    for name in ("log_n", "n_primes", "prime_bits", "log_beta", "log_p", "n_classes", "n_values",
+                 "therm_bits", "tuple_bits", "addr_bits"):
+        setattr(p, name, int(getattr(cfg, name)))
+    p.hash_h3 = int(cfg.hash_h3)
+    p.act = HW_ACT[cfg.act]
+    p.act_arg = int(cfg.act_arg)
+    p.model_seed = int(cfg.model_seed)
+    return p
+
+
+def hw_create(params, device: int = 0) -> Ctx:
+    if not isinstance(params, HwParams):
+        params = params_from_config(params)
+    h = _VP()
+    _check(load().hw_create(ctypes.byref(params), device, ctypes.byref(h)), "hw_create")
+    return Ctx(h, device)
+
+
+def hw_get_sizes(ctx) -> dict:
+    s = HwSizes()
+    _check(load().hw_get_sizes(ctx.handle, ctypes.byref(s)), "hw_get_sizes")
+    d = {f: getattr(s, f) for f, _ in HwSizes._fields_ if f != "q"}
+    d["q"] = [int(v) for v in s.q][: s.r]
+    return d
+
+
+def hw_get_ram_slots(ctx):
+    sz = hw_get_sizes(ctx)
+    n = sz["k0"] * sz["a"]
+    buf = (ctypes.c_int32 * n)()
+    _check(load().hw_get_ram_slots(ctx.handle, ctypes.cast(buf, _VP), n), "hw_get_ram_slots")
+    return list(buf)
+
+
+def hw_train_scratch_words(ctx, n) -> int:
+    return int(load().hw_train_scratch_words(ctx.handle, n))
+
+
+def hw_infer_scratch_words(ctx, n) -> int:
+    return int(load().hw_infer_scratch_words(ctx.handle, n))
+
+
+def hw_keygen(ctx, seed, key, stream=None):
+    _check(load().hw_keygen(ctx.handle, seed, _ptr(key), _stream(stream)), "hw_keygen")
+
+
+def hw_encode(ctx, values, n, bits, stream=None):
+    _check(load().hw_encode(ctx.handle, _ptr(values), n, _ptr(bits), _stream(stream)), "hw_encode")
+
+
+def hw_encrypt_sample(ctx, key, bits, labels, n, seed, first_sample, rgsw, stream=None):
+    _check(load().hw_encrypt_sample(ctx.handle, _ptr(key), _ptr(bits), _ptr(labels), n, seed,
+                                    first_sample, _ptr(rgsw), _stream(stream)), "hw_encrypt_sample")
+
+
+def hw_train_accumulate(ctx, model, rgsw, n, scratch, stream=None):
+    _check(load().hw_train_accumulate(ctx.handle, _ptr(model), _ptr(rgsw), n, _ptr(scratch),
+                                      scratch.numel(), _stream(stream)), "hw_train_accumulate")
+
+
+def hw_infer(ctx, model, rgsw, n, resp, sums, scratch, stream=None):
+    _check(load().hw_infer(ctx.handle, _ptr(model), _ptr(rgsw), n, _ptr(resp), _ptr(sums),
+                           _ptr(scratch), scratch.numel(), _stream(stream)), "hw_infer")
+
+
+def hw_decrypt(ctx, key, what, obj, count, out, stream=None):
+    _check(load().hw_decrypt(ctx.handle, _ptr(key), what, _ptr(obj), count, _ptr(out),
+                             _stream(stream)), "hw_decrypt")
+
+
+def hw_pdact(ctx, counts, n, scores, labels, stream=None):
+    _check(load().hw_pdact(ctx.handle, _ptr(counts), n, _ptr(scores), _ptr(labels),
+                           _stream(stream)), "hw_pdact")
+
+
+def hw_export_rgsw(ctx, rgsw, count, out, stream=None):
+    _check(load().hw_export_rgsw(ctx.handle, _ptr(rgsw), count, _ptr(out), _stream(stream)),
+           "hw_export_rgsw")
+
+
+def hw_ntt_forward(ctx, poly, count, stream=None):
+    _check(load().hw_ntt_forward(ctx.handle, _ptr(poly), count, _stream(stream)), "hw_ntt_forward")
+
+
+def hw_ntt_inverse(ctx, poly, count, stream=None):
+    _check(load().hw_ntt_inverse(ctx.handle, _ptr(poly), count, _stream(stream)), "hw_ntt_inverse")
+
+
+def hw_launch_count(ctx) -> int:
+    return int(load().hw_launch_count(ctx.handle))

@@ -1,0 +1,581 @@
+// api.cu -- host implementation of the C ABI declared in include/hwisard.h.
+//
+// hw_create derives every parameter of a context (Section 2.4 Setup, read
+// as an RNS modulus; Definition 2 for the model shape), builds the transform
+// tables, pi_r and the H3 matrix on the host, and uploads them once.  All
+// per-sample work runs in the kernels of k_crypto.cu and k_wisard.cu.
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/hwisard.h"
+#include "hw_internal.cuh"
+#include "hw_launch.h"
+
+typedef unsigned __int128 u128;
+
+static thread_local std::string g_last_error;
+
+static int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+#define CUDA_TRY(call)                                                                          \
+    do {                                                                                        \
+        cudaError_t e_ = (call);                                                                \
+        if (e_ != cudaSuccess)                                                                  \
+            return fail(HW_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                        __LINE__);                                                              \
+    } while (0)
+
+struct hw_ctx {
+    hw_params prm;
+    hw_sizes sz;
+    int device;
+    DevCtx host;          // host copy (device pointers filled in)
+    DevCtx* dctx;         // device copy
+    void* tables;         // one device block for all tables
+    u64* phase_scratch;   // decryption phases, chunk * r * N words
+    size_t phase_chunk;
+    LaunchInfo li;
+    unsigned long long launches;
+    std::vector<int32_t> ram_slot;
+};
+
+// ----------------------------------------------------------------- host math
+static u64 hmul(u64 a, u64 b, u64 q) { return (u64)(((u128)a * b) % q); }
+static u64 hpow(u64 b, u64 e, u64 q) {
+    u64 r = 1 % q;
+    b %= q;
+    while (e) {
+        if (e & 1) r = hmul(r, b, q);
+        b = hmul(b, b, q);
+        e >>= 1;
+    }
+    return r;
+}
+static u64 hinv(u64 a, u64 q) { return hpow(a, q - 2, q); }
+
+static bool miller_rabin(u64 n) {
+    if (n < 2) return false;
+    const u64 small[] = {2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37};
+    for (u64 p : small) {
+        if (n % p == 0) return n == p;
+    }
+    u64 d = n - 1;
+    int s = 0;
+    while (!(d & 1)) {
+        d >>= 1;
+        s++;
+    }
+    for (u64 a : small) {
+        u64 x = hpow(a, d, n);
+        if (x == 1 || x == n - 1) continue;
+        bool witness = true;
+        for (int k = 1; k < s && witness; k++) {
+            x = hmul(x, x, n);
+            if (x == n - 1) witness = false;
+        }
+        if (witness) return false;
+    }
+    return true;
+}
+
+// A primitive 2N-th root of unity: the first odd x >= 3 whose power
+// x^((q-1)/2N) squares to -1 after log_n doublings.  Any such root gives the
+// same coefficient-domain results; it only fixes the evaluation order.
+static u64 find_root(u64 q, int log_n) {
+    const u64 n = (u64)1 << log_n;
+    for (u64 x = 3; x < q; x += 2) {
+        u64 w = hpow(x, (q - 1) / (2 * n), q);
+        if (hpow(w, n, q) == q - 1) return w;
+    }
+    return 0;
+}
+
+static int brv(int x, int bits) {
+    int y = 0;
+    for (int b = 0; b < bits; b++) y |= ((x >> b) & 1) << (bits - 1 - b);
+    return y;
+}
+
+static u64 shoup(u64 w, u64 q) { return (u64)(((u128)w << 64) / q); }
+
+// little-endian multi-limb helpers
+static void lmul_small(u64* a, u64 m) {
+    u128 carry = 0;
+    for (int t = 0; t < HW_LIMBS; t++) {
+        u128 v = (u128)a[t] * m + carry;
+        a[t] = (u64)v;
+        carry = v >> 64;
+    }
+}
+static u64 lmod(const u64* a, u64 q) {
+    u128 r = 0;
+    for (int t = HW_LIMBS - 1; t >= 0; t--) r = ((r << 64) | a[t]) % q;
+    return (u64)r;
+}
+static void lshr(const u64* a, int s, u64* out) {  // 0 < s < 64
+    for (int t = 0; t < HW_LIMBS; t++) {
+        u64 hi = t + 1 < HW_LIMBS ? a[t + 1] : 0;
+        out[t] = (a[t] >> s) | (hi << (64 - s));
+    }
+}
+
+static int ilog2_ceil(int l) {
+    int L = 0;
+    while ((1 << L) < l) L++;
+    return L;
+}
+
+// ------------------------------------------------------------------ create
+extern "C" int hw_create(const hw_params* p, int cuda_device, hw_ctx** out) {
+    if (!p || !out) return fail(HW_EINVAL, "hw_create: null argument");
+    *out = nullptr;
+    if (p->log_n < 3 || p->log_n > 13) return fail(HW_EINVAL, "log_n must be in [3, 13]");
+    if (p->n_primes < 1 || p->n_primes > 3) return fail(HW_EINVAL, "n_primes must be 1..3");
+    if (p->prime_bits < 20 || p->prime_bits > 55) return fail(HW_EINVAL, "prime_bits must be 20..55");
+    if (p->log_beta < 0 || p->log_beta > 30) return fail(HW_EINVAL, "log_beta must be 0..30");
+    if (p->log_p < 1 || p->log_p > 30) return fail(HW_EINVAL, "log_p must be 1..30");
+    if (p->n_classes < 2 || p->n_classes > 64) return fail(HW_EINVAL, "n_classes must be 2..64");
+    if (p->n_values < 1 || p->therm_bits < 1 || p->therm_bits > 16)
+        return fail(HW_EINVAL, "bad n_values / therm_bits");
+    if (p->addr_bits < 1 || p->addr_bits > 20) return fail(HW_EINVAL, "addr_bits must be 1..20");
+    if (p->hash_h3 && (p->tuple_bits < 1 || p->tuple_bits > 32))
+        return fail(HW_EINVAL, "tuple_bits must be 1..32");
+    if (p->act < 0 || p->act > 2) return fail(HW_EINVAL, "act must be HW_ACT_*");
+
+    hw_ctx* c = new hw_ctx();
+    memset(&c->host, 0, sizeof(DevCtx));
+    c->prm = *p;
+    c->device = cuda_device;
+    c->launches = 0;
+    DevCtx& H = c->host;
+    hw_sizes& S = c->sz;
+    memset(&S, 0, sizeof(S));
+
+    const int log_n = p->log_n, n = 1 << log_n, r = p->n_primes;
+    const int L = ilog2_ceil(p->n_classes);
+    const int a = p->addr_bits;
+    const int s = p->n_values * p->therm_bits;
+    int k0, n_data;
+    if (p->hash_h3) {
+        k0 = (s + p->tuple_bits - 1) / p->tuple_bits;
+        n_data = k0 * a;
+    } else {
+        k0 = (s + a - 1) / a;
+        n_data = s;
+    }
+    int z = L + a - log_n;
+    if (z < 0) z = 0;
+    if (z > HW_MAX_Z) {
+        delete c;
+        return fail(HW_EINVAL, "tree depth z = %d exceeds %d", z, HW_MAX_Z);
+    }
+    if (z - L > 1) {
+        delete c;
+        return fail(HW_EINVAL, "more than one encrypted CMUX-tree level (z - L = %d)", z - L);
+    }
+    const int dpp = p->log_beta ? (p->prime_bits + p->log_beta - 1) / p->log_beta : 1;
+    const int dnum = r * dpp;
+    if (dnum > HW_MAX_DNUM) {
+        delete c;
+        return fail(HW_EINVAL, "too many gadget rows (%d)", dnum);
+    }
+
+    // primes: the r largest q < 2^bits with q = 1 mod 2N, descending
+    std::vector<u64> q;
+    {
+        const u64 m = (u64)2 << log_n;
+        u64 cand = (((u64)1 << p->prime_bits) - 2) / m * m + 1;
+        while ((int)q.size() < r && cand > m) {
+            if (miller_rabin(cand)) q.push_back(cand);
+            cand -= m;
+        }
+        if ((int)q.size() < r) {
+            delete c;
+            return fail(HW_EINVAL, "not enough NTT-friendly primes");
+        }
+    }
+
+    // tree: stored ciphertext indices V, slots and the pruned gate list
+    std::vector<int> V;
+    {
+        std::vector<char> in(1 << z, 0);
+        int xs = z > L ? 1 << (z - L) : 1;
+        for (int cl = 0; cl < p->n_classes; cl++)
+            for (int x = 0; x < xs; x++) in[(cl + (x << L)) % (1 << z)] = 1;
+        for (int v = 0; v < (1 << z); v++) {
+            H.slot_of[v] = -1;
+            if (in[v]) {
+                H.slot_of[v] = (int8_t)V.size();
+                V.push_back(v);
+            }
+        }
+        int ng = 0;
+        for (int i = 0; i < z; i++)
+            for (int j = 0; j < (1 << i); j++) {
+                bool need = false;
+                for (int v : V)
+                    if (v % (1 << (i + 1)) == j + (1 << i)) need = true;
+                if (need) {
+                    H.gate_lvl[ng] = (int8_t)i;
+                    H.gate_j[ng] = (int8_t)j;
+                    ng++;
+                }
+            }
+        H.n_gates = ng;
+    }
+    const int k1 = (int)V.size();
+
+    H.log_n = log_n;
+    H.n = n;
+    H.r = r;
+    H.dnum = dnum;
+    H.dpp = dpp;
+    H.log_beta = p->log_beta;
+    H.L = L;
+    H.a = a;
+    H.k0 = k0;
+    H.k1 = k1;
+    H.z = z;
+    H.n_data = n_data;
+    H.n_slots = L + n_data;
+    H.s = s;
+    H.n_classes = p->n_classes;
+    H.therm_bits = p->therm_bits;
+    H.tuple_bits = p->tuple_bits;
+    H.hash_h3 = p->hash_h3;
+    H.n_values = p->n_values;
+    H.log_p = p->log_p;
+    H.act = p->act;
+    H.act_arg = p->act_arg;
+    H.rlwe_words = (size_t)2 * r * n;
+    H.lwe_words = (size_t)r * (n + 1);
+    H.rgsw_words = (size_t)2 * dnum * H.rlwe_words;
+    H.sample_words = (size_t)H.n_slots * H.rgsw_words;
+    H.model_words = (size_t)k0 * k1 * H.rlwe_words;
+
+    // modulus Q, Delta = floor(Q/p), CRT constants
+    u64 Q[HW_LIMBS] = {1, 0, 0, 0};
+    for (int i = 0; i < r; i++) lmul_small(Q, q[i]);
+    u64 delta[HW_LIMBS];
+    lshr(Q, p->log_p, delta);
+    lshr(Q, 1, H.halfQ);
+    memcpy(H.Q, Q, sizeof(Q));
+    for (int i = 0; i < r; i++) {
+        PrimeConst& P = H.P[i];
+        P.q = q[i];
+        u64 inv = q[i];  // Newton iteration for q^-1 mod 2^64
+        for (int it = 0; it < 6; it++) inv *= 2 - q[i] * inv;
+        P.qneg = (u64)0 - inv;
+        u64 t = ((u64)0 - q[i]) % q[i];  // 2^64 mod q
+        P.r2 = hmul(t, t, q[i]);
+        P.mu = ~(u64)0 / q[i];
+        H.delta[i] = lmod(delta, q[i]);
+        u64 Mi[HW_LIMBS] = {1, 0, 0, 0};
+        for (int k = 0; k < r; k++)
+            if (k != i) lmul_small(Mi, q[k]);
+        memcpy(H.M[i], Mi, sizeof(Mi));
+        u64 y = hinv(lmod(Mi, q[i]), q[i]);
+        H.yM[i] = (u64)(((u128)y << 64) % q[i]);
+        H.n_inv[i] = hinv((u64)n % q[i], q[i]);
+        H.n_inv_s[i] = shoup(H.n_inv[i], q[i]);
+        S.q[i] = q[i];
+    }
+    for (int rho = 0; rho < dnum; rho++) {
+        int i = rho / dpp, k = rho % dpp;
+        H.gconst[rho] = p->log_beta ? hpow((u64)1 << p->log_beta, (u64)k, q[i]) : 1;
+    }
+
+    // transform tables
+    std::vector<u64> tw((size_t)4 * r * n);
+    u64* tw_fwd = tw.data();
+    u64* tw_fwd_s = tw_fwd + (size_t)r * n;
+    u64* tw_inv = tw_fwd_s + (size_t)r * n;
+    u64* tw_inv_s = tw_inv + (size_t)r * n;
+    for (int i = 0; i < r; i++) {
+        u64 psi = find_root(q[i], log_n);
+        if (!psi) {
+            delete c;
+            return fail(HW_EINVAL, "no 2N-th root of unity");
+        }
+        u64 psi_inv = hinv(psi, q[i]);
+        for (int k = 0; k < n; k++) {
+            int e = brv(k, log_n);
+            u64 w = hpow(psi, (u64)e, q[i]), wi = hpow(psi_inv, (u64)e, q[i]);
+            tw_fwd[(size_t)i * n + k] = w;
+            tw_fwd_s[(size_t)i * n + k] = shoup(w, q[i]);
+            tw_inv[(size_t)i * n + k] = wi;
+            tw_inv_s[(size_t)i * n + k] = shoup(wi, q[i]);
+        }
+    }
+
+    // pi_r (Fisher-Yates from the top with the PERM stream), H3 rows, RAM slots
+    std::vector<int32_t> perm(s);
+    for (int k = 0; k < s; k++) perm[k] = k;
+    for (int j = s - 1; j >= 1; j--) {
+        Philox4 w = hw_draw(p->model_seed, HW_TAG_PERM, (u64)j >> 2, 0, 0);
+        int k = (int)(w.v[j & 3] % (u64)(j + 1));
+        std::swap(perm[j], perm[k]);
+    }
+    std::vector<u64> h3(p->hash_h3 ? p->tuple_bits : 1, 0);
+    if (p->hash_h3)
+        for (int i = 0; i < p->tuple_bits; i++) {
+            Philox4 w = hw_draw(p->model_seed, HW_TAG_H3, (u64)i >> 2, 0, 0);
+            h3[i] = w.v[i & 3] & (((u64)1 << a) - 1);
+        }
+    c->ram_slot.assign((size_t)k0 * a, -1);
+    for (int j = 0; j < k0; j++)
+        for (int i = 0; i < a; i++) {
+            if (p->hash_h3)
+                c->ram_slot[(size_t)j * a + i] = L + j * a + i;
+            else if (j * a + i < s)
+                c->ram_slot[(size_t)j * a + i] = L + perm[j * a + i];
+        }
+
+    // upload
+    size_t bytes_tw = tw.size() * 8, bytes_rs = c->ram_slot.size() * 4, bytes_perm = perm.size() * 4,
+           bytes_h3 = h3.size() * 8;
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    size_t total = al(bytes_tw) + al(bytes_rs) + al(bytes_perm) + al(bytes_h3) + al(sizeof(DevCtx));
+    c->phase_chunk = 64;
+    cudaError_t e = cudaSetDevice(cuda_device);
+    if (e == cudaSuccess) e = cudaMalloc(&c->tables, total);
+    if (e == cudaSuccess)
+        e = cudaMalloc(&c->phase_scratch, c->phase_chunk * (size_t)r * n * sizeof(u64));
+    if (e != cudaSuccess) {
+        delete c;
+        return fail(HW_ECUDA, "device allocation failed: %s", cudaGetErrorString(e));
+    }
+    char* base = (char*)c->tables;
+    size_t off = 0;
+    auto put = [&](const void* src, size_t nb) {
+        char* d = base + off;
+        cudaMemcpy(d, src, nb, cudaMemcpyHostToDevice);
+        off += al(nb);
+        return d;
+    };
+    char* d_tw = put(tw.data(), bytes_tw);
+    H.tw_fwd = (const u64*)d_tw;
+    H.tw_fwd_s = H.tw_fwd + (size_t)r * n;
+    H.tw_inv = H.tw_fwd_s + (size_t)r * n;
+    H.tw_inv_s = H.tw_inv + (size_t)r * n;
+    H.ram_slot = (const int32_t*)put(c->ram_slot.data(), bytes_rs);
+    H.perm = (const int32_t*)put(perm.data(), bytes_perm);
+    H.h3 = (const u64*)put(h3.data(), bytes_h3);
+    c->dctx = (DevCtx*)put(&H, sizeof(DevCtx));
+    e = hw_kernels_init(log_n);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        cudaFree(c->tables);
+        cudaFree(c->phase_scratch);
+        delete c;
+        return fail(HW_ECUDA, "context upload failed: %s", cudaGetErrorString(e));
+    }
+
+    // sizes
+    S.n = n;
+    S.r = r;
+    S.L = L;
+    S.a = a;
+    S.s = s;
+    S.k0 = k0;
+    S.k1 = k1;
+    S.z = z;
+    S.dpp = dpp;
+    S.dnum = dnum;
+    S.n_data = n_data;
+    S.n_slots = H.n_slots;
+    S.rlwe_words = H.rlwe_words;
+    S.lwe_words = H.lwe_words;
+    S.rgsw_words = H.rgsw_words;
+    S.key_words = (size_t)2 * r * n;
+    S.model_words = H.model_words;
+    S.sample_words = H.sample_words;
+    S.resp_words = (size_t)p->n_classes * k0 * H.lwe_words;
+    S.sums_words = (size_t)p->n_classes * H.lwe_words;
+
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, cuda_device);
+    LaunchInfo& li = c->li;
+    li.dctx = c->dctx;
+    li.log_n = log_n;
+    li.n = n;
+    li.r = r;
+    li.k0 = k0;
+    li.k1 = k1;
+    li.n_classes = p->n_classes;
+    li.n_data = n_data;
+    li.n_slots = H.n_slots;
+    li.L = L;
+    li.dnum = dnum;
+    li.rlwe_words = H.rlwe_words;
+    li.lwe_words = H.lwe_words;
+    li.rgsw_words = H.rgsw_words;
+    li.sample_words = H.sample_words;
+    li.model_words = H.model_words;
+    li.sm_count = sms;
+    li.launches = &c->launches;
+    *out = c;
+    return HW_OK;
+}
+
+extern "C" int hw_destroy(hw_ctx* c) {
+    if (!c) return HW_OK;
+    cudaSetDevice(c->device);
+    cudaFree(c->tables);
+    cudaFree(c->phase_scratch);
+    delete c;
+    return HW_OK;
+}
+
+extern "C" int hw_get_sizes(const hw_ctx* c, hw_sizes* out) {
+    if (!c || !out) return fail(HW_EINVAL, "hw_get_sizes: null argument");
+    *out = c->sz;
+    return HW_OK;
+}
+
+extern "C" int hw_get_ram_slots(const hw_ctx* c, int32_t* dst, size_t n) {
+    if (!c || !dst) return fail(HW_EINVAL, "hw_get_ram_slots: null argument");
+    if (n < c->ram_slot.size()) return fail(HW_ENOMEM, "hw_get_ram_slots: need %zu entries", c->ram_slot.size());
+    memcpy(dst, c->ram_slot.data(), c->ram_slot.size() * sizeof(int32_t));
+    return HW_OK;
+}
+
+extern "C" uint64_t hw_launch_count(const hw_ctx* c) { return c ? c->launches : 0; }
+
+extern "C" const char* hw_last_error(void) { return g_last_error.c_str(); }
+
+// Persistent-grid scratch: two accumulators per block.
+static size_t acc_words(const hw_ctx* c) { return (size_t)hw_ext_grid(c->li) * 2 * c->sz.rlwe_words; }
+
+extern "C" size_t hw_train_scratch_words(const hw_ctx* c, size_t n) {
+    if (!c) return 0;
+    return n * c->sz.model_words + acc_words(c);
+}
+
+extern "C" size_t hw_infer_scratch_words(const hw_ctx* c, size_t n) {
+    if (!c) return 0;
+    (void)n;
+    return acc_words(c);
+}
+
+#define CHECK_CTX(c)                                                   \
+    do {                                                               \
+        if (!(c)) return fail(HW_EINVAL, "%s: null context", __func__); \
+        cudaSetDevice((c)->device);                                    \
+    } while (0)
+
+extern "C" int hw_keygen(hw_ctx* c, uint64_t seed, uint64_t* key, void* stream) {
+    CHECK_CTX(c);
+    if (!key) return fail(HW_EINVAL, "hw_keygen: null key buffer");
+    CUDA_TRY(launch_keygen(c->li, seed, key, (cudaStream_t)stream));
+    return HW_OK;
+}
+
+extern "C" int hw_encode(hw_ctx* c, const uint8_t* values, size_t n, uint8_t* bits, void* stream) {
+    CHECK_CTX(c);
+    if (n && (!values || !bits)) return fail(HW_EINVAL, "hw_encode: null buffer");
+    CUDA_TRY(launch_encode(c->li, values, n, bits, (cudaStream_t)stream));
+    return HW_OK;
+}
+
+extern "C" int hw_encrypt_sample(hw_ctx* c, const uint64_t* key, const uint8_t* bits,
+                                 const uint32_t* labels, size_t n, uint64_t seed, uint64_t first,
+                                 uint64_t* rgsw, void* stream) {
+    CHECK_CTX(c);
+    if (n && (!key || !bits || !rgsw)) return fail(HW_EINVAL, "hw_encrypt_sample: null buffer");
+    CUDA_TRY(launch_encrypt(c->li, key, bits, labels, n, seed, first, rgsw, (cudaStream_t)stream));
+    return HW_OK;
+}
+
+extern "C" int hw_train_accumulate(hw_ctx* c, uint64_t* model, const uint64_t* rgsw, size_t n,
+                                   uint64_t* scratch, size_t scratch_words, void* stream) {
+    CHECK_CTX(c);
+    if (n == 0) return HW_OK;
+    if (!model || !rgsw || !scratch) return fail(HW_EINVAL, "hw_train_accumulate: null buffer");
+    size_t need = hw_train_scratch_words(c, n);
+    if (scratch_words < need)
+        return fail(HW_ENOMEM, "hw_train_accumulate: scratch has %zu words, needs %zu", scratch_words, need);
+    int grid = hw_ext_grid(c->li);
+    u64* out = scratch;
+    u64* acc = scratch + n * c->sz.model_words;
+    cudaStream_t st = (cudaStream_t)stream;
+    CUDA_TRY(launch_ivp_train(c->li, rgsw, n, out, acc, grid, st));
+    CUDA_TRY(launch_accumulate(c->li, model, out, n, st));
+    return HW_OK;
+}
+
+extern "C" int hw_infer(hw_ctx* c, const uint64_t* model, const uint64_t* rgsw, size_t n,
+                        uint64_t* resp, uint64_t* sums, uint64_t* scratch, size_t scratch_words,
+                        void* stream) {
+    CHECK_CTX(c);
+    if (n == 0) return HW_OK;
+    if (!model || !rgsw || !resp || !sums || !scratch) return fail(HW_EINVAL, "hw_infer: null buffer");
+    size_t need = hw_infer_scratch_words(c, n);
+    if (scratch_words < need)
+        return fail(HW_ENOMEM, "hw_infer: scratch has %zu words, needs %zu", scratch_words, need);
+    int grid = hw_ext_grid(c->li);
+    cudaStream_t st = (cudaStream_t)stream;
+    CUDA_TRY(launch_vp_infer(c->li, model, rgsw, n, resp, scratch, grid, st));
+    CUDA_TRY(launch_class_sums(c->li, resp, n, sums, st));
+    return HW_OK;
+}
+
+extern "C" int hw_decrypt(hw_ctx* c, const uint64_t* key, int what, const uint64_t* obj,
+                          size_t count, int64_t* out, void* stream) {
+    CHECK_CTX(c);
+    if (count == 0) return HW_OK;
+    if (!key || !obj || !out) return fail(HW_EINVAL, "hw_decrypt: null buffer");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (what == HW_DEC_RLWE) {
+        CUDA_TRY(launch_decrypt_rlwe(c->li, key, obj, count, out, c->phase_scratch, c->phase_chunk, st));
+    } else if (what == HW_DEC_LWE) {
+        CUDA_TRY(launch_decrypt_lwe(c->li, key, obj, count, out, st));
+    } else {
+        return fail(HW_EINVAL, "hw_decrypt: unknown object kind %d", what);
+    }
+    return HW_OK;
+}
+
+extern "C" int hw_pdact(hw_ctx* c, const int64_t* counts, size_t n, int64_t* scores, int32_t* labels,
+                        void* stream) {
+    CHECK_CTX(c);
+    if (n && (!counts || !scores || !labels)) return fail(HW_EINVAL, "hw_pdact: null buffer");
+    CUDA_TRY(launch_pdact(c->li, counts, n, scores, labels, (cudaStream_t)stream));
+    return HW_OK;
+}
+
+extern "C" int hw_export_rgsw(hw_ctx* c, const uint64_t* rgsw, size_t count, uint64_t* out,
+                              void* stream) {
+    CHECK_CTX(c);
+    if (count && (!rgsw || !out)) return fail(HW_EINVAL, "hw_export_rgsw: null buffer");
+    if (rgsw == out) return fail(HW_EINVAL, "hw_export_rgsw: output must not alias input");
+    CUDA_TRY(launch_export_rgsw(c->li, rgsw, count, out, (cudaStream_t)stream));
+    return HW_OK;
+}
+
+extern "C" int hw_ntt_forward(hw_ctx* c, uint64_t* poly, size_t count, void* stream) {
+    CHECK_CTX(c);
+    if (count && !poly) return fail(HW_EINVAL, "hw_ntt_forward: null buffer");
+    CUDA_TRY(launch_ntt_batch(c->li, poly, count, 0, (cudaStream_t)stream));
+    return HW_OK;
+}
+
+extern "C" int hw_ntt_inverse(hw_ctx* c, uint64_t* poly, size_t count, void* stream) {
+    CHECK_CTX(c);
+    if (count && !poly) return fail(HW_EINVAL, "hw_ntt_inverse: null buffer");
+    CUDA_TRY(launch_ntt_batch(c->li, poly, count, 1, (cudaStream_t)stream));
+    return HW_OK;
+}

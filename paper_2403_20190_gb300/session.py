@@ -1,0 +1,110 @@
+"""Workload-level convenience over the C ABI: device buffers come from
+torch's caching allocator; every step is one libhwisard call."""
+import torch
+
+from . import binding as B
+
+
+class Session:
+    def __init__(self, cfg, device: int = 0):
+        self.cfg = cfg
+        self.device = torch.device("cuda", device)
+        self.ctx = B.hw_create(cfg, device)
+        self.sz = B.hw_get_sizes(self.ctx)
+
+    # --------------------------------------------------------------- buffers
+    def words(self, n, zero=True):
+        f = torch.zeros if zero else torch.empty
+        return f(int(n), dtype=torch.int64, device=self.device)
+
+    def keygen(self, seed, stream=None):
+        key = self.words(self.sz["key_words"])
+        B.hw_keygen(self.ctx, seed, key, stream)
+        return key
+
+    def new_model(self):
+        return self.words(self.sz["model_words"])
+
+    # ---------------------------------------------------------------- client
+    def encode(self, values, stream=None):
+        """values: uint8 CUDA tensor (n, n_values) -> data bits (n, n_data)."""
+        n = values.shape[0]
+        bits = torch.empty((n, self.sz["n_data"]), dtype=torch.uint8, device=self.device)
+        B.hw_encode(self.ctx, values.contiguous(), n, bits, stream)
+        return bits
+
+    def encrypt(self, key, bits, labels, seed, first_sample=0, out=None, stream=None):
+        n = bits.shape[0]
+        if out is None:
+            out = self.words(n * self.sz["sample_words"], zero=False)
+        lab = None if labels is None else labels.to(torch.int32).contiguous()
+        B.hw_encrypt_sample(self.ctx, key, bits.contiguous(), lab, n, seed, first_sample, out, stream)
+        return out
+
+    # ---------------------------------------------------------------- server
+    def train_scratch(self, n):
+        return self.words(B.hw_train_scratch_words(self.ctx, n), zero=False)
+
+    def train(self, model, rgsw, n, scratch=None, stream=None):
+        if scratch is None:
+            scratch = self.train_scratch(n)
+        B.hw_train_accumulate(self.ctx, model, rgsw, n, scratch, stream)
+        return model
+
+    def infer_buffers(self, n):
+        resp = self.words(n * self.sz["resp_words"], zero=False)
+        sums = self.words(n * self.sz["sums_words"], zero=False)
+        scratch = self.words(B.hw_infer_scratch_words(self.ctx, n), zero=False)
+        return resp, sums, scratch
+
+    def infer(self, model, rgsw, n, bufs=None, stream=None):
+        resp, sums, scratch = bufs if bufs is not None else self.infer_buffers(n)
+        B.hw_infer(self.ctx, model, rgsw, n, resp, sums, scratch, stream)
+        return resp, sums
+
+    # ---------------------------------------------------------------- client
+    def decrypt_rlwe(self, key, obj, count, stream=None):
+        out = torch.empty(int(count) * self.sz["n"], dtype=torch.int64, device=self.device)
+        B.hw_decrypt(self.ctx, key, B.HW_DEC_RLWE, obj, count, out, stream)
+        return out
+
+    def decrypt_lwe(self, key, obj, count, stream=None):
+        out = torch.empty(int(count), dtype=torch.int64, device=self.device)
+        B.hw_decrypt(self.ctx, key, B.HW_DEC_LWE, obj, count, out, stream)
+        return out
+
+    def pdact(self, counts, n, stream=None):
+        l = self.cfg.n_classes
+        scores = torch.empty(n * l, dtype=torch.int64, device=self.device)
+        labels = torch.empty(n, dtype=torch.int32, device=self.device)
+        B.hw_pdact(self.ctx, counts, n, scores, labels, stream)
+        return scores.view(n, l), labels
+
+    def decrypt_model_counts(self, key, model, stream=None):
+        """Decrypted counters W[c][j][addr] (l, k0, 2^a) from the model."""
+        sz = self.sz
+        n, z, L, a = sz["n"], sz["z"], sz["L"], sz["a"]
+        vals = self.decrypt_rlwe(key, model, sz["k0"] * sz["k1"], stream).view(sz["k0"], sz["k1"], n)
+        slot_of = {}
+        k = 0
+        for v in range(1 << z):
+            if any(((c + (x << L)) % (1 << z)) == v for c in range(self.cfg.n_classes)
+                   for x in range(1 << max(0, z - L))):
+                slot_of[v] = k
+                k += 1
+        l = self.cfg.n_classes
+        m = torch.arange(1 << a, device=self.device)[None, :] * (1 << L) + torch.arange(l, device=self.device)[:, None]
+        ct = m % (1 << z)
+        coef = m >> z
+        slot = torch.tensor([slot_of.get(int(v), 0) for v in range(1 << z)], device=self.device)[ct]
+        return vals[:, slot, coef].permute(1, 0, 2).contiguous()
+
+    def responses_counts(self, key, resp, n, stream=None):
+        """Decrypted responses u[i][c][j] (n, l, k0)."""
+        l, k0 = self.cfg.n_classes, self.sz["k0"]
+        return self.decrypt_lwe(key, resp, n * l * k0, stream).view(n, l, k0)
+
+    def export_rgsw(self, rgsw, count, stream=None):
+        out = self.words(int(count) * self.sz["rgsw_words"], zero=False)
+        B.hw_export_rgsw(self.ctx, rgsw, count, out, stream)
+        return out

@@ -1,0 +1,74 @@
+"""The C-ABI library builds, loads and exports every symbol the header
+declares; argument validation fails cleanly without touching the GPU."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_symbols():
+    txt = open(os.path.join(ROOT, "include", "hwisard.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(hw_[a-z_0-9]+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2403_20190_gb300 import binding, build
+    build.build()
+    return binding.load()
+
+
+def test_header_declares_the_boundary():
+    syms = header_symbols()
+    for name in ("hw_create", "hw_keygen", "hw_encrypt_sample", "hw_train_accumulate", "hw_infer",
+                 "hw_decrypt", "hw_pdact", "hw_encode"):
+        assert name in syms
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_2403_20190_gb300 import build
+    out = subprocess.run(["nm", "-D", "--defined-only", build.LIB], capture_output=True, text=True,
+                         check=True).stdout
+    exported = set(re.findall(r"\bT (hw_[a-z_0-9]+)", out))
+    missing = [s for s in header_symbols() if s not in exported]
+    assert not missing, missing
+    for s in header_symbols():
+        assert hasattr(lib, s)
+
+
+def test_binding_covers_every_declared_symbol():
+    from paper_2403_20190_gb300 import binding
+    assert set(header_symbols()) <= set(binding.EXPORTS)
+
+
+def test_invalid_parameters_rejected_before_cuda(lib):
+    from paper_2403_20190_gb300 import binding
+    from synthdata import get_config
+    for field, bad in (("log_n", 40), ("n_primes", 9), ("prime_bits", 63), ("n_classes", 1),
+                       ("addr_bits", 0), ("log_p", 0)):
+        p = binding.params_from_config(get_config("cfg2"))
+        setattr(p, field, bad)
+        h = ctypes.c_void_p()
+        assert lib.hw_create(ctypes.byref(p), 0, ctypes.byref(h)) == -1
+        assert lib.hw_last_error()
+    # more than one encrypted CMUX-tree level is refused
+    p = binding.params_from_config(get_config("cfg4", log_n=12))
+    h = ctypes.c_void_p()
+    assert lib.hw_create(ctypes.byref(p), 0, ctypes.byref(h)) == -1
+    assert b"tree" in lib.hw_last_error()
+
+
+def test_null_context_is_an_error(lib):
+    assert lib.hw_keygen(None, 1, None, None) == -1
+    assert lib.hw_train_scratch_words(None, 5) == 0
+    assert lib.hw_destroy(None) == 0
+
+
+def test_sources_are_sm103a_only():
+    from paper_2403_20190_gb300 import build
+    assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]

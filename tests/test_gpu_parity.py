@@ -1,0 +1,226 @@
+"""Bit-exact parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Small cases cover every tree shape of the workloads on tiny rings; the four
+workload parameter sets are checked on the oracle's sampled outputs (chosen
+RAMs, a few samples), and at batch size with properties that hold at any
+size: decrypted counters equal the Integer WiSARD counts (Algorithm 4) and
+PD-act labels equal the plaintext labels.  Integer work: tolerance 0.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import Oracle, wisard
+from synthdata import get_config, make_dataset
+
+pytestmark = pytest.mark.gpu
+
+
+def u64(t):
+    return t.detach().cpu().numpy().view(np.uint64)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2403_20190_gb300 import binding, build
+    build.build()
+    binding.load()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+
+
+def session(cfg):
+    from paper_2403_20190_gb300.session import Session
+    return Session(cfg, 0)
+
+
+TINY = {
+    "z0": dict(log_n=5, n_primes=1, prime_bits=30, log_beta=5, log_p=8, n_classes=2,
+               n_values=5, therm_bits=2, addr_bits=3, tuple_bits=3),
+    "zL": dict(log_n=3, n_primes=2, prime_bits=50, log_beta=0, log_p=16, n_classes=3,
+               n_values=5, therm_bits=2, addr_bits=3, tuple_bits=3),
+    "zltL_h3": dict(log_n=3, n_primes=3, prime_bits=55, log_beta=0, log_p=20, n_classes=5,
+                    n_values=4, therm_bits=3, addr_bits=2, tuple_bits=4, hash_h3=1),
+    "zgtL": dict(log_n=3, n_primes=3, prime_bits=55, log_beta=0, log_p=22, n_classes=3,
+                 n_values=4, therm_bits=2, addr_bits=4, tuple_bits=4),
+    "r2_beta1024": dict(log_n=4, n_primes=2, prime_bits=30, log_beta=10, log_p=12, n_classes=4,
+                        n_values=6, therm_bits=2, addr_bits=3, tuple_bits=3),
+}
+
+
+def tiny_cfg(name):
+    return get_config("cfg1", data_kind="uniform", act="log", act_arg=0, **TINY[name])
+
+
+def run_pipeline(cfg, n_train, n_test, seed_tr=31, seed_te=41, key_seed=21):
+    sess = session(cfg)
+    dev = sess.device
+    vals, labels = make_dataset(cfg, "train", n=n_train)
+    tvals, _ = make_dataset(cfg, "test", n=n_test)
+    key = sess.keygen(key_seed)
+    bits = sess.encode(torch.from_numpy(vals).to(dev))
+    rg = sess.encrypt(key, bits, torch.from_numpy(labels.astype(np.int32)).to(dev), seed=seed_tr)
+    model = sess.new_model()
+    sess.train(model, rg, n_train)
+    tbits = sess.encode(torch.from_numpy(tvals).to(dev))
+    trg = sess.encrypt(key, tbits, None, seed=seed_te)
+    resp, sums = sess.infer(model, trg, n_test)
+    torch.cuda.synchronize()
+    return dict(sess=sess, key=key, vals=vals, labels=labels, tvals=tvals, bits=bits, tbits=tbits,
+                rg=rg, trg=trg, model=model, resp=resp, sums=sums)
+
+
+@pytest.mark.parametrize("name", list(TINY))
+def test_tiny_rings_full_parity(name):
+    cfg = tiny_cfg(name)
+    o = Oracle(cfg)
+    P = o.P
+    R = run_pipeline(cfg, 7, 3)
+    sess = R["sess"]
+    s = o.keygen(21)
+    # key
+    key = u64(R["key"]).reshape(2, P.r, P.n)
+    for j in range(P.r):
+        assert [int(v) for v in key[0, j]] == [int(x) % P.q[j] for x in s]
+    # client encoding
+    obits = wisard.encode(P, R["vals"])
+    assert np.array_equal(R["bits"].cpu().numpy(), obits)
+    # encryption (every slot of sample 1, canonical form)
+    exp = u64(sess.export_rgsw(R["rg"], 7 * P.n_slots)).reshape(7, P.n_slots, -1)
+    for b in range(P.n_slots):
+        val = (int(R["labels"][1]) >> b) & 1 if b < P.L else int(obits[1, b - P.L])
+        ref = o.export_rgsw(o.encrypt_bit(s, 31, 1 * P.n_slots + b, val))
+        assert np.array_equal(exp[1, b], ref), f"RGSW slot {b}"
+    # training: whole model
+    H = o.train(o.new_model(), s, 31, obits, R["labels"])
+    assert np.array_equal(u64(R["model"]).reshape(H.shape), H)
+    # inference: responses and class sums
+    otb = wisard.encode(P, R["tvals"])
+    oresp, osums = o.infer(H, s, 41, otb)
+    assert np.array_equal(u64(R["resp"]).reshape(oresp.shape), oresp)
+    assert np.array_equal(u64(R["sums"]).reshape(osums.shape), osums)
+    # decryption and PD-act
+    W = wisard.integer_wisard_train(P, obits, R["labels"])
+    assert np.array_equal(sess.decrypt_model_counts(R["key"], R["model"]).cpu().numpy(), W)
+    counts = sess.responses_counts(R["key"], R["resp"], 3)
+    assert np.array_equal(counts.cpu().numpy(), wisard.lookups(P, W, otb))
+    sums_dec = sess.decrypt_lwe(R["key"], R["sums"], 3 * cfg.n_classes).view(3, cfg.n_classes)
+    assert np.array_equal(sums_dec.cpu().numpy(), wisard.lookups(P, W, otb).sum(axis=2))
+    _, lab = sess.pdact(counts.contiguous(), 3)
+    assert np.array_equal(lab.cpu().numpy(), wisard.evaluate(P, W, otb)[1])
+
+
+def test_ntt_roundtrip_and_edge_values():
+    cfg = get_config("cfg3")
+    sess = session(cfg)
+    sz = sess.sz
+    n, r = sz["n"], sz["r"]
+    count = 3 * r + 1  # ragged: polynomial t uses prime t mod r
+    rng = np.random.default_rng(0)
+    x = np.zeros((count, n), dtype=np.uint64)
+    for t in range(count):
+        q = sz["q"][t % r]
+        x[t] = rng.integers(0, q, size=n, dtype=np.uint64)
+    x[0, :4] = [0, sz["q"][0] - 1, (sz["q"][0] - 1) // 2, 1]
+    dev = torch.from_numpy(x.view(np.int64)).to(sess.device)
+    from paper_2403_20190_gb300 import binding as B
+    B.hw_ntt_forward(sess.ctx, dev, count)
+    fwd = u64(dev).reshape(count, n).copy()
+    assert not np.array_equal(fwd, x)
+    for t in range(count):
+        assert (fwd[t] < sz["q"][t % r]).all()
+    B.hw_ntt_inverse(sess.ctx, dev, count)
+    assert np.array_equal(u64(dev).reshape(count, n), x)
+
+
+@pytest.mark.parametrize("name,n_train,n_test,rams", [
+    ("cfg1", 6, 3, [0, 13, 29]),
+    ("cfg2", 3, 2, [0, 77, 130]),
+    ("cfg3", 2, 1, [5, 146]),
+    ("cfg4", 2, 1, [0, 503]),
+])
+def test_workload_parameters_sampled_parity(name, n_train, n_test, rams):
+    """Real ring sizes and primes: RGSW rows, trained model rows and
+    inference responses on chosen RAMs (the last RAM included) bit-exact."""
+    cfg = get_config(name)
+    o = Oracle(cfg)
+    P = o.P
+    R = run_pipeline(cfg, n_train, n_test)
+    sess = R["sess"]
+    s = o.keygen(21)
+    obits = wisard.encode(P, R["vals"])
+    assert np.array_equal(R["bits"].cpu().numpy(), obits)
+    # one label slot and one data slot of the last sample, canonical form
+    i = n_train - 1
+    for b in (0, P.n_slots - 1):
+        exp = u64(sess.export_rgsw(R["rg"][(i * P.n_slots + b) * sess.sz["rgsw_words"]:
+                                         (i * P.n_slots + b + 1) * sess.sz["rgsw_words"]], 1))
+        val = (int(R["labels"][i]) >> b) & 1 if b < P.L else int(obits[i, b - P.L])
+        ref = o.export_rgsw(o.encrypt_bit(s, 31, i * P.n_slots + b, val))
+        assert np.array_equal(exp, ref), f"RGSW slot {b}"
+    H = o.train(o.new_model(), s, 31, obits, R["labels"], rams=rams)
+    gH = u64(R["model"]).reshape(H.shape)
+    assert np.array_equal(gH[rams], H[rams])
+    otb = wisard.encode(P, R["tvals"])
+    oresp, _ = o.infer(H, s, 41, otb, rams=rams)
+    gresp = u64(R["resp"]).reshape(n_test, cfg.n_classes, P.k0, -1)
+    assert np.array_equal(gresp[:, :, rams], oresp)
+
+
+@pytest.mark.parametrize("name,n_train,n_test", [("cfg1", 200, 100), ("cfg2", 64, 32)])
+def test_batch_invariants(name, n_train, n_test):
+    """At batch size: decrypted counters == Algorithm 4 counts for every RAM,
+    decrypted responses == plaintext lookups, class sums == Algorithm 2 scores
+    (cfg2; cfg1's 30-bit modulus leaves class sums undecodable by design),
+    PD-act labels == plaintext labels."""
+    cfg = get_config(name)
+    o = Oracle(cfg)
+    P = o.P
+    R = run_pipeline(cfg, n_train, n_test)
+    sess = R["sess"]
+    obits = wisard.encode(P, R["vals"])
+    W = wisard.integer_wisard_train(P, obits, R["labels"])
+    assert np.array_equal(sess.decrypt_model_counts(R["key"], R["model"]).cpu().numpy(), W)
+    otb = wisard.encode(P, R["tvals"])
+    counts = sess.responses_counts(R["key"], R["resp"], n_test)
+    assert np.array_equal(counts.cpu().numpy(), wisard.lookups(P, W, otb))
+    if name != "cfg1":
+        sd = sess.decrypt_lwe(R["key"], R["sums"], n_test * cfg.n_classes).view(n_test, -1)
+        assert np.array_equal(sd.cpu().numpy(), wisard.lookups(P, W, otb).sum(axis=2))
+    _, lab = sess.pdact(counts.contiguous(), n_test)
+    assert np.array_equal(lab.cpu().numpy(), wisard.evaluate(P, W, otb)[1])
+
+
+def test_empty_batches_and_scratch_checks():
+    from paper_2403_20190_gb300 import binding as B
+    cfg = tiny_cfg("zL")
+    sess = session(cfg)
+    model = sess.new_model()
+    empty = sess.words(1)
+    B.hw_train_accumulate(sess.ctx, model, empty, 0, empty)
+    assert not model.any()
+    key = sess.keygen(1)
+    bits = torch.zeros((2, sess.sz["n_data"]), dtype=torch.uint8, device=sess.device)
+    rg = sess.encrypt(key, bits, torch.zeros(2, dtype=torch.int32, device=sess.device), seed=1)
+    small = sess.words(B.hw_train_scratch_words(sess.ctx, 2) - 1)
+    with pytest.raises(B.HwError):
+        B.hw_train_accumulate(sess.ctx, model, rg, 2, small)
+
+
+def test_split_batches_equal_one_batch():
+    """Training in two calls equals training in one (addition mod q is
+    associative): the batched path is bit-identical to sequential calls."""
+    cfg = tiny_cfg("zgtL")
+    sess = session(cfg)
+    dev = sess.device
+    vals, labels = make_dataset(cfg, "train", n=6)
+    key = sess.keygen(3)
+    bits = sess.encode(torch.from_numpy(vals).to(dev))
+    lab = torch.from_numpy(labels.astype(np.int32)).to(dev)
+    rg = sess.encrypt(key, bits, lab, seed=5)
+    one = sess.train(sess.new_model(), rg, 6)
+    two = sess.new_model()
+    sw = sess.sz["sample_words"]
+    sess.train(two, rg[:4 * sw], 4)
+    sess.train(two, rg[4 * sw:], 2)
+    torch.cuda.synchronize()
+    assert torch.equal(one, two)
