@@ -118,7 +118,9 @@ __global__ void __launch_bounds__(1024) k_vp_infer(const DevCtx* __restrict__ Cp
         const int i = ij / C.k0, j = ij % C.k0;
         const u64* sample = rgsw + (size_t)i * C.sample_words;
         const u64* Hj = model + (size_t)j * C.k1 * rl;
-        u64* lwe = resp + (size_t)item * C.lwe_words;
+        // items run class-fastest (the l classes of a (sample, RAM) share its
+        // RGSW bits); responses are stored [sample][class][RAM]
+        u64* lwe = resp + (((size_t)i * l + c) * C.k0 + j) * C.lwe_words;
         const u64* src;
         int e0;
         int cur = 0;
