@@ -1,0 +1,453 @@
+#!/usr/bin/env python3
+"""Benchmark of the encrypted WiSARD hot path on GB300; prints one JSON line.
+
+A step is one pass of the whole path over one batch: B training samples are
+encoded, RGSW-encrypted and trained into the resident model (IVP +
+accumulate), and B test samples are encoded, encrypted, inferred (VP,
+ExtractLWE, class sums), decrypted and classified with PD-act.  The workload
+is the batched 10-class 28x28 digit configuration (N = 4096, two ~50-bit RNS
+primes, 131 RAMs of 2^12 entries).  Raw samples sit in HBM before the timed
+region; encrypted batches (~50 GB per step) are far larger than L2.
+
+--impl reference times the CPU oracle on the host cores instead, on a
+bounded sample of the same workload.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "encrypted samples/s (train + inference, bit-exact)"
+UNIT = "samples/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+# Integer multiply throughput of one SM per clock (32-bit multiply-add lanes)
+# and the minimum 32x32-bit multiplies of one 64-bit Shoup modular product
+# (high half of x*w': 4 partial products; low halves of x*w and qhat*q: 3 each).
+IMAD_PER_CLK_PER_SM = 64
+MULS_PER_MODMUL = 10
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--config", default="cfg2")
+    ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-ntt", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------- helpers
+def peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            d = json.load(f)
+        return d, "measured"
+    except OSError:
+        return {"hbm_gbs": FALLBACK_HBM_GBS, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.device)], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "gb300" else "gloo"
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return ws, rank, local, pg
+
+
+# -------------------------------------------------------------- the oracle
+def _oracle_worker(job):
+    """One worker of the CPU baseline: the oracle encrypts one train and one
+    test sample's bits for its RAMs, runs the IVP of each RAM and the VP of
+    each (RAM, class); returns the seconds it took."""
+    cfg_name, rams = job
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    from oracle import Oracle, wisard
+    from synthdata import get_config, make_dataset
+    cfg = get_config(cfg_name)
+    t0 = time.perf_counter()
+    o = Oracle(cfg)
+    vals, labels = make_dataset(cfg, "train", n=1)
+    tvals, _ = make_dataset(cfg, "test", n=1)
+    s = o.keygen(cfg.key_seed)
+    bits = wisard.encode(o.P, vals)
+    tbits = wisard.encode(o.P, tvals)
+    H = o.train(o.new_model(), s, 101, bits, labels, rams=rams)
+    o.infer(H, s, 202, tbits, rams=rams)
+    _ = np
+    return time.perf_counter() - t0
+
+
+def oracle_sample(cfg_name, k0, workers, rams_per_worker=1):
+    import multiprocessing as mp
+    jobs = []
+    stride = max(1, k0 // (workers * rams_per_worker))
+    r = 0
+    for w in range(workers):
+        rams = [(r + t * stride) % k0 for t in range(rams_per_worker)]
+        r += 1
+        jobs.append((cfg_name, rams))
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(workers) as pool:
+        pool.map(_oracle_worker, jobs)
+    wall = time.perf_counter() - t0
+    rams_done = workers * rams_per_worker
+    samples = 2.0 * rams_done / k0  # one train + one test sample, over all k0 RAMs
+    return samples / wall, wall, rams_done
+
+
+def reference_arm(args, ws, rank):
+    if ws > 1 and rank != 0:
+        return
+    from synthdata import get_config
+    from oracle import Oracle
+    cfg = get_config(args.config)
+    k0 = Oracle(cfg).P.k0
+    cores = min(os.cpu_count() or 1, 16)
+    times = []
+    for it in range(args.warmup + args.steps):
+        rate, wall, rams = oracle_sample(args.config, k0, cores)
+        if it >= args.warmup:
+            times.append((rate, wall, rams))
+    rate = statistics.mean(t[0] for t in times)
+    sample = (f"per step: 1 train + 1 test sample restricted to {times[0][2]} of {k0} RAMs "
+              f"(one RAM per worker process), scaled by {k0}/{times[0][2]}")
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * statistics.mean(t[1] for t in times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic",
+            "config": {"workload": workload_name(cfg), "sample": sample},
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def workload_name(cfg):
+    return (f"{cfg.name}: {cfg.n_classes}-class synthetic {cfg.data_kind}, {cfg.n_values} values x "
+            f"{cfg.therm_bits}-bit thermometer, {cfg.addr_bits}-bit RAM addresses, "
+            f"N=2^{cfg.log_n}, {cfg.n_primes}x{cfg.prime_bits}-bit RNS primes")
+
+
+# ------------------------------------------------------------ the GPU arm
+def algorithmic_counts(sess, cfg):
+    """Modular multiplications of the VP kernel per test sample and of the
+    IVP kernel per train sample, counted from the algorithm: every external
+    product runs 2*dnum*r forward and 2*r inverse transforms of (N/2) log2 N
+    butterflies each, and 2*(2*dnum)*r*N products in evaluation form."""
+    from paper_2403_20190_gb300 import binding as B
+    sz = sess.sz
+    n, r, dnum, L, z, a, k0, l = (sz["n"], sz["r"], sz["dnum"], sz["L"], sz["z"], sz["a"],
+                                  sz["k0"], cfg.n_classes)
+    logn = n.bit_length() - 1
+    bfly = (n // 2) * logn
+    per_ext = 2 * dnum * r * bfly + 2 * r * bfly + 2 * 2 * dnum * r * n
+    slots = B.hw_get_ram_slots(sess.ctx)
+    ext_train = ext_infer = 0
+    gates = {1: 0}
+    for j in range(k0):
+        enc = [slots[j * a + i] >= 0 for i in range(a)]
+        # training: rotation bits z..L+a-1 that are encrypted (labels always are)
+        rot = sum(1 for t in range(z, L + a) if (t < L or enc[t - L]))
+        ext_train += rot
+        # inference: encrypted address bits among the rotation bits, plus a tree CMUX if z > L
+        rot_i = sum(1 for t in range(max(z, L), L + a) if enc[t - L])
+        tree_i = 1 if (z > L and enc[z - 1 - L]) else 0
+        ext_infer += l * (rot_i + tree_i)
+    _ = gates
+    # pruned CDEMUX gates per RAM (same for every RAM when their tree bits are encrypted)
+    V = set()
+    for c in range(l):
+        for x in range(1 << max(0, z - L)):
+            V.add((c + (x << L)) % (1 << z))
+    g = sum(1 for i in range(z) for jj in range(1 << i)
+            if any(v % (1 << (i + 1)) == jj + (1 << i) for v in V))
+    ext_train += k0 * g
+    return {"per_ext_modmul": per_ext, "ext_train_per_sample": ext_train,
+            "ext_infer_per_sample": ext_infer,
+            "rgsw_bytes": sz["rgsw_words"] * 8}
+
+
+def gpu_arm(args, ws, rank, local, pg):
+    import numpy as np
+    import torch
+
+    from paper_2403_20190_gb300 import binding as B
+    from paper_2403_20190_gb300 import build as libbuild
+    from paper_2403_20190_gb300.session import Session
+    from synthdata import get_config, make_dataset
+
+    libbuild.build()
+    torch.cuda.set_device(local)
+    cfg = get_config(args.config)
+    sess = Session(cfg, local)
+    dev = sess.device
+    bsz = args.batch
+    sz = sess.sz
+    n_pool = max(cfg.n_train, bsz)
+    # the whole train / test sets of the workload, resident in HBM as raw bytes
+    tr_vals, tr_lab = make_dataset(cfg, "train", n=n_pool)
+    te_vals, _ = make_dataset(cfg, "test", n=max(cfg.n_test, bsz))
+    tr_vals_d = torch.from_numpy(tr_vals).to(dev)
+    tr_lab_d = torch.from_numpy(tr_lab.astype(np.int32)).to(dev)
+    te_vals_d = torch.from_numpy(te_vals).to(dev)
+
+    key = sess.keygen(cfg.key_seed)
+    model = sess.new_model()
+    rgsw = sess.words(bsz * sz["sample_words"], zero=False)
+    tscratch = sess.train_scratch(bsz)
+    ibufs = sess.infer_buffers(bsz)
+    bits = torch.empty((bsz, sz["n_data"]), dtype=torch.uint8, device=dev)
+    counts = torch.empty(bsz * cfg.n_classes * sz["k0"], dtype=torch.int64, device=dev)
+    scores = torch.empty(bsz * cfg.n_classes, dtype=torch.int64, device=dev)
+    labels_out = torch.empty(bsz, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    n_tr = tr_vals_d.shape[0]
+    n_te = te_vals_d.shape[0]
+    offset = rank * 7919  # replicas draw different samples
+
+    def step(k, evs=None, host=None):
+        i0 = ((k * bsz + offset) % n_tr)
+        i0 = min(i0, n_tr - bsz)
+        j0 = min(((k * bsz + offset) % n_te), n_te - bsz)
+        if host is not None:
+            h_tr, h_lab, h_te = host[:3]
+            tv = tr_vals_d[:bsz]
+            tl = tr_lab_d[:bsz]
+            tev = te_vals_d[:bsz]
+            tv.copy_(h_tr, non_blocking=True)
+            tl.copy_(h_lab, non_blocking=True)
+            tev.copy_(h_te, non_blocking=True)
+        else:
+            tv, tl, tev = tr_vals_d[i0:i0 + bsz], tr_lab_d[i0:i0 + bsz], te_vals_d[j0:j0 + bsz]
+        ev = (lambda name: evs[name].record(stream)) if evs else (lambda name: None)
+        ev("t0")
+        B.hw_encode(sess.ctx, tv, bsz, bits, stream)
+        B.hw_encrypt_sample(sess.ctx, key, bits, tl, bsz, 1000 + k, 0, rgsw, stream)
+        ev("t1")
+        B.hw_train_accumulate(sess.ctx, model, rgsw, bsz, tscratch, stream)
+        ev("t2")
+        B.hw_encode(sess.ctx, tev, bsz, bits, stream)
+        B.hw_encrypt_sample(sess.ctx, key, bits, None, bsz, 500000 + k, 0, rgsw, stream)
+        ev("t3")
+        resp, sums, scr = ibufs
+        B.hw_infer(sess.ctx, model, rgsw, bsz, resp, sums, scr, stream)
+        ev("t4")
+        B.hw_decrypt(sess.ctx, key, B.HW_DEC_LWE, resp, bsz * cfg.n_classes * sz["k0"], counts, stream)
+        B.hw_pdact(sess.ctx, counts, bsz, scores, labels_out, stream)
+        ev("t5")
+        if host is not None:
+            host[3].copy_(labels_out, non_blocking=True)
+
+    names = ["t0", "t1", "t2", "t3", "t4", "t5"]
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if pg is not None:
+            pg.barrier()
+
+    evsets = [{nm: torch.cuda.Event(enable_timing=True) for nm in names} for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = B.hw_launch_count(sess.ctx)
+    barrier()
+    torch.cuda.synchronize()
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for k in range(args.steps):
+        step(args.warmup + k, evsets[k])
+    end.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = B.hw_launch_count(sess.ctx) - launches0
+    clk = clocks.stop()
+    elapsed_ms = start.elapsed_time(end)
+    if pg is not None:
+        t = torch.tensor([elapsed_ms], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    phase = {"encrypt_train": [], "train": [], "encrypt_test": [], "infer": [], "decrypt_pdact": []}
+    keys = list(phase)
+    for evs in evsets:
+        for a, b, kname in zip(names[:-1], names[1:], keys):
+            phase[kname].append(evs[a].elapsed_time(evs[b]))
+    ph = {k: statistics.mean(v) for k, v in phase.items()}
+    total_samples = 2 * bsz * args.steps * ws
+    value = total_samples / (elapsed_ms / 1000.0)
+
+    # e2e through the C ABI with pinned host buffers, copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        h_tr = torch.from_numpy(tr_vals[:bsz].copy()).pin_memory()
+        h_lab = torch.from_numpy(tr_lab[:bsz].astype(np.int32)).pin_memory()
+        h_te = torch.from_numpy(te_vals[:bsz].copy()).pin_memory()
+        h_out = torch.empty(bsz, dtype=torch.int32).pin_memory()
+        host = (h_tr, h_lab, h_te, h_out)
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            step(args.warmup + args.steps + k, None, host)
+            torch.cuda.current_stream().synchronize()
+            _ = int(h_out[0])
+        t1 = time.perf_counter()
+        e2e_s = t1 - t0
+        if pg is not None:
+            t = torch.tensor([e2e_s], device=dev)
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": total_samples / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": int(h_tr.numel() + h_lab.numel() * 4 + h_te.numel()),
+               "d2h_bytes_per_step": int(h_out.numel() * 4)}
+
+    # roofline of the dominant kernel (the VP inference kernel)
+    pk, pk_kind = peaks()
+    alg = algorithmic_counts(sess, cfg)
+    sm_count = torch.cuda.get_device_properties(local).multi_processor_count
+    sm_mhz = pk.get("sm_max_mhz", 2070.0)
+    peak_modmul = sm_count * IMAD_PER_CLK_PER_SM * sm_mhz * 1e6 / MULS_PER_MODMUL
+    infer_modmul = alg["ext_infer_per_sample"] * bsz * alg["per_ext_modmul"]
+    achieved = infer_modmul / (ph["infer"] / 1000.0)
+    roofline = {"bound": "alu", "kernel": "k_vp_infer", "achieved": achieved / 1e12,
+                "peak": peak_modmul / 1e12, "unit": "T modmul/s", "frac": achieved / peak_modmul,
+                "traffic": None,
+                "peak_kind": f"derived: {sm_count} SMs x {IMAD_PER_CLK_PER_SM} int32 multiplies/clk x "
+                             f"{sm_mhz:.0f} MHz / {MULS_PER_MODMUL} per 64-bit modular product"}
+    train_modmul = alg["ext_train_per_sample"] * bsz * alg["per_ext_modmul"]
+
+    # batched NTT throughput (forward transforms, one read + one write per polynomial)
+    ntt = None
+    if not args.no_ntt:
+        count = 65536 if sz["n"] <= 4096 else 32768
+        polys = sess.words(count * sz["n"])
+        for _ in range(3):
+            B.hw_ntt_forward(sess.ctx, polys, count, stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 5
+        e0.record(stream)
+        for _ in range(reps):
+            B.hw_ntt_forward(sess.ctx, polys, count, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / reps / 1000.0
+        gbs = 2.0 * count * sz["n"] * 8 / t / 1e9
+        ntt = {"gbs": gbs, "frac_of_hbm": gbs / pk["hbm_gbs"], "polys": count, "n": sz["n"],
+               "peak_gbs": pk["hbm_gbs"], "peak_kind": pk_kind}
+        del polys
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cores = min(os.cpu_count() or 1, 16)
+        rate, wall, rams = oracle_sample(args.config, sz["k0"], cores)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"1 train + 1 test sample restricted to {rams} of {sz['k0']} RAMs "
+                         f"(one per worker), {wall:.1f} s wall, scaled by {sz['k0']}/{rams}"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic",
+            "config": {"workload": workload_name(cfg), "batch_train": bsz, "batch_test": bsz,
+                       "l2": "inputs larger than L2 (encrypted batch ~%.0f GB)" %
+                             (bsz * sz["sample_words"] * 8 / 1e9),
+                       "parallelism": "replicas" if ws > 1 else "single GPU"},
+            "train_samples_per_s": bsz / (ph["train"] / 1000.0),
+            "inferences_per_s": bsz / (ph["infer"] / 1000.0),
+            "train_modmul_per_s": train_modmul / (ph["train"] / 1000.0),
+            "phases_ms": ph,
+            "roofline": roofline,
+            "ntt": ntt,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clk,
+            "p99_ms": None,
+        }
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    ws, rank, local, pg = dist_setup(args)
+    if args.impl == "reference":
+        reference_arm(args, ws, rank)
+    else:
+        gpu_arm(args, ws, rank, local, pg)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
