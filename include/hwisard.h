@@ -154,6 +154,27 @@ int hw_decrypt(hw_ctx* ctx, const uint64_t* key_dev, int what, const uint64_t* o
 int hw_pdact(hw_ctx* ctx, const int64_t* counts_dev, size_t n, int64_t* scores_dev,
              int32_t* labels_dev, void* stream);
 
+/* hw_infer without caller scratch (the paper has no counterpart; this is a
+ * library convenience).  For callers that cannot allocate device memory --
+ * a request loop that may not call cudaMalloc, or a plug-in that only sees
+ * the input and output buffers -- the per-block accumulators of the
+ * inference kernel come from a static device array of
+ * HW_STATIC_SCRATCH_BYTES that every GPU loading the library holds until the
+ * process exits.  Results are identical to hw_infer().
+ * - The first call on a device looks up the array's device address (with
+ *   that device current); make that first call before any stream capture.
+ * - All calls share the array: calls whose work overlaps on the GPU (other
+ *   streams, other threads, other contexts on the same device) race.  Order
+ *   them, e.g. on one stream.
+ * - Rings whose two accumulators per block exceed the array (2 * rlwe_words
+ *   * 8 bytes > HW_STATIC_SCRATCH_BYTES) are rejected with HW_EINVAL; the
+ *   number of resident blocks is capped so that all of them fit.
+ * - Nothing is allocated or freed: no cudaMalloc, cudaFree or allocating
+ *   library call. */
+#define HW_STATIC_SCRATCH_BYTES (48u << 20)
+int hw_infer_static_scratch(hw_ctx* ctx, const uint64_t* model_dev, const uint64_t* rgsw_dev,
+                            size_t n, uint64_t* resp_dev, uint64_t* sums_dev, void* stream);
+
 /* Canonical coefficient form of count RGSW ciphertexts (for checks). */
 int hw_export_rgsw(hw_ctx* ctx, const uint64_t* rgsw_dev, size_t count, uint64_t* out_dev,
                    void* stream);

@@ -54,6 +54,7 @@ _SIGS = {
     "hw_encrypt_sample": (ctypes.c_int, [_VP, _VP, _VP, _VP, _SZ, _U64, _U64, _VP, _VP]),
     "hw_train_accumulate": (ctypes.c_int, [_VP, _VP, _VP, _SZ, _VP, _SZ, _VP]),
     "hw_infer": (ctypes.c_int, [_VP, _VP, _VP, _SZ, _VP, _VP, _VP, _SZ, _VP]),
+    "hw_infer_static_scratch": (ctypes.c_int, [_VP, _VP, _VP, _SZ, _VP, _VP, _VP]),
     "hw_decrypt": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, _SZ, _VP, _VP]),
     "hw_pdact": (ctypes.c_int, [_VP, _VP, _SZ, _VP, _VP, _VP]),
     "hw_export_rgsw": (ctypes.c_int, [_VP, _VP, _SZ, _VP, _VP]),
@@ -188,6 +189,13 @@ def hw_train_accumulate(ctx, model, rgsw, n, scratch, stream=None):
 def hw_infer(ctx, model, rgsw, n, resp, sums, scratch, stream=None):
     _check(load().hw_infer(ctx.handle, _ptr(model), _ptr(rgsw), n, _ptr(resp), _ptr(sums),
                            _ptr(scratch), scratch.numel(), _stream(stream)), "hw_infer")
+
+
+def hw_infer_static_scratch(ctx, model, rgsw, n, resp, sums, stream=None):
+    """hw_infer for callers that cannot allocate: the kernel's accumulators
+    live in the library's static device array (see include/hwisard.h)."""
+    _check(load().hw_infer_static_scratch(ctx.handle, _ptr(model), _ptr(rgsw), n, _ptr(resp),
+                                          _ptr(sums), _stream(stream)), "hw_infer_static_scratch")
 
 
 def hw_decrypt(ctx, key, what, obj, count, out, stream=None):

@@ -455,6 +455,11 @@ extern "C" int hw_get_ram_slots(const hw_ctx* c, int32_t* dst, size_t n) {
 
 extern "C" uint64_t hw_launch_count(const hw_ctx* c) { return c ? c->launches : 0; }
 
+// Accessors for entry points defined in other translation units.
+const LaunchInfo* hw_ctx_launch_info(const hw_ctx* c) { return &c->li; }
+int hw_ctx_device(const hw_ctx* c) { return c->device; }
+int hw_ctx_fail(int code, const char* msg) { return fail(code, "%s", msg); }
+
 extern "C" const char* hw_last_error(void) { return g_last_error.c_str(); }
 
 // Persistent-grid scratch: two accumulators per block.
