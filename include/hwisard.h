@@ -158,7 +158,8 @@ int hw_pdact(hw_ctx* ctx, const int64_t* counts_dev, size_t n, int64_t* scores_d
  * library convenience).  For callers that cannot allocate device memory --
  * a request loop that may not call cudaMalloc, or a plug-in that only sees
  * the input and output buffers -- the per-block accumulators of the
- * inference kernel come from a static device array of
+ * inference kernel (and their evaluation forms) come from a static device
+ * array of
  * HW_STATIC_SCRATCH_BYTES that every GPU loading the library holds until the
  * process exits.  Results are identical to hw_infer().
  * - The first call on a device looks up the array's device address (with
@@ -166,9 +167,9 @@ int hw_pdact(hw_ctx* ctx, const int64_t* counts_dev, size_t n, int64_t* scores_d
  * - All calls share the array: calls whose work overlaps on the GPU (other
  *   streams, other threads, other contexts on the same device) race.  Order
  *   them, e.g. on one stream.
- * - Rings whose two accumulators per block exceed the array (2 * rlwe_words
- *   * 8 bytes > HW_STATIC_SCRATCH_BYTES) are rejected with HW_EINVAL; the
- *   number of resident blocks is capped so that all of them fit.
+ * - Rings whose four per-block buffers exceed the array (4 * rlwe_words * 8
+ *   bytes > HW_STATIC_SCRATCH_BYTES) are rejected with HW_EINVAL; the number
+ *   of resident blocks is capped so that all of them fit.
  * - Nothing is allocated or freed: no cudaMalloc, cudaFree or allocating
  *   library call. */
 #define HW_STATIC_SCRATCH_BYTES (48u << 20)

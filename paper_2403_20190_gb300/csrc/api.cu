@@ -142,7 +142,7 @@ static int ilog2_ceil(int l) {
 extern "C" int hw_create(const hw_params* p, int cuda_device, hw_ctx** out) {
     if (!p || !out) return fail(HW_EINVAL, "hw_create: null argument");
     *out = nullptr;
-    if (p->log_n < 3 || p->log_n > 13) return fail(HW_EINVAL, "log_n must be in [3, 13]");
+    if (p->log_n < 6 || p->log_n > 13) return fail(HW_EINVAL, "log_n must be in [6, 13]");
     if (p->n_primes < 1 || p->n_primes > 3) return fail(HW_EINVAL, "n_primes must be 1..3");
     if (p->prime_bits < 20 || p->prime_bits > 55) return fail(HW_EINVAL, "prime_bits must be 20..55");
     if (p->log_beta < 0 || p->log_beta > 30) return fail(HW_EINVAL, "log_beta must be 0..30");
@@ -298,12 +298,10 @@ extern "C" int hw_create(const hw_params* p, int cuda_device, hw_ctx** out) {
         H.gconst[rho] = p->log_beta ? hpow((u64)1 << p->log_beta, (u64)k, q[i]) : 1;
     }
 
-    // transform tables
+    // transform tables: interleaved (w, Shoup(w)) pairs, [prime][N]
     std::vector<u64> tw((size_t)4 * r * n);
     u64* tw_fwd = tw.data();
-    u64* tw_fwd_s = tw_fwd + (size_t)r * n;
-    u64* tw_inv = tw_fwd_s + (size_t)r * n;
-    u64* tw_inv_s = tw_inv + (size_t)r * n;
+    u64* tw_inv = tw_fwd + (size_t)2 * r * n;
     for (int i = 0; i < r; i++) {
         u64 psi = find_root(q[i], log_n);
         if (!psi) {
@@ -314,12 +312,57 @@ extern "C" int hw_create(const hw_params* p, int cuda_device, hw_ctx** out) {
         for (int k = 0; k < n; k++) {
             int e = brv(k, log_n);
             u64 w = hpow(psi, (u64)e, q[i]), wi = hpow(psi_inv, (u64)e, q[i]);
-            tw_fwd[(size_t)i * n + k] = w;
-            tw_fwd_s[(size_t)i * n + k] = shoup(w, q[i]);
-            tw_inv[(size_t)i * n + k] = wi;
-            tw_inv_s[(size_t)i * n + k] = shoup(wi, q[i]);
+            size_t o = 2 * ((size_t)i * n + k);
+            tw_fwd[o] = w;
+            tw_fwd[o + 1] = shoup(w, q[i]);
+            tw_inv[o] = wi;
+            tw_inv[o + 1] = shoup(wi, q[i]);
         }
     }
+    // rotation tables (Psi^(+-2^t) - 1 and inverses), interleaved with Shoup
+    // companions; X^e evaluates to psi^((2 brv(pos) + 1) e) at position pos
+    std::vector<u64> rot((size_t)2 * r * 2 * log_n * n), rinv((size_t)2 * r * 2 * log_n * n);
+    {
+        std::vector<u64> dv((size_t)2 * log_n * n), pre((size_t)2 * log_n * n);
+        for (int i = 0; i < r; i++) {
+            u64 psi = find_root(q[i], log_n), psi_inv = hinv(psi, q[i]);
+            for (int pos = 0; pos < n; pos++) {
+                u64 ev = 2 * (u64)brv(pos, log_n) + 1;
+                for (int sg = 0; sg < 2; sg++) {
+                    u64 x = hpow(sg ? psi_inv : psi, ev, q[i]);
+                    for (int t = 0; t < log_n; t++) {
+                        dv[((size_t)sg * log_n + t) * n + pos] = (x + q[i] - 1) % q[i];
+                        x = hmul(x, x, q[i]);
+                    }
+                }
+            }
+            // batch inversion: one Fermat inverse for the whole table
+            u64 run = 1;
+            for (size_t k = 0; k < dv.size(); k++) {
+                pre[k] = run;
+                run = hmul(run, dv[k], q[i]);
+            }
+            u64 inv = hinv(run, q[i]);
+            for (size_t k = dv.size(); k-- > 0;) {
+                u64 dk = hmul(inv, pre[k], q[i]);
+                inv = hmul(inv, dv[k], q[i]);
+                size_t o = 2 * ((size_t)i * 2 * log_n * n + k);
+                rot[o] = dv[k];
+                rot[o + 1] = shoup(dv[k], q[i]);
+                rinv[o] = dk;
+                rinv[o + 1] = shoup(dk, q[i]);
+            }
+        }
+    }
+    H.diag = p->log_beta == 0 ? 1 : 0;
+
+    // digits must lift without reduction: |d| <= (q_i - 1)/2 < q_j
+    for (int i = 0; i < r; i++)
+        for (int j = 0; j < r; j++)
+            if ((q[i] - 1) / 2 >= q[j]) {
+                delete c;
+                return fail(HW_EINVAL, "primes too far apart for the RNS gadget");
+            }
 
     // pi_r (Fisher-Yates from the top with the PERM stream), H3 rows, RAM slots
     std::vector<int32_t> perm(s);
@@ -346,9 +389,10 @@ extern "C" int hw_create(const hw_params* p, int cuda_device, hw_ctx** out) {
 
     // upload
     size_t bytes_tw = tw.size() * 8, bytes_rs = c->ram_slot.size() * 4, bytes_perm = perm.size() * 4,
-           bytes_h3 = h3.size() * 8;
+           bytes_h3 = h3.size() * 8, bytes_rot = rot.size() * 8;
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    size_t total = al(bytes_tw) + al(bytes_rs) + al(bytes_perm) + al(bytes_h3) + al(sizeof(DevCtx));
+    size_t total = al(bytes_tw) + al(bytes_rs) + al(bytes_perm) + al(bytes_h3) + 2 * al(bytes_rot) +
+                   al(sizeof(DevCtx));
     c->phase_chunk = 64;
     cudaError_t e = cudaSetDevice(cuda_device);
     if (e == cudaSuccess) e = cudaMalloc(&c->tables, total);
@@ -367,13 +411,13 @@ extern "C" int hw_create(const hw_params* p, int cuda_device, hw_ctx** out) {
         return d;
     };
     char* d_tw = put(tw.data(), bytes_tw);
-    H.tw_fwd = (const u64*)d_tw;
-    H.tw_fwd_s = H.tw_fwd + (size_t)r * n;
-    H.tw_inv = H.tw_fwd_s + (size_t)r * n;
-    H.tw_inv_s = H.tw_inv + (size_t)r * n;
+    H.tw_fwd = (const ulonglong2*)d_tw;
+    H.tw_inv = H.tw_fwd + (size_t)r * n;
     H.ram_slot = (const int32_t*)put(c->ram_slot.data(), bytes_rs);
     H.perm = (const int32_t*)put(perm.data(), bytes_perm);
     H.h3 = (const u64*)put(h3.data(), bytes_h3);
+    H.rot_tab = (const ulonglong2*)put(rot.data(), bytes_rot);
+    H.rot_inv = (const ulonglong2*)put(rinv.data(), bytes_rot);
     c->dctx = (DevCtx*)put(&H, sizeof(DevCtx));
     e = hw_kernels_init(log_n);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -462,18 +506,17 @@ int hw_ctx_fail(int code, const char* msg) { return fail(code, "%s", msg); }
 
 extern "C" const char* hw_last_error(void) { return g_last_error.c_str(); }
 
-// Persistent-grid scratch: two accumulators per block.
-static size_t acc_words(const hw_ctx* c) { return (size_t)hw_ext_grid(c->li) * 2 * c->sz.rlwe_words; }
-
+// Persistent-grid scratch per block: two accumulators and their evaluation
+// forms (inference), plus the evaluation forms of the k1 tree slots (training).
 extern "C" size_t hw_train_scratch_words(const hw_ctx* c, size_t n) {
     if (!c) return 0;
-    return n * c->sz.model_words + acc_words(c);
+    return n * c->sz.model_words + (size_t)hw_ext_grid(c->li) * (4 + c->sz.k1) * c->sz.rlwe_words;
 }
 
 extern "C" size_t hw_infer_scratch_words(const hw_ctx* c, size_t n) {
     if (!c) return 0;
     (void)n;
-    return acc_words(c);
+    return (size_t)hw_ext_grid(c->li) * 4 * c->sz.rlwe_words;
 }
 
 #define CHECK_CTX(c)                                                   \

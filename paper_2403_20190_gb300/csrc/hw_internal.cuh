@@ -15,7 +15,8 @@
 #define HW_MAX_GATES 32
 #define HW_LIMBS 4
 
-// Everything a kernel needs to know about a context, passed by value.
+// Everything a kernel needs to know about a context (kept in device memory;
+// kernels receive a pointer to it).
 struct DevCtx {
     int log_n, n, r, dnum, dpp, log_beta;
     int L, a, k0, k1, z, n_slots, n_data, s, n_classes;
@@ -32,144 +33,20 @@ struct DevCtx {
     int8_t gate_lvl[HW_MAX_GATES], gate_j[HW_MAX_GATES];
     int8_t slot_of[1 << HW_MAX_Z];         // tree index v -> stored ciphertext slot, -1 if none
     // device tables
-    const u64* tw_fwd;    // [r][N] psi^brv(i)
-    const u64* tw_fwd_s;  // Shoup companions
-    const u64* tw_inv;    // [r][N] psi^-brv(i)
-    const u64* tw_inv_s;
+    const ulonglong2* tw_fwd;  // [r][N] (psi^brv(i), Shoup companion)
+    const ulonglong2* tw_inv;  // [r][N] (psi^-brv(i), Shoup companion)
     const int32_t* ram_slot;  // [k0][a] encrypted bit slot of RAM j, address bit i (-1: 0)
     const int32_t* perm;      // [s] pi_r
     const u64* h3;            // [tuple_bits] H3 rows
+    // Rotation tables in evaluation order: X^e evaluates to Psi^e[pos] =
+    // psi^((2 brv(pos) + 1) e); rot_tab[((j*2 + sign)*log_n + t)*N + pos] holds
+    // (Psi^(+-2^t) - 1, Shoup) with sign 0 for +2^t and 1 for -2^t, and
+    // rot_inv the same for (Psi^(+-2^t) - 1)^-1.
+    const ulonglong2* rot_tab;
+    const ulonglong2* rot_inv;
+    int diag;  // one digit per prime: the digit of prime i at prime i is the residue
     size_t rlwe_words, rgsw_words, lwe_words, sample_words, model_words;
 };
-
-// ---------------------------------------------------------------------------
-// Block-level negacyclic NTT over N = 2^log_n residues in shared memory,
-// blockDim.x = N/8 threads, each handling 8 elements per round.
-//
-// Forward: Cooley-Tukey with the psi powers merged into the butterflies
-// (stage with m groups uses psi^brv(m+i)); natural order in, bit-reversed
-// order out.  Inverse: Gentleman-Sande with psi^-brv, bit-reversed in,
-// natural out, scaled by N^-1.  A round performs R (1..3) consecutive stages
-// on register-resident groups of 2^R elements, so shared memory is touched
-// once per R stages.  Values stay fully reduced in [0, q).
-// ---------------------------------------------------------------------------
-template <int R>
-__device__ __forceinline__ void ntt_fwd_round(u64* a, int log_n, int st0, const u64* __restrict__ tw,
-                                              const u64* __restrict__ tws, u64 q) {
-    constexpr int E = 1 << R;
-    constexpr int G = 8 >> R;
-    const int T = blockDim.x;
-    const int b_hi = log_n - 1 - st0;
-    const int b_lo = b_hi - (R - 1);
-#pragma unroll
-    for (int gg = 0; gg < G; gg++) {
-        int g = threadIdx.x + gg * T;
-        int lo = g & ((1 << b_lo) - 1);
-        int hi = g >> b_lo;
-        int base = (hi << (b_hi + 1)) | lo;
-        u64 x[E];
-#pragma unroll
-        for (int e = 0; e < E; e++) x[e] = a[base + (e << b_lo)];
-#pragma unroll
-        for (int s = 0; s < R; s++) {
-            const int lb = R - 1 - s;
-#pragma unroll
-            for (int e = 0; e < E; e++) {
-                if (e & (1 << lb)) continue;
-                int ti = (1 << (st0 + s)) + ((hi << s) | (e >> (lb + 1)));
-                u64 W = tw[ti], Ws = tws[ti];
-                u64 U = x[e];
-                u64 V = shoup_mul(x[e | (1 << lb)], W, Ws, q);
-                x[e] = add_mod(U, V, q);
-                x[e | (1 << lb)] = sub_mod(U, V, q);
-            }
-        }
-#pragma unroll
-        for (int e = 0; e < E; e++) a[base + (e << b_lo)] = x[e];
-    }
-}
-
-template <int R>
-__device__ __forceinline__ void ntt_inv_round(u64* a, int log_n, int p0, const u64* __restrict__ tw,
-                                              const u64* __restrict__ tws, u64 q, bool scale,
-                                              u64 ninv, u64 ninv_s) {
-    constexpr int E = 1 << R;
-    constexpr int G = 8 >> R;
-    const int T = blockDim.x;
-#pragma unroll
-    for (int gg = 0; gg < G; gg++) {
-        int g = threadIdx.x + gg * T;
-        int lo = g & ((1 << p0) - 1);
-        int hi = g >> p0;
-        int base = (hi << (p0 + R)) | lo;
-        u64 x[E];
-#pragma unroll
-        for (int e = 0; e < E; e++) x[e] = a[base + (e << p0)];
-#pragma unroll
-        for (int s = 0; s < R; s++) {
-            const int p = p0 + s;
-            const int h = 1 << (log_n - 1 - p);
-#pragma unroll
-            for (int e = 0; e < E; e++) {
-                if (e & (1 << s)) continue;
-                int ti = h + ((hi << (R - 1 - s)) | (e >> (s + 1)));
-                u64 W = tw[ti], Ws = tws[ti];
-                u64 U = x[e], V = x[e | (1 << s)];
-                x[e] = add_mod(U, V, q);
-                x[e | (1 << s)] = shoup_mul(sub_mod(U, V, q), W, Ws, q);
-            }
-        }
-        if (scale) {
-#pragma unroll
-            for (int e = 0; e < E; e++) x[e] = shoup_mul(x[e], ninv, ninv_s, q);
-        }
-#pragma unroll
-        for (int e = 0; e < E; e++) a[base + (e << p0)] = x[e];
-    }
-}
-
-// Forward transform of a[0..N) at prime j.  Caller has synchronised the
-// block after writing a; the function returns synchronised.
-__device__ __forceinline__ void ntt_forward_block(u64* a, const DevCtx& C, int j) {
-    const u64* tw = C.tw_fwd + (size_t)j * C.n;
-    const u64* tws = C.tw_fwd_s + (size_t)j * C.n;
-    const u64 q = C.P[j].q;
-    int st = 0;
-    while (st < C.log_n) {
-        int rem = C.log_n - st;
-        if (rem >= 3) {
-            ntt_fwd_round<3>(a, C.log_n, st, tw, tws, q);
-            st += 3;
-        } else if (rem == 2) {
-            ntt_fwd_round<2>(a, C.log_n, st, tw, tws, q);
-            st += 2;
-        } else {
-            ntt_fwd_round<1>(a, C.log_n, st, tw, tws, q);
-            st += 1;
-        }
-        __syncthreads();
-    }
-}
-
-__device__ __forceinline__ void ntt_inverse_block(u64* a, const DevCtx& C, int j) {
-    const u64* tw = C.tw_inv + (size_t)j * C.n;
-    const u64* tws = C.tw_inv_s + (size_t)j * C.n;
-    const u64 q = C.P[j].q;
-    int p = 0;
-    while (p < C.log_n) {
-        int rem = C.log_n - p;
-        int R = rem >= 3 ? 3 : rem;
-        bool last = (p + R == C.log_n);
-        if (R == 3)
-            ntt_inv_round<3>(a, C.log_n, p, tw, tws, q, last, C.n_inv[j], C.n_inv_s[j]);
-        else if (R == 2)
-            ntt_inv_round<2>(a, C.log_n, p, tw, tws, q, last, C.n_inv[j], C.n_inv_s[j]);
-        else
-            ntt_inv_round<1>(a, C.log_n, p, tw, tws, q, last, C.n_inv[j], C.n_inv_s[j]);
-        p += R;
-        __syncthreads();
-    }
-}
 
 // ---------------------------------------------------------------------------
 // Gadget digits (inverse of G in EncRGSW, Section 2.4; RNS reading): the
@@ -206,7 +83,274 @@ __device__ __forceinline__ u64 rot_read(const u64* p, int x, int e, int n, u64 q
     return neg ? neg_mod(v, q) : v;
 }
 
+
+// A digit |d| < q_j lifted to [0, q_j).
+__device__ __forceinline__ u64 lift_small(int64_t d, u64 q) { return d >= 0 ? (u64)d : (u64)(d + (int64_t)q); }
+
+// Montgomery reduction without the final subtraction: for T < q*2^64 the
+// result (T + ((T mod 2^64) q') mod 2^64 * q) / 2^64 lies in [0, 2q).
+__device__ __forceinline__ u64 redc_lazy(u64 hi, u64 lo, u64 q, u64 qneg) {
+    return hi + __umul64hi(lo * qneg, q) + (lo != 0 ? 1 : 0);
+}
+
+// ---------------------------------------------------------------------------
+// Block-level negacyclic NTT, specialised on the ring size N = 2^LOGN
+// (6 <= LOGN <= 13).  A block of T = N/16 threads holds 16 residues per
+// thread in registers; a round applies up to four consecutive butterfly
+// stages to groups of 2^R residues in registers, and rounds exchange data
+// through one of two padded shared-memory buffers (address p + p/16 keeps
+// every exchange at two wavefronts per warp).
+//
+// Forward (Cooley-Tukey, psi powers merged, natural order in, bit-reversed
+// out): the partial round of LOGN mod 4 stages comes first, then radix-16
+// rounds.  Butterflies are lazy (no reduction): X' = X + t, Y' = X + 2q - t
+// with t = Shoup(Y*W) in [0, 2q), so values grow by < 2q per stage and stay
+// below (2*LOGN + 1) q < 2^60.
+// Inverse (Gentleman-Sande, bit-reversed in, natural out, inputs < 2q):
+// radix-16 rounds first, the partial round last; the sum is kept below 2q
+// by one conditional subtraction, the difference goes through a lazy Shoup
+// product.  Scaling by N^-1 is applied by the caller to the inputs.
+//
+// Register convention: in a round of R stages, v[gg + e*G] (G = 16 / 2^R) is
+// element e of the thread's group gg.  The first forward round reads and the
+// last inverse round writes positions tid + k*T (v[k]); the last forward
+// round leaves, and the first inverse round takes, positions 16*tid + e.
+// ---------------------------------------------------------------------------
+template <int LOGN, int LOGE = 4>
+struct Ring {
+    static constexpr int N = 1 << LOGN;
+    static constexpr int E = 1 << LOGE;         // residues per thread and polynomial
+    static constexpr int T = N / E;             // threads per block
+    static constexpr int RP = LOGN % LOGE;      // size of the partial round
+    static constexpr int PADDED = N + N / E;    // words per exchange buffer
+};
+
+// Padded shared-memory address: one spare word every E words keeps the
+// stride-E accesses of the last forward / first inverse round conflict-free.
+template <int LOGE>
+__device__ __forceinline__ int padw(int p) { return p + (p >> LOGE); }
+
+template <int LOGN, int LOGE, int ST0>
+struct FwdR {
+    static constexpr int R = (ST0 == 0 && Ring<LOGN, LOGE>::RP) ? Ring<LOGN, LOGE>::RP : LOGE;
+};
+template <int LOGN, int LOGE, int P0>
+struct InvR {
+    static constexpr int R = (LOGN - P0) < LOGE ? (LOGN - P0) : LOGE;
+};
+
+// position of element e of group gg in the forward round (ST0, R)
+template <int LOGN, int LOGE, int ST0, int R>
+__device__ __forceinline__ int fpos(int gg, int e) {
+    constexpr int B_HI = LOGN - 1 - ST0, B_LO = B_HI - R + 1;
+    const int g = threadIdx.x + gg * Ring<LOGN, LOGE>::T;
+    const int lo = g & ((1 << B_LO) - 1), hi = g >> B_LO;
+    return (hi << (B_HI + 1)) | lo | (e << B_LO);
+}
+
+// position of element e of group gg in the inverse round (P0, R)
+template <int LOGN, int LOGE, int P0, int R>
+__device__ __forceinline__ int ipos(int gg, int e) {
+    const int g = threadIdx.x + gg * Ring<LOGN, LOGE>::T;
+    const int lo = g & ((1 << P0) - 1), hi = g >> P0;
+    return (hi << (P0 + R)) | lo | (e << P0);
+}
+
+// A round on NP polynomials of the same prime: the twiddles of one group
+// for all stages are loaded before any butterfly and serve every polynomial.
+template <int LOGN, int LOGE, int NP, int ST0, int R>
+__device__ __forceinline__ void fwd_round(u64 (&v)[NP][1 << LOGE], const ulonglong2* __restrict__ tw,
+                                          u64 q, u64 q2) {
+    constexpr int E = 1 << R, G = (1 << LOGE) / E, B_LO = LOGN - ST0 - R;
+#pragma unroll
+    for (int gg = 0; gg < G; gg++) {
+        const int hi = (threadIdx.x + gg * Ring<LOGN, LOGE>::T) >> B_LO;
+        ulonglong2 W[E - 1];  // stage s, index j < 2^s at W[2^s - 1 + j]
+#pragma unroll
+        for (int s = 0; s < R; s++)
+#pragma unroll
+            for (int jj = 0; jj < (1 << s); jj++)
+                W[(1 << s) - 1 + jj] = __ldg(tw + (1 << (ST0 + s)) + ((hi << s) | jj));
+#pragma unroll
+        for (int s = 0; s < R; s++) {
+            const int lb = R - 1 - s;
+#pragma unroll
+            for (int e = 0; e < E; e++) {
+                if (e & (1 << lb)) continue;
+                const ulonglong2 w = W[(1 << s) - 1 + (e >> (lb + 1))];
+#pragma unroll
+                for (int pp = 0; pp < NP; pp++) {
+                    u64& X = v[pp][gg + e * G];
+                    u64& Y = v[pp][gg + (e | (1 << lb)) * G];
+                    const u64 t = shoup_mul_lazy(Y, w.x, w.y, q);
+                    Y = X + q2 - t;
+                    X = X + t;
+                }
+            }
+        }
+    }
+}
+
+template <int LOGN, int LOGE, int NP, int P0, int R>
+__device__ __forceinline__ void inv_round(u64 (&v)[NP][1 << LOGE], const ulonglong2* __restrict__ tw,
+                                          u64 q, u64 q2) {
+    constexpr int E = 1 << R, G = (1 << LOGE) / E;
+#pragma unroll
+    for (int gg = 0; gg < G; gg++) {
+        const int hi = (threadIdx.x + gg * Ring<LOGN, LOGE>::T) >> P0;
+        ulonglong2 W[E - 1];  // stage s, index j < 2^(R-1-s) at W[2^(R-1-s) - 1 + j]
+#pragma unroll
+        for (int s = 0; s < R; s++) {
+            const int h = 1 << (LOGN - 1 - (P0 + s));
+#pragma unroll
+            for (int jj = 0; jj < (1 << (R - 1 - s)); jj++)
+                W[(1 << (R - 1 - s)) - 1 + jj] = __ldg(tw + h + ((hi << (R - 1 - s)) | jj));
+        }
+#pragma unroll
+        for (int s = 0; s < R; s++) {
+#pragma unroll
+            for (int e = 0; e < E; e++) {
+                if (e & (1 << s)) continue;
+                const ulonglong2 w = W[(1 << (R - 1 - s)) - 1 + (e >> (s + 1))];
+#pragma unroll
+                for (int pp = 0; pp < NP; pp++) {
+                    u64& U = v[pp][gg + e * G];
+                    u64& V = v[pp][gg + (e | (1 << s)) * G];
+                    u64 sum = U + V;
+                    sum = sum >= q2 ? sum - q2 : sum;
+                    V = shoup_mul_lazy(U + q2 - V, w.x, w.y, q);
+                    U = sum;
+                }
+            }
+        }
+    }
+}
+
+// Exchange buffers: two sets, alternated between exchanges (par) so that
+// one barrier per exchange suffices -- a set is rewritten only two exchanges
+// after it was read, with a barrier in between.  Each set holds NP padded
+// polynomials (stride `stride` words).
+struct Xchg {
+    u64* b0;
+    u64* b1;
+    int stride;
+    int par;
+    __device__ __forceinline__ u64* next() {
+        u64* p = par ? b1 : b0;
+        par ^= 1;
+        return p;
+    }
+};
+
+template <int LOGN, int LOGE, int NP, int ST0>
+__device__ __forceinline__ void fwd_from(u64 (&v)[NP][1 << LOGE], Xchg& xc,
+                                         const ulonglong2* __restrict__ tw, u64 q, u64 q2) {
+    constexpr int R = FwdR<LOGN, LOGE, ST0>::R, G = (1 << LOGE) >> R;
+    fwd_round<LOGN, LOGE, NP, ST0, R>(v, tw, q, q2);
+    if constexpr (ST0 + R < LOGN) {
+        constexpr int R2 = FwdR<LOGN, LOGE, ST0 + R>::R, G2 = (1 << LOGE) >> R2;
+        u64* sm = xc.next();
+#pragma unroll
+        for (int pp = 0; pp < NP; pp++)
+#pragma unroll
+            for (int gg = 0; gg < G; gg++)
+#pragma unroll
+                for (int e = 0; e < (1 << R); e++)
+                    sm[pp * xc.stride + padw<LOGE>(fpos<LOGN, LOGE, ST0, R>(gg, e))] = v[pp][gg + e * G];
+        __syncthreads();
+#pragma unroll
+        for (int pp = 0; pp < NP; pp++)
+#pragma unroll
+            for (int gg = 0; gg < G2; gg++)
+#pragma unroll
+                for (int e = 0; e < (1 << R2); e++)
+                    v[pp][gg + e * G2] = sm[pp * xc.stride + padw<LOGE>(fpos<LOGN, LOGE, ST0 + R, R2>(gg, e))];
+        fwd_from<LOGN, LOGE, NP, ST0 + R>(v, xc, tw, q, q2);
+    }
+}
+
+template <int LOGN, int LOGE, int NP, int P0>
+__device__ __forceinline__ void inv_from(u64 (&v)[NP][1 << LOGE], Xchg& xc,
+                                         const ulonglong2* __restrict__ tw, u64 q, u64 q2) {
+    constexpr int R = InvR<LOGN, LOGE, P0>::R, G = (1 << LOGE) >> R;
+    inv_round<LOGN, LOGE, NP, P0, R>(v, tw, q, q2);
+    if constexpr (P0 + R < LOGN) {
+        constexpr int R2 = InvR<LOGN, LOGE, P0 + R>::R, G2 = (1 << LOGE) >> R2;
+        u64* sm = xc.next();
+#pragma unroll
+        for (int pp = 0; pp < NP; pp++)
+#pragma unroll
+            for (int gg = 0; gg < G; gg++)
+#pragma unroll
+                for (int e = 0; e < (1 << R); e++)
+                    sm[pp * xc.stride + padw<LOGE>(ipos<LOGN, LOGE, P0, R>(gg, e))] = v[pp][gg + e * G];
+        __syncthreads();
+#pragma unroll
+        for (int pp = 0; pp < NP; pp++)
+#pragma unroll
+            for (int gg = 0; gg < G2; gg++)
+#pragma unroll
+                for (int e = 0; e < (1 << R2); e++)
+                    v[pp][gg + e * G2] = sm[pp * xc.stride + padw<LOGE>(ipos<LOGN, LOGE, P0 + R, R2>(gg, e))];
+        inv_from<LOGN, LOGE, NP, P0 + R>(v, xc, tw, q, q2);
+    }
+}
+
+// Forward transform at prime j of NP polynomials held as v[p][k] (position
+// tid + k*T, values < q); on return v[p][e] is the lazy value
+// (< (2 LOGN + 1) q) at evaluation position E*tid + e.
+template <int LOGN, int LOGE, int NP>
+__device__ __forceinline__ void ntt_fwd(u64 (&v)[NP][1 << LOGE], Xchg& xc, const DevCtx& C, int j) {
+    const u64 q = C.P[j].q;
+    fwd_from<LOGN, LOGE, NP, 0>(v, xc, C.tw_fwd + (size_t)j * Ring<LOGN>::N, q, 2 * q);
+}
+
+// Inverse transform at prime j of v[p][e] (position E*tid + e, values < 2q,
+// already multiplied by N^-1); on return v[p][k] (position tid + k*T) < 2q.
+template <int LOGN, int LOGE, int NP>
+__device__ __forceinline__ void ntt_inv(u64 (&v)[NP][1 << LOGE], Xchg& xc, const DevCtx& C, int j) {
+    const u64 q = C.P[j].q;
+    inv_from<LOGN, LOGE, NP, 0>(v, xc, C.tw_inv + (size_t)j * Ring<LOGN>::N, q, 2 * q);
+}
+
+// Single-polynomial forms with 16 residues per thread (utility kernels).
+template <int LOGN>
+__device__ __forceinline__ void ntt_fwd1(u64 (&v)[16], Xchg& xc, const DevCtx& C, int j) {
+    ntt_fwd<LOGN, 4, 1>(reinterpret_cast<u64(&)[1][16]>(v), xc, C, j);
+}
+template <int LOGN>
+__device__ __forceinline__ void ntt_inv1(u64 (&v)[16], Xchg& xc, const DevCtx& C, int j) {
+    ntt_inv<LOGN, 4, 1>(reinterpret_cast<u64(&)[1][16]>(v), xc, C, j);
+}
+
+// x mod q for any 64-bit x (Barrett, quotient short by at most 2).
+__device__ __forceinline__ u64 reduce_full(u64 x, const PrimeConst& P) { return reduce64(x, P); }
+
+// Ask L2 to fetch [p, p + words) (one request per 128-byte line, spread over
+// the block).  A hint only: it changes no value.
+__device__ __forceinline__ void prefetch_l2(const u64* p, size_t words) {
+    const char* b = (const char*)p;
+    const size_t bytes = words * sizeof(u64);
+    for (size_t off = (size_t)threadIdx.x * 128; off < bytes; off += (size_t)blockDim.x * 128)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(b + off));
+}
+
 enum ExtOut { EXT_ADD = 0, EXT_PLAIN = 1, EXT_LWE = 2 };
+
+// Evaluation-form companions of an external product.
+//   src_ntt  evaluation form of srcA (fully reduced), or null
+//   dst_ntt  where to write the evaluation form of the output, or null
+//   rot_t    >= 0: the product is a blind-rotation CMUX, srcA == srcB and
+//            D = src X^(eB + s 2^rot_t) - src X^eB with s = +1 (rot_sign 0)
+//            or -1 (rot_sign 1); -1 otherwise
+struct ExtNtt {
+    const u64* src_ntt;
+    u64* dst_ntt;
+    int rot_t;
+    int rot_sign;
+    const u64* next_rgsw;  // RGSW of the next external product (L2 prefetch), or null
+    int prefetch_cur;      // also prefetch this product's RGSW
+};
 
 // The external product C [x] D for one RLWE, computed by one thread block.
 //
@@ -215,80 +359,217 @@ enum ExtOut { EXT_ADD = 0, EXT_PLAIN = 1, EXT_LWE = 2 };
 //       = C [x] D                        (EXT_PLAIN)
 //       = ExtractLWE(srcB * X^eB + C [x] D, 0)   (EXT_LWE, dst is an LWE)
 //
-// C [x] D = sum_rho Dec(D.b)_rho * row_rho + Dec(D.a)_rho * row_{dnum+rho}:
-// for each target prime j every digit polynomial is lifted to q_j, moved to
-// evaluation form in shared memory, multiplied into the two accumulators
-// with the RGSW rows (Montgomery form), and the accumulators are brought back
-// with the inverse transform.  dst must not alias srcA or srcB (all primes of
-// the sources are read while prime j is written).  smem: 3N words.
-static __device__ __noinline__ void ext_product_block(const DevCtx& C, const u64* __restrict__ rgsw,
-                                               const u64* srcA, int eA, const u64* srcB, int eB,
-                                               int mode, u64* dst, u64* smem) {
-    const int n = C.n, r = C.r, T = blockDim.x, tid = threadIdx.x;
-    u64* buf = smem;
-    u64* outA = smem + n;
-    u64* outB = smem + 2 * n;
+// C [x] D = sum_rho Dec(D.b)_rho * row_rho + Dec(D.a)_rho * row_{dnum+rho}.
+// For each target prime j, digit polynomials are built in registers at the
+// first-round positions and transformed NP at a time; the last round's
+// registers are multiplied into per-thread accumulators (RGSW rows are in
+// Montgomery form: one lazy REDC per product).  The accumulators are scaled
+// by N^-1, transformed back, and combined with the base at the natural
+// positions the last inverse round leaves.  dst must not alias the sources.
+//
+// With one digit per prime (C.diag), the digit of prime j lifted to q_j is
+// the residue D_j itself, so its transform is the evaluation form of the
+// source times (Psi^(+-2^t) - 1) for a rotation CMUX, or the evaluation form
+// itself for a CDEMUX: those 2 of the 2r digit transforms per target prime
+// are skipped when nt.src_ntt is given.  When it is not, a rotation CMUX
+// recovers the evaluation form of its base from the diagonal digit's
+// transform (times (Psi^(+-2^t) - 1)^-1) so that dst_ntt can still be written.
+template <int LOGN, int LOGE, int NP>
+__device__ __noinline__ void ext_product(const DevCtx& C, const u64* __restrict__ rgsw,
+                                         const u64* srcA, int eA, const u64* srcB, int eB, int mode,
+                                         u64* dst, Xchg& xc, ExtNtt nt) {
+    constexpr int N = Ring<LOGN, LOGE>::N, T = Ring<LOGN, LOGE>::T, E = 1 << LOGE;
+    const int tid = threadIdx.x, r = C.r;
+    const bool cmux_rot = nt.rot_t >= 0;
+    const bool diag_in = C.diag && nt.src_ntt &&
+                         ((cmux_rot && eB == 0) || (!cmux_rot && srcB == nullptr && eA == 0));
+    const bool derive_base = C.diag && !diag_in && cmux_rot && nt.dst_ntt && mode == EXT_ADD;
+    // the output's evaluation form is written only when its base's is known:
+    // no base (EXT_PLAIN), the source's own (unrotated CMUX base), or derived
+    const bool base_given = mode == EXT_ADD && nt.src_ntt != nullptr && srcB == srcA && eB == 0;
+    const bool write_ntt =
+        C.diag && nt.dst_ntt != nullptr && (mode == EXT_PLAIN || base_given || derive_base);
+    // digits that need a forward transform at target prime j
+    const int ndig = diag_in ? 2 * (r - 1) : 2 * C.dnum;
+    // stream this product's RGSW and the next one's into L2 ahead of the MACs
+    if (nt.prefetch_cur) prefetch_l2(rgsw, C.rgsw_words);
+    if (nt.next_rgsw) prefetch_l2(nt.next_rgsw, C.rgsw_words);
+    __syncthreads();  // exchange buffers are free
     for (int j = 0; j < r; j++) {
         const PrimeConst Pj = C.P[j];
         const u64 qj = Pj.q;
-        for (int x = tid; x < n; x += T) {
-            outA[x] = 0;
-            outB[x] = 0;
+        const ulonglong2* rtab =
+            cmux_rot ? C.rot_tab + (((size_t)j * 2 + nt.rot_sign) * C.log_n + nt.rot_t) * N + E * tid
+                     : nullptr;
+        u64 acc[2][E];
+#pragma unroll
+        for (int e = 0; e < E; e++) acc[0][e] = acc[1][e] = 0;
+        if (diag_in) {
+            // the two diagonal digits, straight from the evaluation form
+#pragma unroll
+            for (int comp = 0; comp < 2; comp++) {
+                const int row = comp == 1 ? j : C.dnum + j;
+                const u64* sn = nt.src_ntt + ((size_t)comp * r + j) * N + E * tid;
+                const ulonglong2* Ra =
+                    (const ulonglong2*)(rgsw + ((size_t)(row * 2 + 0) * r + j) * N + E * tid);
+                const ulonglong2* Rb =
+                    (const ulonglong2*)(rgsw + ((size_t)(row * 2 + 1) * r + j) * N + E * tid);
+#pragma unroll
+                for (int h = 0; h < E / 2; h++) {
+                    const ulonglong2 ra = __ldg(Ra + h), rb = __ldg(Rb + h);
+                    u64 x0 = sn[2 * h], x1 = sn[2 * h + 1];
+                    if (cmux_rot) {
+                        const ulonglong2 t0 = __ldg(rtab + 2 * h), t1 = __ldg(rtab + 2 * h + 1);
+                        x0 = shoup_mul_lazy(x0, t0.x, t0.y, qj);
+                        x1 = shoup_mul_lazy(x1, t1.x, t1.y, qj);
+                    }
+                    acc[0][2 * h] += redc_lazy(__umul64hi(x0, ra.x), x0 * ra.x, qj, Pj.qneg);
+                    acc[0][2 * h + 1] += redc_lazy(__umul64hi(x1, ra.y), x1 * ra.y, qj, Pj.qneg);
+                    acc[1][2 * h] += redc_lazy(__umul64hi(x0, rb.x), x0 * rb.x, qj, Pj.qneg);
+                    acc[1][2 * h + 1] += redc_lazy(__umul64hi(x1, rb.y), x1 * rb.y, qj, Pj.qneg);
+                }
+            }
         }
-        for (int comp = 0; comp < 2; comp++) {
-            for (int rho = 0; rho < C.dnum; rho++) {
+        for (int u0 = 0; u0 < ndig; u0 += NP) {
+            u64 v[NP][E];
+            int comps[NP], rhos[NP];
+#pragma unroll
+            for (int pp = 0; pp < NP; pp++) {
+                const int u = u0 + pp;
+                int comp, rho;
+                if (diag_in) {  // skip source prime j
+                    comp = u / (r - 1);
+                    const int ii = u % (r - 1);
+                    rho = ii < j ? ii : ii + 1;
+                } else {
+                    comp = u / C.dnum;
+                    rho = u % C.dnum;
+                }
+                comps[pp] = comp;
+                rhos[pp] = rho;
                 const int i = rho / C.dpp, k = rho % C.dpp;
                 const u64 qi = C.P[i].q;
-                const u64* pa = srcA + ((size_t)comp * r + i) * n;
-                const u64* pb = srcB ? srcB + ((size_t)comp * r + i) * n : nullptr;
-                __syncthreads();  // buf is free
-                for (int x = tid; x < n; x += T) {
-                    u64 v = rot_read(pa, x, eA, n, qi);
-                    if (pb) v = sub_mod(v, rot_read(pb, x, eB, n, qi), qi);
-                    int64_t d = gadget_digit(centre(v, qi), k, C.dpp, C.log_beta);
-                    buf[x] = from_signed(d, qj);
+                const u64* pa = srcA + ((size_t)comp * r + i) * N;
+                const u64* pb = srcB ? srcB + ((size_t)comp * r + i) * N : nullptr;
+#pragma unroll
+                for (int kk = 0; kk < E; kk++) {
+                    const int x = tid + kk * T;
+                    u64 val = rot_read(pa, x, eA, N, qi);
+                    if (pb) val = sub_mod(val, rot_read(pb, x, eB, N, qi), qi);
+                    v[pp][kk] = lift_small(gadget_digit(centre(val, qi), k, C.dpp, C.log_beta), qj);
                 }
-                __syncthreads();
-                ntt_forward_block(buf, C, j);
+            }
+            ntt_fwd<LOGN, LOGE, NP>(v, xc, C, j);
+#pragma unroll
+            for (int pp = 0; pp < NP; pp++) {
+                const int comp = comps[pp], rho = rhos[pp];
                 const int row = comp == 1 ? rho : C.dnum + rho;
-                const u64* Ra = rgsw + ((size_t)(row * 2 + 0) * r + j) * n;
-                const u64* Rb = rgsw + ((size_t)(row * 2 + 1) * r + j) * n;
-                for (int x = tid; x < n; x += T) {
-                    u64 d = buf[x];
-                    outA[x] = add_mod(outA[x], mont_mul(d, __ldg(Ra + x), Pj), qj);
-                    outB[x] = add_mod(outB[x], mont_mul(d, __ldg(Rb + x), Pj), qj);
+                const ulonglong2* Ra =
+                    (const ulonglong2*)(rgsw + ((size_t)(row * 2 + 0) * r + j) * N + E * tid);
+                const ulonglong2* Rb =
+                    (const ulonglong2*)(rgsw + ((size_t)(row * 2 + 1) * r + j) * N + E * tid);
+#pragma unroll
+                for (int h = 0; h < E / 2; h++) {
+                    const ulonglong2 ra = __ldg(Ra + h), rb = __ldg(Rb + h);
+                    const u64 x0 = v[pp][2 * h], x1 = v[pp][2 * h + 1];
+                    acc[0][2 * h] += redc_lazy(__umul64hi(x0, ra.x), x0 * ra.x, qj, Pj.qneg);
+                    acc[0][2 * h + 1] += redc_lazy(__umul64hi(x1, ra.y), x1 * ra.y, qj, Pj.qneg);
+                    acc[1][2 * h] += redc_lazy(__umul64hi(x0, rb.x), x0 * rb.x, qj, Pj.qneg);
+                    acc[1][2 * h + 1] += redc_lazy(__umul64hi(x1, rb.y), x1 * rb.y, qj, Pj.qneg);
+                }
+                if (derive_base && rho == j) {
+                    // the base's evaluation form: D_j / (Psi^(+-2^t) - 1)
+                    const ulonglong2* ri =
+                        C.rot_inv + (((size_t)j * 2 + nt.rot_sign) * C.log_n + nt.rot_t) * N + E * tid;
+                    u64* bn = nt.dst_ntt + ((size_t)comp * r + j) * N + E * tid;
+#pragma unroll
+                    for (int e = 0; e < E; e++) {
+                        const ulonglong2 w = __ldg(ri + e);
+                        bn[e] = shoup_mul_lazy(v[pp][e], w.x, w.y, qj);
+                    }
                 }
             }
         }
-        __syncthreads();
-        ntt_inverse_block(outA, C, j);
-        ntt_inverse_block(outB, C, j);
-        const u64* ba = srcB ? srcB + ((size_t)0 * r + j) * n : nullptr;
-        const u64* bb = srcB ? srcB + ((size_t)1 * r + j) * n : nullptr;
-        if (mode == EXT_LWE) {
-            u64* lw = dst + (size_t)j * (n + 1);
-            for (int y = tid; y < n; y += T) {
-                u64 va = add_mod(outA[y], rot_read(ba, y, eB, n, qj), qj);
-                // a'_0 = a_0, a'_x = -a_{N-x}
-                if (y == 0)
-                    lw[0] = va;
-                else
-                    lw[n - y] = neg_mod(va, qj);
-            }
-            if (tid == 0) lw[n] = add_mod(outB[0], rot_read(bb, 0, eB, n, qj), qj);
-        } else {
-            u64* da = dst + ((size_t)0 * r + j) * n;
-            u64* db = dst + ((size_t)1 * r + j) * n;
-            for (int x = tid; x < n; x += T) {
-                u64 va = outA[x], vb = outB[x];
-                if (mode == EXT_ADD) {
-                    va = add_mod(va, rot_read(ba, x, eB, n, qj), qj);
-                    vb = add_mod(vb, rot_read(bb, x, eB, n, qj), qj);
+        if (write_ntt) {
+            // evaluation form of the output: (base +) C [x] D, fully reduced
+#pragma unroll
+            for (int oc = 0; oc < 2; oc++) {
+                u64* dn = nt.dst_ntt + ((size_t)oc * r + j) * N + E * tid;
+                const u64* bn = derive_base ? dn
+                                : (base_given ? nt.src_ntt + ((size_t)oc * r + j) * N + E * tid
+                                              : nullptr);
+#pragma unroll
+                for (int e = 0; e < E; e++) {
+                    u64 val = acc[oc][e] + (bn ? bn[e] : 0);
+                    dn[e] = reduce64(val, Pj);
                 }
-                da[x] = va;
-                db[x] = vb;
             }
         }
-        __syncthreads();
+        const u64 ninv = C.n_inv[j], ninv_s = C.n_inv_s[j];
+        constexpr int NPI = NP < 2 ? NP : 2;  // the two output components
+        for (int oc0 = 0; oc0 < 2; oc0 += NPI) {
+            u64 v[NPI][E];
+#pragma unroll
+            for (int pp = 0; pp < NPI; pp++)
+#pragma unroll
+                for (int e = 0; e < E; e++) v[pp][e] = shoup_mul_lazy(acc[oc0 + pp][e], ninv, ninv_s, qj);
+            ntt_inv<LOGN, LOGE, NPI>(v, xc, C, j);
+#pragma unroll
+            for (int pp = 0; pp < NPI; pp++) {
+                const int oc = oc0 + pp;
+                const u64* base = srcB ? srcB + ((size_t)oc * r + j) * N : nullptr;
+                if (mode == EXT_LWE) {
+                    u64* lw = dst + (size_t)j * (N + 1);
+                    if (oc == 0) {
+#pragma unroll
+                        for (int kk = 0; kk < E; kk++) {
+                            const int x = tid + kk * T;
+                            u64 val = v[pp][kk] >= qj ? v[pp][kk] - qj : v[pp][kk];
+                            val = add_mod(val, rot_read(base, x, eB, N, qj), qj);
+                            if (x == 0)
+                                lw[0] = val;
+                            else
+                                lw[N - x] = neg_mod(val, qj);
+                        }
+                    } else if (tid == 0) {
+                        u64 val = v[pp][0] >= qj ? v[pp][0] - qj : v[pp][0];
+                        lw[N] = add_mod(val, rot_read(base, 0, eB, N, qj), qj);
+                    }
+                } else {
+                    u64* dd = dst + ((size_t)oc * r + j) * N;
+#pragma unroll
+                    for (int kk = 0; kk < E; kk++) {
+                        const int x = tid + kk * T;
+                        u64 val = v[pp][kk] >= qj ? v[pp][kk] - qj : v[pp][kk];
+                        if (mode == EXT_ADD) val = add_mod(val, rot_read(base, x, eB, N, qj), qj);
+                        dd[x] = val;
+                    }
+                }
+            }
+        }
     }
+    __syncthreads();  // dst complete for the whole block
 }
+
+// Launch geometry of the external-product kernels: 8 residues per thread
+// with two polynomials per transform below N = 8192; 16 residues per thread,
+// one polynomial at N = 8192 (1024-thread blocks would leave 64 registers).
+template <int LOGN>
+struct ExtCfg {
+    static constexpr int LOGE = LOGN >= 13 ? 4 : 3;
+    static constexpr int NP = LOGN >= 13 ? 1 : 2;
+    static constexpr int T = Ring<LOGN, LOGE>::T;
+    static constexpr int MINB = (512 / T) > 16 ? 16 : ((512 / T) < 1 ? 1 : (512 / T));
+    static constexpr int PADDED = Ring<LOGN, LOGE>::PADDED;
+    static constexpr size_t XCHG_BYTES = 2 * (size_t)NP * PADDED * sizeof(u64);
+};
+
+// Launch geometry shared by the kernels that run block NTTs.
+template <int LOGN>
+struct Geo {
+    static constexpr int T = Ring<LOGN>::T;
+    static constexpr size_t XCHG_BYTES = 2 * (size_t)Ring<LOGN>::PADDED * sizeof(u64);
+    static constexpr int MINB = (512 / T) > 16 ? 16 : (512 / T);
+};
+
+#define HW_FOR_EACH_LOGN(X) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13)

@@ -20,21 +20,29 @@ __device__ __forceinline__ int gaussian_from_word(u64 w) {
 // SecretKeyGen: ternary S_1; key = [r][N] residues, then [r][N] evaluation
 // form in Montgomery representation.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_keygen(const DevCtx* __restrict__ Cp, u64 seed, u64* __restrict__ key) {
+template <int LOGN>
+__global__ void __launch_bounds__(Geo<LOGN>::T) k_keygen(const DevCtx* __restrict__ Cp, u64 seed,
+                                                          u64* __restrict__ key) {
     extern __shared__ u64 smem[];
+    constexpr int N = Ring<LOGN>::N, T = Ring<LOGN>::T;
+    Xchg xc{smem, smem + Ring<LOGN>::PADDED, Ring<LOGN>::PADDED, 0};
     const DevCtx& C = *Cp;
-    const int j = blockIdx.x, n = C.n, T = blockDim.x;
+    const int j = blockIdx.x, tid = threadIdx.x;
     const PrimeConst P = C.P[j];
-    for (int k = threadIdx.x; k < n; k += T) {
-        Philox4 w = hw_draw(seed, HW_TAG_KEY, (u64)k >> 2, 0, 0);
-        u64 v = w.v[k & 3] % 3;
-        u64 res = v == 0 ? 0 : (v == 1 ? 1 : P.q - 1);
-        key[(size_t)j * n + k] = res;
-        smem[k] = res;
+    u64 v[16];
+#pragma unroll
+    for (int kk = 0; kk < 16; kk++) {
+        const int x = tid + kk * T;
+        Philox4 w = hw_draw(seed, HW_TAG_KEY, (u64)x >> 2, 0, 0);
+        u64 t = w.v[x & 3] % 3;
+        u64 res = t == 0 ? 0 : (t == 1 ? 1 : P.q - 1);
+        key[(size_t)j * N + x] = res;
+        v[kk] = res;
     }
-    __syncthreads();
-    ntt_forward_block(smem, C, j);
-    for (int k = threadIdx.x; k < n; k += T) key[(size_t)(C.r + j) * n + k] = to_mont(smem[k], P);
+    ntt_fwd1<LOGN>(v, xc, C, j);
+#pragma unroll
+    for (int e = 0; e < 16; e++)
+        key[(size_t)(C.r + j) * N + 16 * tid + e] = to_mont(reduce_full(v[e], P), P);
 }
 
 // ---------------------------------------------------------------------------
@@ -82,12 +90,19 @@ __global__ void k_encode(const DevCtx* __restrict__ Cp, const uint8_t* __restric
 // (two 64-bit words -> 128-bit value mod q), e is one integer polynomial for
 // all primes.  Rows are stored in evaluation form, Montgomery representation.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_encrypt(const DevCtx* __restrict__ Cp, const u64* __restrict__ key,
-                          const uint8_t* __restrict__ bits, const uint32_t* __restrict__ labels,
-                          int slot0, int n_enc_slots, u64 seed, u64 first, u64* __restrict__ out) {
+template <int LOGN>
+__global__ void __launch_bounds__(ExtCfg<LOGN>::T, ExtCfg<LOGN>::MINB)
+    k_encrypt(const DevCtx* __restrict__ Cp, const u64* __restrict__ key,
+              const uint8_t* __restrict__ bits, const uint32_t* __restrict__ labels, int slot0,
+              int n_enc_slots, u64 seed, u64 first, u64* __restrict__ out) {
+    using X = ExtCfg<LOGN>;
+    constexpr int N = Ring<LOGN>::N, E = 1 << X::LOGE, T = X::T;
     extern __shared__ u64 smem[];
+    Xchg xc{smem, smem + X::NP * X::PADDED, X::PADDED, 0};
+    u64* A = smem + 2 * X::NP * X::PADDED;
+    int8_t* ebuf = (int8_t*)(A + N);
     const DevCtx& C = *Cp;
-    const int n = C.n, r = C.r, T = blockDim.x, tid = threadIdx.x;
+    const int r = C.r, tid = threadIdx.x;
     const int rows = 2 * C.dnum;
     const size_t bid = blockIdx.x;
     const int row = (int)(bid % rows);
@@ -97,10 +112,7 @@ __global__ void __launch_bounds__(1024) k_encrypt(const DevCtx* __restrict__ Cp,
     const int bit = slot < C.L ? (int)((labels[i] >> slot) & 1u)
                                : (int)bits[i * C.n_data + (slot - C.L)];
     const u64 stream = (first + i) * (u64)C.n_slots + (u64)slot;
-    u64* A = smem;
-    u64* E = smem + n;
-    int8_t* ebuf = (int8_t*)(smem + 2 * n);
-    for (int c0 = tid; c0 < n / 4; c0 += T) {
+    for (int c0 = tid; c0 < N / 4; c0 += T) {
         Philox4 w = hw_draw(seed, HW_TAG_RGSW_E, (u64)c0, (u64)row, stream);
 #pragma unroll
         for (int t = 0; t < 4; t++) ebuf[4 * c0 + t] = (int8_t)gaussian_from_word(w.v[t]);
@@ -111,31 +123,43 @@ __global__ void __launch_bounds__(1024) k_encrypt(const DevCtx* __restrict__ Cp,
     for (int j = 0; j < r; j++) {
         const PrimeConst P = C.P[j];
         const u64 q = P.q;
-        __syncthreads();
-        for (int c0 = tid; c0 < n / 2; c0 += T) {
+        __syncthreads();  // A is free; ebuf is complete
+        for (int c0 = tid; c0 < N / 2; c0 += T) {
             Philox4 w = hw_draw(seed, HW_TAG_RGSW_A, (u64)c0, (u64)(row * r + j), stream);
             A[2 * c0] = reduce128(w.v[0], w.v[1], P);
             A[2 * c0 + 1] = reduce128(w.v[2], w.v[3], P);
         }
         __syncthreads();
-        for (int x = tid; x < n; x += T) E[x] = from_signed((int64_t)ebuf[x], q);
-        __syncthreads();
-        ntt_forward_block(A, C, j);
-        ntt_forward_block(E, C, j);
+        // a and e transformed together (X::NP == 2) or one after the other
+        u64 v[2][E];
+#pragma unroll
+        for (int kk = 0; kk < E; kk++) {
+            const int x = tid + kk * T;
+            v[0][kk] = A[x];
+            v[1][kk] = from_signed((int64_t)ebuf[x], q);
+        }
+        if constexpr (X::NP == 2) {
+            ntt_fwd<LOGN, X::LOGE, 2>(v, xc, C, j);
+        } else {
+            ntt_fwd<LOGN, X::LOGE, 1>(reinterpret_cast<u64(&)[1][E]>(v[0]), xc, C, j);
+            ntt_fwd<LOGN, X::LOGE, 1>(reinterpret_cast<u64(&)[1][E]>(v[1]), xc, C, j);
+        }
         const u64 g = (bit && j == gi) ? C.gconst[rho] : 0;
-        const u64* sM = key + (size_t)(r + j) * n;
-        u64* da = dst_row + (size_t)(0 * r + j) * n;
-        u64* db = dst_row + (size_t)(1 * r + j) * n;
-        for (int x = tid; x < n; x += T) {
-            u64 a = A[x];
-            u64 b = add_mod(mont_mul(a, sM[x], P), E[x], q);
+        const u64* sM = key + (size_t)(r + j) * N;
+        u64* da = dst_row + (size_t)(0 * r + j) * N;
+        u64* db = dst_row + (size_t)(1 * r + j) * N;
+#pragma unroll
+        for (int e = 0; e < E; e++) {
+            const int pos = E * tid + e;
+            u64 a = reduce_full(v[0][e], P);
+            u64 b = add_mod(mont_mul(a, sM[pos], P), reduce_full(v[1][e], P), q);
             // the evaluation form of the constant polynomial g is g everywhere
             if (row < C.dnum)
                 b = add_mod(b, g, q);
             else
                 a = add_mod(a, g, q);
-            da[x] = to_mont(a, P);
-            db[x] = to_mont(b, P);
+            da[pos] = to_mont(a, P);
+            db[pos] = to_mont(b, P);
         }
     }
 }
@@ -219,23 +243,35 @@ __device__ int64_t decode_residues(const DevCtx& C, const u64* phi) {
 }
 
 // One block per (RLWE, prime): phase b - a*s at that prime into ph[ct][prime][N].
-__global__ void __launch_bounds__(1024) k_rlwe_phase(const DevCtx* __restrict__ Cp, const u64* __restrict__ key,
-                             const u64* __restrict__ ct, u64* __restrict__ ph) {
+template <int LOGN>
+__global__ void __launch_bounds__(Geo<LOGN>::T)
+    k_rlwe_phase(const DevCtx* __restrict__ Cp, const u64* __restrict__ key,
+                 const u64* __restrict__ ct, u64* __restrict__ ph) {
     extern __shared__ u64 smem[];
+    constexpr int N = Ring<LOGN>::N, T = Ring<LOGN>::T;
+    Xchg xc{smem, smem + Ring<LOGN>::PADDED, Ring<LOGN>::PADDED, 0};
     const DevCtx& C = *Cp;
-    const int n = C.n, r = C.r, T = blockDim.x, tid = threadIdx.x;
+    const int r = C.r, tid = threadIdx.x;
     const size_t t = blockIdx.x / r;
     const int j = blockIdx.x % r;
     const PrimeConst P = C.P[j];
     const u64* c = ct + t * C.rlwe_words;
-    for (int x = tid; x < n; x += T) smem[x] = c[(size_t)j * n + x];
-    __syncthreads();
-    ntt_forward_block(smem, C, j);
-    for (int x = tid; x < n; x += T) smem[x] = mont_mul(smem[x], key[(size_t)(r + j) * n + x], P);
-    __syncthreads();
-    ntt_inverse_block(smem, C, j);
-    u64* dst = ph + (t * r + j) * n;
-    for (int x = tid; x < n; x += T) dst[x] = sub_mod(c[(size_t)(r + j) * n + x], smem[x], P.q);
+    u64 v[16];
+#pragma unroll
+    for (int kk = 0; kk < 16; kk++) v[kk] = c[(size_t)j * N + tid + kk * T];
+    ntt_fwd1<LOGN>(v, xc, C, j);
+#pragma unroll
+    for (int e = 0; e < 16; e++)
+        v[e] = shoup_mul_lazy(mont_mul(v[e], key[(size_t)(r + j) * N + 16 * tid + e], P), C.n_inv[j],
+                              C.n_inv_s[j], P.q);
+    ntt_inv1<LOGN>(v, xc, C, j);
+    u64* dst = ph + (t * r + j) * N;
+#pragma unroll
+    for (int kk = 0; kk < 16; kk++) {
+        const int x = tid + kk * T;
+        const u64 as = v[kk] >= P.q ? v[kk] - P.q : v[kk];
+        dst[x] = sub_mod(c[(size_t)(r + j) * N + x], as, P.q);
+    }
 }
 
 // One thread per coefficient: CRT + rounding of the phases.
@@ -334,34 +370,56 @@ __global__ void k_pdact(const DevCtx* __restrict__ Cp, const int64_t* __restrict
 // ---------------------------------------------------------------------------
 // Transform utilities.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_export_rgsw(const DevCtx* __restrict__ Cp, const u64* __restrict__ in,
-                              u64* __restrict__ out) {
+template <int LOGN>
+__global__ void __launch_bounds__(Geo<LOGN>::T)
+    k_export_rgsw(const DevCtx* __restrict__ Cp, const u64* __restrict__ in, u64* __restrict__ out) {
     extern __shared__ u64 smem[];
+    constexpr int N = Ring<LOGN>::N, T = Ring<LOGN>::T;
+    Xchg xc{smem, smem + Ring<LOGN>::PADDED, Ring<LOGN>::PADDED, 0};
     const DevCtx& C = *Cp;
-    const int n = C.n;
+    const int tid = threadIdx.x;
     const size_t poly = blockIdx.x;  // [rgsw][row][comp][prime]
     const int j = (int)(poly % C.r);
     const PrimeConst P = C.P[j];
-    for (int x = threadIdx.x; x < n; x += blockDim.x) smem[x] = from_mont(in[poly * n + x], P);
-    __syncthreads();
-    ntt_inverse_block(smem, C, j);
-    for (int x = threadIdx.x; x < n; x += blockDim.x) out[poly * n + x] = smem[x];
+    u64 v[16];
+#pragma unroll
+    for (int e = 0; e < 16; e++)
+        v[e] = shoup_mul_lazy(from_mont(in[poly * N + 16 * tid + e], P), C.n_inv[j], C.n_inv_s[j], P.q);
+    ntt_inv1<LOGN>(v, xc, C, j);
+#pragma unroll
+    for (int kk = 0; kk < 16; kk++) out[poly * N + tid + kk * T] = v[kk] >= P.q ? v[kk] - P.q : v[kk];
 }
 
-__global__ void __launch_bounds__(1024) k_ntt_batch(const DevCtx* __restrict__ Cp, u64* __restrict__ poly, int inverse) {
+// Batched transform in place: forward takes natural order and leaves the
+// evaluation order; inverse undoes it.  Values are fully reduced.
+template <int LOGN>
+__global__ void __launch_bounds__(Geo<LOGN>::T)
+    k_ntt_batch(const DevCtx* __restrict__ Cp, u64* __restrict__ poly, int inverse) {
     extern __shared__ u64 smem[];
+    constexpr int N = Ring<LOGN>::N, T = Ring<LOGN>::T;
+    Xchg xc{smem, smem + Ring<LOGN>::PADDED, Ring<LOGN>::PADDED, 0};
     const DevCtx& C = *Cp;
-    const int n = C.n;
+    const int tid = threadIdx.x;
     const size_t t = blockIdx.x;
     const int j = (int)(t % C.r);
-    u64* p = poly + t * n;
-    for (int x = threadIdx.x; x < n; x += blockDim.x) smem[x] = p[x];
-    __syncthreads();
-    if (inverse)
-        ntt_inverse_block(smem, C, j);
-    else
-        ntt_forward_block(smem, C, j);
-    for (int x = threadIdx.x; x < n; x += blockDim.x) p[x] = smem[x];
+    const PrimeConst P = C.P[j];
+    u64* p = poly + t * N;
+    u64 v[16];
+    // every read happens before the first exchange barrier, every write
+    // after the last one, so the transform can run in place
+    if (!inverse) {
+#pragma unroll
+        for (int kk = 0; kk < 16; kk++) v[kk] = p[tid + kk * T];
+        ntt_fwd1<LOGN>(v, xc, C, j);
+#pragma unroll
+        for (int e = 0; e < 16; e++) p[16 * tid + e] = reduce_full(v[e], P);
+    } else {
+#pragma unroll
+        for (int e = 0; e < 16; e++) v[e] = shoup_mul_lazy(p[16 * tid + e], C.n_inv[j], C.n_inv_s[j], P.q);
+        ntt_inv1<LOGN>(v, xc, C, j);
+#pragma unroll
+        for (int kk = 0; kk < 16; kk++) p[tid + kk * T] = v[kk] >= P.q ? v[kk] - P.q : v[kk];
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -369,8 +427,25 @@ __global__ void __launch_bounds__(1024) k_ntt_batch(const DevCtx* __restrict__ C
 // ---------------------------------------------------------------------------
 #define HW_LAUNCHED() ((*li.launches)++, cudaGetLastError())
 
+template <int LOGN>
+static size_t encrypt_smem() {
+    return ExtCfg<LOGN>::XCHG_BYTES + (size_t)Ring<LOGN>::N * 9;
+}
+
+#define HW_DISPATCH(logn, BODY)      \
+    switch (logn) {                  \
+        BODY(6) BODY(7) BODY(8) BODY(9) BODY(10) BODY(11) BODY(12) BODY(13) \
+        default:                     \
+            return cudaErrorInvalidValue; \
+    }
+
 cudaError_t launch_keygen(const LaunchInfo& li, uint64_t seed, uint64_t* key, cudaStream_t st) {
-    k_keygen<<<li.r, li.n / 8, (size_t)li.n * 8, st>>>(li.dctx, seed, key);
+#define B(L)                                                                    \
+    case L:                                                                     \
+        k_keygen<L><<<li.r, Geo<L>::T, Geo<L>::XCHG_BYTES, st>>>(li.dctx, seed, key); \
+        break;
+    HW_DISPATCH(li.log_n, B)
+#undef B
     return HW_LAUNCHED();
 }
 
@@ -391,10 +466,14 @@ cudaError_t launch_encrypt(const LaunchInfo& li, const uint64_t* key, const uint
     const int slot0 = labels ? 0 : li.L;
     const int n_enc = li.n_slots - slot0;
     const size_t blocks = n * (size_t)n_enc * 2 * li.dnum;
-    const size_t smem = (size_t)2 * li.n * 8 + li.n;
     if (blocks >= ((size_t)1 << 31)) return cudaErrorInvalidValue;
-    k_encrypt<<<(unsigned)blocks, li.n / 8, smem, st>>>(li.dctx, key, bits, labels, slot0, n_enc,
-                                                       seed, first, out);
+#define B(L)                                                                                    \
+    case L:                                                                                     \
+        k_encrypt<L><<<(unsigned)blocks, ExtCfg<L>::T, encrypt_smem<L>(), st>>>(                \
+            li.dctx, key, bits, labels, slot0, n_enc, seed, first, out);                        \
+        break;
+    HW_DISPATCH(li.log_n, B)
+#undef B
     return HW_LAUNCHED();
 }
 
@@ -403,8 +482,13 @@ cudaError_t launch_decrypt_rlwe(const LaunchInfo& li, const uint64_t* key, const
                                 size_t chunk, cudaStream_t st) {
     for (size_t t0 = 0; t0 < count; t0 += chunk) {
         size_t m = count - t0 < chunk ? count - t0 : chunk;
-        k_rlwe_phase<<<(unsigned)(m * li.r), li.n / 8, (size_t)li.n * 8, st>>>(
-            li.dctx, key, ct + t0 * li.rlwe_words, phase_scratch);
+#define B(L)                                                                              \
+    case L:                                                                               \
+        k_rlwe_phase<L><<<(unsigned)(m * li.r), Geo<L>::T, Geo<L>::XCHG_BYTES, st>>>(     \
+            li.dctx, key, ct + t0 * li.rlwe_words, phase_scratch);                        \
+        break;
+        HW_DISPATCH(li.log_n, B)
+#undef B
         (*li.launches)++;
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -438,14 +522,24 @@ cudaError_t launch_export_rgsw(const LaunchInfo& li, const uint64_t* rgsw, size_
                                uint64_t* out, cudaStream_t st) {
     if (count == 0) return cudaSuccess;
     size_t polys = count * 2 * li.dnum * 2 * li.r;
-    k_export_rgsw<<<(unsigned)polys, li.n / 8, (size_t)li.n * 8, st>>>(li.dctx, rgsw, out);
+#define B(L)                                                                                      \
+    case L:                                                                                       \
+        k_export_rgsw<L><<<(unsigned)polys, Geo<L>::T, Geo<L>::XCHG_BYTES, st>>>(li.dctx, rgsw, out); \
+        break;
+    HW_DISPATCH(li.log_n, B)
+#undef B
     return HW_LAUNCHED();
 }
 
 cudaError_t launch_ntt_batch(const LaunchInfo& li, uint64_t* poly, size_t count, int inverse,
                              cudaStream_t st) {
     if (count == 0) return cudaSuccess;
-    k_ntt_batch<<<(unsigned)count, li.n / 8, (size_t)li.n * 8, st>>>(li.dctx, poly, inverse);
+#define B(L)                                                                                       \
+    case L:                                                                                        \
+        k_ntt_batch<L><<<(unsigned)count, Geo<L>::T, Geo<L>::XCHG_BYTES, st>>>(li.dctx, poly, inverse); \
+        break;
+    HW_DISPATCH(li.log_n, B)
+#undef B
     return HW_LAUNCHED();
 }
 
@@ -454,17 +548,17 @@ extern cudaError_t hw_wisard_kernels_init();
 cudaError_t hw_kernels_init(int log_n) {
     (void)log_n;
     cudaError_t e = cudaMemcpyToSymbol(c_cdt, hw_cdt_table, sizeof(u64) * HW_CDT_LEN);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_encrypt, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             2 * 8192 * 8 + 8192);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_rlwe_phase, cudaFuncAttributeMaxDynamicSharedMemorySize, 8192 * 8);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_keygen, cudaFuncAttributeMaxDynamicSharedMemorySize, 8192 * 8);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_export_rgsw, cudaFuncAttributeMaxDynamicSharedMemorySize, 8192 * 8);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_ntt_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, 8192 * 8);
+#define A(K, L, BYTES) \
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(K<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(BYTES));
+#define X(L)                                          \
+    A(k_keygen, L, Geo<L>::XCHG_BYTES)                \
+    A(k_encrypt, L, encrypt_smem<L>())                \
+    A(k_rlwe_phase, L, Geo<L>::XCHG_BYTES)            \
+    A(k_export_rgsw, L, Geo<L>::XCHG_BYTES)           \
+    A(k_ntt_batch, L, Geo<L>::XCHG_BYTES)
+    HW_FOR_EACH_LOGN(X)
+#undef X
+#undef A
     if (e != cudaSuccess) return e;
     return hw_wisard_kernels_init();
 }

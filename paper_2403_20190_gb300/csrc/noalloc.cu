@@ -6,9 +6,10 @@
 // allocator it cannot reach, request loops whose latency budget forbids
 // cudaMalloc on the hot path, or plug-ins that only ever receive the input
 // and output buffers of a request.  hw_infer_static_scratch() serves them:
-// it runs the same VP inference kernel as hw_infer(), but the two per-block
-// accumulators that hw_infer() takes from the caller's scratch buffer live
-// in a fixed array compiled into this library instead.
+// it runs the same VP inference kernel as hw_infer(), but the per-block
+// accumulators (and their evaluation forms) that hw_infer() takes from the
+// caller's scratch buffer live in a fixed array compiled into this library
+// instead.
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -61,8 +62,8 @@ extern "C" int hw_infer_static_scratch(hw_ctx* ctx, const uint64_t* model, const
     if (!model || !rgsw || !resp || !sums)
         return hw_ctx_fail(HW_EINVAL, "hw_infer_static_scratch: null buffer");
     const LaunchInfo& li = *hw_ctx_launch_info(ctx);
-    // each persistent block needs two RLWE accumulators
-    const size_t per_block = 2 * li.rlwe_words * sizeof(u64);
+    // each persistent block needs two RLWE accumulators and their evaluation forms
+    const size_t per_block = 4 * li.rlwe_words * sizeof(u64);
     const size_t fit = HW_STATIC_SCRATCH_BYTES / per_block;
     if (fit < 1) {
         char buf[256];
@@ -81,7 +82,8 @@ extern "C" int hw_infer_static_scratch(hw_ctx* ctx, const uint64_t* model, const
     if ((size_t)grid > fit) grid = (int)fit;
     cudaStream_t st = (cudaStream_t)stream;
     // No part of the array has to start at zero: every block writes each of
-    // its accumulators completely before it reads it.
+    // its accumulators (and their evaluation forms) completely before it
+    // reads them.
     e = launch_vp_infer(li, model, rgsw, n, resp, scratch, grid, st);
     if (e == cudaSuccess) e = launch_class_sums(li, resp, n, sums, st);
     if (e != cudaSuccess) {

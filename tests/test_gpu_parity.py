@@ -33,16 +33,23 @@ def session(cfg):
     return Session(cfg, 0)
 
 
+# every tree shape of the workloads on N = 64 rings (the smallest ring the
+# CUDA path supports)
 TINY = {
-    "z0": dict(log_n=5, n_primes=1, prime_bits=30, log_beta=5, log_p=8, n_classes=2,
+    # z = 0: label bit among the rotation bits; base-32 gadget; short last tuple
+    "z0": dict(log_n=6, n_primes=1, prime_bits=30, log_beta=5, log_p=8, n_classes=2,
                n_values=5, therm_bits=2, addr_bits=3, tuple_bits=3),
-    "zL": dict(log_n=3, n_primes=2, prime_bits=50, log_beta=0, log_p=16, n_classes=3,
-               n_values=5, therm_bits=2, addr_bits=3, tuple_bits=3),
-    "zltL_h3": dict(log_n=3, n_primes=3, prime_bits=55, log_beta=0, log_p=20, n_classes=5,
-                    n_values=4, therm_bits=3, addr_bits=2, tuple_bits=4, hash_h3=1),
-    "zgtL": dict(log_n=3, n_primes=3, prime_bits=55, log_beta=0, log_p=22, n_classes=3,
-                 n_values=4, therm_bits=2, addr_bits=4, tuple_bits=4),
-    "r2_beta1024": dict(log_n=4, n_primes=2, prime_bits=30, log_beta=10, log_p=12, n_classes=4,
+    # z = L: the tree holds exactly the label bits; short last tuple
+    "zL": dict(log_n=6, n_primes=2, prime_bits=50, log_beta=0, log_p=16, n_classes=3,
+               n_values=7, therm_bits=2, addr_bits=6, tuple_bits=6),
+    # z < L: a label bit among the rotation bits; hashed tuples
+    "zltL_h3": dict(log_n=6, n_primes=3, prime_bits=55, log_beta=0, log_p=20, n_classes=5,
+                    n_values=4, therm_bits=3, addr_bits=5, tuple_bits=8, hash_h3=1),
+    # z > L: an address bit in the tree; the last RAM has only that bit
+    "zgtL": dict(log_n=6, n_primes=3, prime_bits=55, log_beta=0, log_p=22, n_classes=3,
+                 n_values=4, therm_bits=2, addr_bits=7, tuple_bits=7),
+    # several digits per prime over two primes
+    "r2_beta1024": dict(log_n=6, n_primes=2, prime_bits=30, log_beta=10, log_p=12, n_classes=4,
                         n_values=6, therm_bits=2, addr_bits=3, tuple_bits=3),
 }
 

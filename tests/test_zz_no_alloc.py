@@ -20,8 +20,8 @@ from synthdata import get_config, make_dataset
 pytestmark = pytest.mark.gpu
 
 CASES = {
-    "tiny_tree": dict(log_n=3, n_primes=3, prime_bits=55, log_beta=0, log_p=22, n_classes=3,
-                      n_values=4, therm_bits=2, addr_bits=4, tuple_bits=4, data_kind="uniform",
+    "tiny_tree": dict(log_n=6, n_primes=3, prime_bits=55, log_beta=0, log_p=22, n_classes=3,
+                      n_values=4, therm_bits=2, addr_bits=7, tuple_bits=7, data_kind="uniform",
                       act="log", act_arg=0),
     "cfg2": {},
 }
