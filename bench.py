@@ -42,7 +42,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--config", default="cfg2")
-    ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--batch", type=int, default=0,
+                    help="samples per step (0: the workload's default, sized to fit HBM)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-ntt", action="store_true")
@@ -234,6 +235,12 @@ def algorithmic_counts(sess, cfg):
             "rgsw_bytes": sz["rgsw_words"] * 8}
 
 
+# samples per step: cfg1's whole test set; for the larger rings, what keeps one
+# encrypted batch (786 MiB, 3.9 GiB, 15.5 GiB per sample) plus scratch well
+# inside HBM
+DEFAULT_BATCH = {"cfg1": 100, "cfg2": 64, "cfg3": 16, "cfg4": 4}
+
+
 def gpu_arm(args, ws, rank, local, pg):
     import numpy as np
     import torch
@@ -248,7 +255,7 @@ def gpu_arm(args, ws, rank, local, pg):
     cfg = get_config(args.config)
     sess = Session(cfg, local)
     dev = sess.device
-    bsz = args.batch
+    bsz = args.batch or DEFAULT_BATCH.get(args.config, 16)
     sz = sess.sz
     n_pool = max(cfg.n_train, bsz)
     # the whole train / test sets of the workload, resident in HBM as raw bytes
