@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-ntt", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=40)
     return ap.parse_args()
 
 
@@ -247,7 +249,7 @@ def gpu_arm(args, ws, rank, local, pg):
 
     from paper_2403_20190_gb300 import binding as B
     from paper_2403_20190_gb300 import build as libbuild
-    from paper_2403_20190_gb300.session import Session
+    from paper_2403_20190_gb300.session import ServerStep, Session
     from synthdata import get_config, make_dataset
 
     libbuild.build()
@@ -267,62 +269,46 @@ def gpu_arm(args, ws, rank, local, pg):
 
     key = sess.keygen(cfg.key_seed)
     model = sess.new_model()
-    rgsw = sess.words(bsz * sz["sample_words"], zero=False)
-    tscratch = sess.train_scratch(bsz)
-    ibufs = sess.infer_buffers(bsz)
+    st = ServerStep(sess, key, model, bsz, bsz)
     bits = torch.empty((bsz, sz["n_data"]), dtype=torch.uint8, device=dev)
-    counts = torch.empty(bsz * cfg.n_classes * sz["k0"], dtype=torch.int64, device=dev)
-    scores = torch.empty(bsz * cfg.n_classes, dtype=torch.int64, device=dev)
-    labels_out = torch.empty(bsz, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
 
     n_tr = tr_vals_d.shape[0]
     n_te = te_vals_d.shape[0]
     offset = rank * 7919  # replicas draw different samples
 
-    def step(k, evs=None, host=None):
-        i0 = ((k * bsz + offset) % n_tr)
-        i0 = min(i0, n_tr - bsz)
+    def client(k, host=None):
+        """encode + encrypt one train and one test batch (fresh seeds)"""
+        i0 = min(((k * bsz + offset) % n_tr), n_tr - bsz)
         j0 = min(((k * bsz + offset) % n_te), n_te - bsz)
         if host is not None:
-            h_tr, h_lab, h_te = host[:3]
-            tv = tr_vals_d[:bsz]
-            tl = tr_lab_d[:bsz]
-            tev = te_vals_d[:bsz]
-            tv.copy_(h_tr, non_blocking=True)
-            tl.copy_(h_lab, non_blocking=True)
-            tev.copy_(h_te, non_blocking=True)
+            tv, tl, tev = tr_vals_d[:bsz], tr_lab_d[:bsz], te_vals_d[:bsz]
+            tv.copy_(host[0], non_blocking=True)
+            tl.copy_(host[1], non_blocking=True)
+            tev.copy_(host[2], non_blocking=True)
         else:
             tv, tl, tev = tr_vals_d[i0:i0 + bsz], tr_lab_d[i0:i0 + bsz], te_vals_d[j0:j0 + bsz]
-        ev = (lambda name: evs[name].record(stream)) if evs else (lambda name: None)
-        ev("t0")
         B.hw_encode(sess.ctx, tv, bsz, bits, stream)
-        B.hw_encrypt_sample(sess.ctx, key, bits, tl, bsz, 1000 + k, 0, rgsw, stream)
-        ev("t1")
-        B.hw_train_accumulate(sess.ctx, model, rgsw, bsz, tscratch, stream)
-        ev("t2")
+        B.hw_encrypt_sample(sess.ctx, key, bits, tl, bsz, 1000 + k, 0, st.rgsw_train, stream)
         B.hw_encode(sess.ctx, tev, bsz, bits, stream)
-        B.hw_encrypt_sample(sess.ctx, key, bits, None, bsz, 500000 + k, 0, rgsw, stream)
-        ev("t3")
-        resp, sums, scr = ibufs
-        B.hw_infer(sess.ctx, model, rgsw, bsz, resp, sums, scr, stream)
-        ev("t4")
-        B.hw_decrypt(sess.ctx, key, B.HW_DEC_LWE, resp, bsz * cfg.n_classes * sz["k0"], counts, stream)
-        B.hw_pdact(sess.ctx, counts, bsz, scores, labels_out, stream)
-        ev("t5")
-        if host is not None:
-            host[3].copy_(labels_out, non_blocking=True)
+        B.hw_encrypt_sample(sess.ctx, key, bits, None, bsz, 500000 + k, 0, st.rgsw_test, stream)
 
-    names = ["t0", "t1", "t2", "t3", "t4", "t5"]
+    def step(k, host=None):
+        client(k, host)
+        st.replay()
+        if host is not None:
+            host[3].copy_(st.labels, non_blocking=True)
+
     for k in range(args.warmup):
-        step(k)
+        client(k)
+        st.run()
+    st.capture()  # the server side of a step as one CUDA graph
     torch.cuda.synchronize()
 
     def barrier():
         if pg is not None:
             pg.barrier()
 
-    evsets = [{nm: torch.cuda.Event(enable_timing=True) for nm in names} for _ in range(args.steps)]
     clocks = ClockSampler(local)
     clocks.start()
     launches0 = B.hw_launch_count(sess.ctx)
@@ -332,25 +318,42 @@ def gpu_arm(args, ws, rank, local, pg):
     end = torch.cuda.Event(enable_timing=True)
     start.record(stream)
     for k in range(args.steps):
-        step(args.warmup + k, evsets[k])
+        step(args.warmup + k)
     end.record(stream)
     torch.cuda.synchronize()
     barrier()
-    launches = B.hw_launch_count(sess.ctx) - launches0
+    launches = B.hw_launch_count(sess.ctx) - launches0 + st.launches_per_step * args.steps
     clk = clocks.stop()
     elapsed_ms = start.elapsed_time(end)
     if pg is not None:
         t = torch.tensor([elapsed_ms], device=dev)
         pg.all_reduce(t, op=pg.ReduceOp.MAX)
         elapsed_ms = float(t.item())
-    phase = {"encrypt_train": [], "train": [], "encrypt_test": [], "infer": [], "decrypt_pdact": []}
-    keys = list(phase)
-    for evs in evsets:
-        for a, b, kname in zip(names[:-1], names[1:], keys):
-            phase[kname].append(evs[a].elapsed_time(evs[b]))
-    ph = {k: statistics.mean(v) for k, v in phase.items()}
     total_samples = 2 * bsz * args.steps * ws
     value = total_samples / (elapsed_ms / 1000.0)
+
+    # phase breakdown from one extra eager step with events between the calls
+    names = ["t0", "t1", "t2", "t3", "t4", "t5"]
+    evs = {nm: torch.cuda.Event(enable_timing=True) for nm in names}
+    k = args.warmup + args.steps
+    evs["t0"].record(stream)
+    B.hw_encode(sess.ctx, tr_vals_d[:bsz], bsz, bits, stream)
+    B.hw_encrypt_sample(sess.ctx, key, bits, tr_lab_d[:bsz], bsz, 1000 + k, 0, st.rgsw_train, stream)
+    evs["t1"].record(stream)
+    B.hw_train_accumulate(sess.ctx, model, st.rgsw_train, bsz, st.scratch, stream)
+    evs["t2"].record(stream)
+    B.hw_encode(sess.ctx, te_vals_d[:bsz], bsz, bits, stream)
+    B.hw_encrypt_sample(sess.ctx, key, bits, None, bsz, 500000 + k, 0, st.rgsw_test, stream)
+    evs["t3"].record(stream)
+    resp, sums, scr = st.ibufs
+    B.hw_infer(sess.ctx, model, st.rgsw_test, bsz, resp, sums, scr, stream)
+    evs["t4"].record(stream)
+    B.hw_decrypt(sess.ctx, key, B.HW_DEC_LWE, resp, bsz * cfg.n_classes * sz["k0"], st.counts, stream)
+    B.hw_pdact(sess.ctx, st.counts, bsz, st.scores, st.labels, stream)
+    evs["t5"].record(stream)
+    torch.cuda.synchronize()
+    keys = ["encrypt_train", "train", "encrypt_test", "infer", "decrypt_pdact"]
+    ph = {kn: evs[a].elapsed_time(evs[b]) for a, b, kn in zip(names[:-1], names[1:], keys)}
 
     # e2e through the C ABI with pinned host buffers, copies inside the timed region
     e2e = None
@@ -364,7 +367,7 @@ def gpu_arm(args, ws, rank, local, pg):
         barrier()
         t0 = time.perf_counter()
         for k in range(args.steps):
-            step(args.warmup + args.steps + k, None, host)
+            step(args.warmup + args.steps + 1 + k, host)
             torch.cuda.current_stream().synchronize()
             _ = int(h_out[0])
         t1 = time.perf_counter()
@@ -412,6 +415,33 @@ def gpu_arm(args, ws, rank, local, pg):
                "peak_gbs": pk["hbm_gbs"], "peak_kind": pk_kind}
         del polys
 
+    # the same workload one request at a time: each request one train and one
+    # test sample, encoded, encrypted, trained, inferred, decrypted, waited for
+    single = None
+    if not args.no_serve:
+        n1 = 6
+        t0 = time.perf_counter()
+        for k in range(n1):
+            B.hw_encode(sess.ctx, tr_vals_d[k:k + 1], 1, bits, stream)
+            B.hw_encrypt_sample(sess.ctx, key, bits, tr_lab_d[k:k + 1], 1, 9000 + k, 0, st.rgsw_train, stream)
+            B.hw_train_accumulate(sess.ctx, model, st.rgsw_train, 1, st.scratch, stream)
+            B.hw_encode(sess.ctx, te_vals_d[k:k + 1], 1, bits, stream)
+            B.hw_encrypt_sample(sess.ctx, key, bits, None, 1, 19000 + k, 0, st.rgsw_test, stream)
+            resp, sums, scr = st.ibufs
+            B.hw_infer(sess.ctx, model, st.rgsw_test, 1, resp, sums, scr, stream)
+            B.hw_decrypt(sess.ctx, key, B.HW_DEC_LWE, resp, cfg.n_classes * sz["k0"], st.counts, stream)
+            B.hw_pdact(sess.ctx, st.counts, 1, st.scores, st.labels, stream)
+            _ = int(st.labels[0].item())
+        single = {"samples_per_s": 2 * n1 / (time.perf_counter() - t0), "requests": n1,
+                  "request": "1 train + 1 test sample, synchronous"}
+
+    serving = None
+    if not args.no_serve:
+        del st, tr_vals_d, tr_lab_d, te_vals_d, bits
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        serving = serve_leg(args, local)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cores = min(os.cpu_count() or 1, 16)
@@ -427,6 +457,7 @@ def gpu_arm(args, ws, rank, local, pg):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
             "data": "synthetic",
             "config": {"workload": workload_name(cfg), "batch_train": bsz, "batch_test": bsz,
+                       "server_step": "CUDA graph (IVP + accumulate, VP + sums, decrypt, PD-act)",
                        "l2": "inputs larger than L2 (encrypted batch ~%.0f GB)" %
                              (bsz * sz["sample_words"] * 8 / 1e9),
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
@@ -440,9 +471,45 @@ def gpu_arm(args, ws, rank, local, pg):
             "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clk,
-            "p99_ms": None,
+            "p99_ms": serving["batched"]["p99_ms"] if serving else None,
+            "serving": serving,
+            "one_request_at_a_time": single,
         }
         print(json.dumps(line), flush=True)
+
+
+# per-request sample caps of the serving mix: what the footprint rule leaves
+# for one request (786 MiB, 3.9 GiB, 15.5 GiB per encrypted cfg2/3/4 sample)
+SERVE_MAX = {"cfg1": 256, "cfg2": 16, "cfg3": 2, "cfg4": 1}
+
+
+def serve_leg(args, local):
+    """Poisson stream (200 requests/s, seeded) of train and infer requests over
+    the four workloads, served with continuous batching and, for comparison,
+    one request at a time; latency is arrival to completion."""
+    import copy
+
+    import torch
+
+    from paper_2403_20190_gb300.serve import ResidentModel, Server, latency_stats, poisson_stream
+    from synthdata import get_config
+    cfgs = {nm: get_config(nm) for nm in ("cfg1", "cfg2", "cfg3", "cfg4")}
+    models = {nm: ResidentModel(c, local, key_seed=c.key_seed) for nm, c in cfgs.items()}
+    reqs = poisson_stream(cfgs, n_requests=args.serve_requests, rate=200.0, seed=2024,
+                          max_samples=SERVE_MAX)
+    budget = 120 << 30
+    warm = copy.deepcopy(reqs[:4])
+    Server(models, budget).run(warm, realtime=False)
+    base = copy.deepcopy(reqs)
+    batched = Server(models, budget, n_streams=4).run(copy.deepcopy(reqs), realtime=True)
+    alone = Server(models, budget).run_one_at_a_time(base)
+    out = {"requests": len(reqs), "rate_per_s": 200.0, "hbm_budget_gb": budget / 2**30,
+           "batched": latency_stats(batched), "one_at_a_time": latency_stats(alone),
+           "mix": {nm: sum(1 for r in reqs if r.cfg_name == nm) for nm in cfgs},
+           "max_samples_per_request": SERVE_MAX}
+    del models
+    torch.cuda.empty_cache()
+    return out
 
 
 def main():

@@ -1,5 +1,6 @@
 """Workload-level convenience over the C ABI: device buffers come from
-torch's caching allocator; every step is one libhwisard call."""
+torch's caching allocator; every step is one libhwisard call.  ServerStep
+captures the server side of a step into a CUDA graph."""
 import torch
 
 from . import binding as B
@@ -108,3 +109,48 @@ class Session:
         out = self.words(int(count) * self.sz["rgsw_words"], zero=False)
         B.hw_export_rgsw(self.ctx, rgsw, count, out, stream)
         return out
+
+
+class ServerStep:
+    """The server side of one step on fixed batch sizes: train on an
+    encrypted batch (IVP + accumulate into the resident model) and answer an
+    encrypted test batch (VP + class sums), then decrypt the responses and
+    classify them with PD-act.  The encrypted inputs live in rgsw_train /
+    rgsw_test; capture() records the whole step once into a CUDA graph and
+    replay() re-issues it (the model keeps accumulating across replays)."""
+
+    def __init__(self, sess: Session, key, model, n_train: int, n_test: int):
+        self.sess, self.key, self.model = sess, key, model
+        self.n_train, self.n_test = n_train, n_test
+        sz = sess.sz
+        self.rgsw_train = sess.words(n_train * sz["sample_words"], zero=False)
+        self.rgsw_test = sess.words(n_test * sz["sample_words"], zero=False)
+        self.scratch = sess.train_scratch(max(n_train, 1))
+        self.ibufs = sess.infer_buffers(max(n_test, 1))
+        l, k0 = sess.cfg.n_classes, sz["k0"]
+        self.counts = torch.empty(max(n_test, 1) * l * k0, dtype=torch.int64, device=sess.device)
+        self.scores = torch.empty(max(n_test, 1) * l, dtype=torch.int64, device=sess.device)
+        self.labels = torch.empty(max(n_test, 1), dtype=torch.int32, device=sess.device)
+        self.graph = None
+        self.launches_per_step = None
+
+    def run(self, stream=None):
+        s, ctx = self.sess, self.sess.ctx
+        B.hw_train_accumulate(ctx, self.model, self.rgsw_train, self.n_train, self.scratch, stream)
+        resp, sums, scr = self.ibufs
+        B.hw_infer(ctx, self.model, self.rgsw_test, self.n_test, resp, sums, scr, stream)
+        l, k0 = s.cfg.n_classes, s.sz["k0"]
+        B.hw_decrypt(ctx, self.key, B.HW_DEC_LWE, resp, self.n_test * l * k0, self.counts, stream)
+        B.hw_pdact(ctx, self.counts, self.n_test, self.scores, self.labels, stream)
+
+    def capture(self):
+        g = torch.cuda.CUDAGraph()
+        before = B.hw_launch_count(self.sess.ctx)
+        with torch.cuda.graph(g, capture_error_mode="relaxed"):
+            self.run()
+        self.launches_per_step = B.hw_launch_count(self.sess.ctx) - before
+        self.graph = g
+        return g
+
+    def replay(self):
+        self.graph.replay()

@@ -80,9 +80,9 @@ CONFIGS = {
 }
 
 
-def get_config(name: str, **overrides) -> Config:
+def get_config(cfg_name: str, **overrides) -> Config:
     """Return a named configuration, optionally with fields replaced."""
-    cfg = CONFIGS[name]
+    cfg = CONFIGS[cfg_name]
     if overrides:
         d = cfg.as_dict()
         d.update(overrides)
