@@ -395,25 +395,35 @@ def gpu_arm(args, ws, rank, local, pg):
                              f"{sm_mhz:.0f} MHz / {MULS_PER_MODMUL} per 64-bit modular product"}
     train_modmul = alg["ext_train_per_sample"] * bsz * alg["per_ext_modmul"]
 
-    # batched NTT throughput (forward transforms, one read + one write per polynomial)
+    # batched NTT throughput (forward transforms, one read + one write per
+    # polynomial): this workload's ring, and cfg1's 30-bit ring, where the
+    # 32-bit transform makes the NTT bound by HBM rather than by integer
+    # multiplies
     ntt = None
     if not args.no_ntt:
-        count = 65536 if sz["n"] <= 4096 else 32768
-        polys = sess.words(count * sz["n"])
-        for _ in range(3):
-            B.hw_ntt_forward(sess.ctx, polys, count, stream)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        reps = 5
-        e0.record(stream)
-        for _ in range(reps):
-            B.hw_ntt_forward(sess.ctx, polys, count, stream)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        t = e0.elapsed_time(e1) / reps / 1000.0
-        gbs = 2.0 * count * sz["n"] * 8 / t / 1e9
-        ntt = {"gbs": gbs, "frac_of_hbm": gbs / pk["hbm_gbs"], "polys": count, "n": sz["n"],
-               "peak_gbs": pk["hbm_gbs"], "peak_kind": pk_kind}
-        del polys
+        def ntt_rate(ctx_sess, count):
+            nn = ctx_sess.sz["n"]
+            polys = ctx_sess.words(count * nn)
+            for _ in range(3):
+                B.hw_ntt_forward(ctx_sess.ctx, polys, count, stream)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 5
+            e0.record(stream)
+            for _ in range(reps):
+                B.hw_ntt_forward(ctx_sess.ctx, polys, count, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) / reps / 1000.0
+            gbs = 2.0 * count * nn * 8 / t / 1e9
+            del polys
+            return {"gbs": gbs, "frac_of_hbm": gbs / pk["hbm_gbs"], "polys": count, "n": nn,
+                    "prime_bits": ctx_sess.cfg.prime_bits, "ms_per_launch": t * 1000.0}
+        ntt = {"peak_gbs": pk["hbm_gbs"], "peak_kind": pk_kind,
+               args.config: ntt_rate(sess, 65536 if sz["n"] <= 4096 else 32768)}
+        if args.config != "cfg1":
+            s1 = Session(get_config("cfg1"), local)
+            ntt["cfg1"] = ntt_rate(s1, 262144)
+            del s1
 
     # the same workload one request at a time: each request one train and one
     # test sample, encoded, encrypted, trained, inferred, decrypted, waited for

@@ -346,7 +346,10 @@ extern "C" int hw_create(const hw_params* p, int cuda_device, hw_ctx** out) {
             for (size_t k = dv.size(); k-- > 0;) {
                 u64 dk = hmul(inv, pre[k], q[i]);
                 inv = hmul(inv, dv[k], q[i]);
-                size_t o = 2 * ((size_t)i * 2 * log_n * n + k);
+                // thread-major: position pos of a row sits at eval_addr(pos)
+                const size_t row = k / n;
+                const int pos = (int)(k % n);
+                size_t o = 2 * ((size_t)i * 2 * log_n * n + row * n + eval_addr(pos, log_n));
                 rot[o] = dv[k];
                 rot[o + 1] = shoup(dv[k], q[i]);
                 rinv[o] = dk;
@@ -355,6 +358,26 @@ extern "C" int hw_create(const hw_params* p, int cuda_device, hw_ctx** out) {
         }
     }
     H.diag = p->log_beta == 0 ? 1 : 0;
+
+    // 32-bit transform tables when every prime is below 2^30
+    const bool small_q = p->prime_bits <= 30;
+    std::vector<uint32_t> tw32(small_q ? (size_t)4 * r * n : 1, 0);
+    if (small_q)
+        for (int i = 0; i < r; i++) {
+            const uint32_t qi = (uint32_t)q[i];
+            for (int k = 0; k < n; k++) {
+                const u64* f = &tw[2 * ((size_t)i * n + k)];
+                const u64* b = &tw[(size_t)2 * r * n + 2 * ((size_t)i * n + k)];
+                size_t o = 2 * ((size_t)i * n + k);
+                tw32[o] = (uint32_t)f[0];
+                tw32[o + 1] = (uint32_t)((f[0] << 32) / qi);
+                tw32[(size_t)2 * r * n + o] = (uint32_t)b[0];
+                tw32[(size_t)2 * r * n + o + 1] = (uint32_t)((b[0] << 32) / qi);
+            }
+            u64 ni = hinv((u64)n % q[i], q[i]);
+            H.n_inv32[i] = (uint32_t)ni;
+            H.n_inv32_s[i] = (uint32_t)((ni << 32) / qi);
+        }
 
     // digits must lift without reduction: |d| <= (q_i - 1)/2 < q_j
     for (int i = 0; i < r; i++)
@@ -389,10 +412,10 @@ extern "C" int hw_create(const hw_params* p, int cuda_device, hw_ctx** out) {
 
     // upload
     size_t bytes_tw = tw.size() * 8, bytes_rs = c->ram_slot.size() * 4, bytes_perm = perm.size() * 4,
-           bytes_h3 = h3.size() * 8, bytes_rot = rot.size() * 8;
+           bytes_h3 = h3.size() * 8, bytes_rot = rot.size() * 8, bytes_tw32 = tw32.size() * 4;
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     size_t total = al(bytes_tw) + al(bytes_rs) + al(bytes_perm) + al(bytes_h3) + 2 * al(bytes_rot) +
-                   al(sizeof(DevCtx));
+                   al(bytes_tw32) + al(sizeof(DevCtx));
     c->phase_chunk = 64;
     cudaError_t e = cudaSetDevice(cuda_device);
     if (e == cudaSuccess) e = cudaMalloc(&c->tables, total);
@@ -418,6 +441,11 @@ extern "C" int hw_create(const hw_params* p, int cuda_device, hw_ctx** out) {
     H.h3 = (const u64*)put(h3.data(), bytes_h3);
     H.rot_tab = (const ulonglong2*)put(rot.data(), bytes_rot);
     H.rot_inv = (const ulonglong2*)put(rinv.data(), bytes_rot);
+    {
+        const uint2* t32 = (const uint2*)put(tw32.data(), bytes_tw32);
+        H.tw32_fwd = small_q ? t32 : nullptr;
+        H.tw32_inv = small_q ? t32 + (size_t)r * n : nullptr;
+    }
     c->dctx = (DevCtx*)put(&H, sizeof(DevCtx));
     e = hw_kernels_init(log_n);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -470,6 +498,7 @@ extern "C" int hw_create(const hw_params* p, int cuda_device, hw_ctx** out) {
     li.sample_words = H.sample_words;
     li.model_words = H.model_words;
     li.sm_count = sms;
+    li.small_q = p->prime_bits <= 30 ? 1 : 0;
     li.launches = &c->launches;
     *out = c;
     return HW_OK;

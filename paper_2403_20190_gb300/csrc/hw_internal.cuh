@@ -44,6 +44,10 @@ struct DevCtx {
     // rot_inv the same for (Psi^(+-2^t) - 1)^-1.
     const ulonglong2* rot_tab;
     const ulonglong2* rot_inv;
+    // 32-bit transform tables (w, floor(w 2^32 / q)) when every q_i < 2^30, else null
+    const uint2* tw32_fwd;
+    const uint2* tw32_inv;
+    uint32_t n_inv32[HW_MAXP], n_inv32_s[HW_MAXP];
     int diag;  // one digit per prime: the digit of prime i at prime i is the residue
     size_t rlwe_words, rgsw_words, lwe_words, sample_words, model_words;
 };
@@ -116,6 +120,21 @@ __device__ __forceinline__ u64 redc_lazy(u64 hi, u64 lo, u64 q, u64 qneg) {
 // last inverse round writes positions tid + k*T (v[k]); the last forward
 // round leaves, and the first inverse round takes, positions 16*tid + e.
 // ---------------------------------------------------------------------------
+// Residues per thread of the external-product geometry (8 below N = 8192,
+// 16 at N = 8192); shared by the kernels and the host tables.
+__host__ __device__ constexpr int ext_loge(int log_n) { return log_n >= 13 ? 4 : 3; }
+
+// Evaluation-form arrays (RGSW rows, the key's evaluation form, rotation
+// tables, evaluation-form copies of ciphertexts) are stored thread-major in
+// the external-product geometry: evaluation position E*t + e lives at
+// address e*T + t (T = N/E threads), so every load and store in that
+// geometry is coalesced.
+__host__ __device__ inline int eval_addr(int pos, int log_n) {
+    const int loge = ext_loge(log_n);
+    const int T = (1 << log_n) >> loge;
+    return (pos & ((1 << loge) - 1)) * T + (pos >> loge);
+}
+
 template <int LOGN, int LOGE = 4>
 struct Ring {
     static constexpr int N = 1 << LOGN;
@@ -313,6 +332,176 @@ __device__ __forceinline__ void ntt_inv(u64 (&v)[NP][1 << LOGE], Xchg& xc, const
     inv_from<LOGN, LOGE, NP, 0>(v, xc, C.tw_inv + (size_t)j * Ring<LOGN>::N, q, 2 * q);
 }
 
+// ---------------------------------------------------------------------------
+// 32-bit transform for primes below 2^30 (Harvey butterflies, values < 4q <
+// 2^32): forward X' = X~ + t, Y' = X~ + 2q - t with X~ = X reduced below 2q
+// and t = Shoup(Y*W) in [0, 2q); inverse as the 64-bit one.  Same positions,
+// rounds and exchanges as the 64-bit transform.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ u32 shoup32_lazy(u32 x, u32 w, u32 ws, u32 q) {
+    return x * w - __umulhi(x, ws) * q;
+}
+
+template <int LOGN, int LOGE, int NP, int ST0, int R>
+__device__ __forceinline__ void fwd_round32(u32 (&v)[NP][1 << LOGE], const uint2* __restrict__ tw,
+                                            u32 q, u32 q2) {
+    constexpr int E = 1 << R, G = (1 << LOGE) / E, B_LO = LOGN - ST0 - R;
+#pragma unroll
+    for (int gg = 0; gg < G; gg++) {
+        const int hi = (threadIdx.x + gg * Ring<LOGN, LOGE>::T) >> B_LO;
+        uint2 W[E - 1];
+#pragma unroll
+        for (int s = 0; s < R; s++)
+#pragma unroll
+            for (int jj = 0; jj < (1 << s); jj++)
+                W[(1 << s) - 1 + jj] = __ldg(tw + (1 << (ST0 + s)) + ((hi << s) | jj));
+#pragma unroll
+        for (int s = 0; s < R; s++) {
+            const int lb = R - 1 - s;
+#pragma unroll
+            for (int e = 0; e < E; e++) {
+                if (e & (1 << lb)) continue;
+                const uint2 w = W[(1 << s) - 1 + (e >> (lb + 1))];
+#pragma unroll
+                for (int pp = 0; pp < NP; pp++) {
+                    u32& X = v[pp][gg + e * G];
+                    u32& Y = v[pp][gg + (e | (1 << lb)) * G];
+                    const u32 x = X >= q2 ? X - q2 : X;
+                    const u32 t = shoup32_lazy(Y, w.x, w.y, q);
+                    Y = x + q2 - t;
+                    X = x + t;
+                }
+            }
+        }
+    }
+}
+
+template <int LOGN, int LOGE, int NP, int P0, int R>
+__device__ __forceinline__ void inv_round32(u32 (&v)[NP][1 << LOGE], const uint2* __restrict__ tw,
+                                            u32 q, u32 q2) {
+    constexpr int E = 1 << R, G = (1 << LOGE) / E;
+#pragma unroll
+    for (int gg = 0; gg < G; gg++) {
+        const int hi = (threadIdx.x + gg * Ring<LOGN, LOGE>::T) >> P0;
+        uint2 W[E - 1];
+#pragma unroll
+        for (int s = 0; s < R; s++) {
+            const int h = 1 << (LOGN - 1 - (P0 + s));
+#pragma unroll
+            for (int jj = 0; jj < (1 << (R - 1 - s)); jj++)
+                W[(1 << (R - 1 - s)) - 1 + jj] = __ldg(tw + h + ((hi << (R - 1 - s)) | jj));
+        }
+#pragma unroll
+        for (int s = 0; s < R; s++) {
+#pragma unroll
+            for (int e = 0; e < E; e++) {
+                if (e & (1 << s)) continue;
+                const uint2 w = W[(1 << (R - 1 - s)) - 1 + (e >> (s + 1))];
+#pragma unroll
+                for (int pp = 0; pp < NP; pp++) {
+                    u32& U = v[pp][gg + e * G];
+                    u32& V = v[pp][gg + (e | (1 << s)) * G];
+                    u32 sum = U + V;
+                    sum = sum >= q2 ? sum - q2 : sum;
+                    V = shoup32_lazy(U + q2 - V, w.x, w.y, q);
+                    U = sum;
+                }
+            }
+        }
+    }
+}
+
+template <int LOGN, int LOGE, int NP, int ST0>
+__device__ __forceinline__ void fwd_from32(u32 (&v)[NP][1 << LOGE], Xchg& xc,
+                                           const uint2* __restrict__ tw, u32 q, u32 q2) {
+    constexpr int R = FwdR<LOGN, LOGE, ST0>::R, G = (1 << LOGE) >> R;
+    fwd_round32<LOGN, LOGE, NP, ST0, R>(v, tw, q, q2);
+    if constexpr (ST0 + R < LOGN) {
+        constexpr int R2 = FwdR<LOGN, LOGE, ST0 + R>::R, G2 = (1 << LOGE) >> R2;
+        u32* sm = (u32*)xc.next();
+#pragma unroll
+        for (int pp = 0; pp < NP; pp++)
+#pragma unroll
+            for (int gg = 0; gg < G; gg++)
+#pragma unroll
+                for (int e = 0; e < (1 << R); e++)
+                    sm[pp * xc.stride + padw<LOGE>(fpos<LOGN, LOGE, ST0, R>(gg, e))] = v[pp][gg + e * G];
+        __syncthreads();
+#pragma unroll
+        for (int pp = 0; pp < NP; pp++)
+#pragma unroll
+            for (int gg = 0; gg < G2; gg++)
+#pragma unroll
+                for (int e = 0; e < (1 << R2); e++)
+                    v[pp][gg + e * G2] = sm[pp * xc.stride + padw<LOGE>(fpos<LOGN, LOGE, ST0 + R, R2>(gg, e))];
+        fwd_from32<LOGN, LOGE, NP, ST0 + R>(v, xc, tw, q, q2);
+    }
+}
+
+template <int LOGN, int LOGE, int NP, int P0>
+__device__ __forceinline__ void inv_from32(u32 (&v)[NP][1 << LOGE], Xchg& xc,
+                                           const uint2* __restrict__ tw, u32 q, u32 q2) {
+    constexpr int R = InvR<LOGN, LOGE, P0>::R, G = (1 << LOGE) >> R;
+    inv_round32<LOGN, LOGE, NP, P0, R>(v, tw, q, q2);
+    if constexpr (P0 + R < LOGN) {
+        constexpr int R2 = InvR<LOGN, LOGE, P0 + R>::R, G2 = (1 << LOGE) >> R2;
+        u32* sm = (u32*)xc.next();
+#pragma unroll
+        for (int pp = 0; pp < NP; pp++)
+#pragma unroll
+            for (int gg = 0; gg < G; gg++)
+#pragma unroll
+                for (int e = 0; e < (1 << R); e++)
+                    sm[pp * xc.stride + padw<LOGE>(ipos<LOGN, LOGE, P0, R>(gg, e))] = v[pp][gg + e * G];
+        __syncthreads();
+#pragma unroll
+        for (int pp = 0; pp < NP; pp++)
+#pragma unroll
+            for (int gg = 0; gg < G2; gg++)
+#pragma unroll
+                for (int e = 0; e < (1 << R2); e++)
+                    v[pp][gg + e * G2] = sm[pp * xc.stride + padw<LOGE>(ipos<LOGN, LOGE, P0 + R, R2>(gg, e))];
+        inv_from32<LOGN, LOGE, NP, P0 + R>(v, xc, tw, q, q2);
+    }
+}
+
+// A warp's 32*E consecutive positions E*(32w + lane) + e (thread-held as
+// v[e]) moved to/from dst[position] with coalesced global accesses, through
+// a warp-private region of 32*(E+1) words of wbuf (padded: conflict-free).
+template <int E, typename W>
+__device__ __forceinline__ void warp_store_positions(W* dst, const W (&v)[E], W* wbuf) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    W* wb = wbuf + w * 32 * (E + 1);
+    __syncwarp();
+#pragma unroll
+    for (int e = 0; e < E; e++) wb[lane * (E + 1) + e] = v[e];
+    __syncwarp();
+    W* d = dst + (size_t)w * 32 * E;
+#pragma unroll
+    for (int k = 0; k < E; k++) {
+        const int idx = k * 32 + lane;
+        d[idx] = wb[idx + idx / E];
+    }
+    __syncwarp();
+}
+
+template <int E, typename W, typename S>
+__device__ __forceinline__ void warp_load_positions(const S* src, W (&v)[E], W* wbuf) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    W* wb = wbuf + w * 32 * (E + 1);
+    const S* s = src + (size_t)w * 32 * E;
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < E; k++) {
+        const int idx = k * 32 + lane;
+        wb[idx + idx / E] = (W)s[idx];
+    }
+    __syncwarp();
+#pragma unroll
+    for (int e = 0; e < E; e++) v[e] = wb[lane * (E + 1) + e];
+    __syncwarp();
+}
+
 // Single-polynomial forms with 16 residues per thread (utility kernels).
 template <int LOGN>
 __device__ __forceinline__ void ntt_fwd1(u64 (&v)[16], Xchg& xc, const DevCtx& C, int j) {
@@ -399,7 +588,7 @@ __device__ __noinline__ void ext_product(const DevCtx& C, const u64* __restrict_
         const PrimeConst Pj = C.P[j];
         const u64 qj = Pj.q;
         const ulonglong2* rtab =
-            cmux_rot ? C.rot_tab + (((size_t)j * 2 + nt.rot_sign) * C.log_n + nt.rot_t) * N + E * tid
+            cmux_rot ? C.rot_tab + (((size_t)j * 2 + nt.rot_sign) * C.log_n + nt.rot_t) * N + tid
                      : nullptr;
         u64 acc[2][E];
 #pragma unroll
@@ -409,24 +598,19 @@ __device__ __noinline__ void ext_product(const DevCtx& C, const u64* __restrict_
 #pragma unroll
             for (int comp = 0; comp < 2; comp++) {
                 const int row = comp == 1 ? j : C.dnum + j;
-                const u64* sn = nt.src_ntt + ((size_t)comp * r + j) * N + E * tid;
-                const ulonglong2* Ra =
-                    (const ulonglong2*)(rgsw + ((size_t)(row * 2 + 0) * r + j) * N + E * tid);
-                const ulonglong2* Rb =
-                    (const ulonglong2*)(rgsw + ((size_t)(row * 2 + 1) * r + j) * N + E * tid);
+                const u64* sn = nt.src_ntt + ((size_t)comp * r + j) * N + tid;
+                const u64* Ra = rgsw + ((size_t)(row * 2 + 0) * r + j) * N + tid;
+                const u64* Rb = rgsw + ((size_t)(row * 2 + 1) * r + j) * N + tid;
 #pragma unroll
-                for (int h = 0; h < E / 2; h++) {
-                    const ulonglong2 ra = __ldg(Ra + h), rb = __ldg(Rb + h);
-                    u64 x0 = sn[2 * h], x1 = sn[2 * h + 1];
+                for (int e = 0; e < E; e++) {
+                    const u64 ra = __ldg(Ra + e * T), rb = __ldg(Rb + e * T);
+                    u64 x = sn[e * T];
                     if (cmux_rot) {
-                        const ulonglong2 t0 = __ldg(rtab + 2 * h), t1 = __ldg(rtab + 2 * h + 1);
-                        x0 = shoup_mul_lazy(x0, t0.x, t0.y, qj);
-                        x1 = shoup_mul_lazy(x1, t1.x, t1.y, qj);
+                        const ulonglong2 t0 = __ldg(rtab + e * T);
+                        x = shoup_mul_lazy(x, t0.x, t0.y, qj);
                     }
-                    acc[0][2 * h] += redc_lazy(__umul64hi(x0, ra.x), x0 * ra.x, qj, Pj.qneg);
-                    acc[0][2 * h + 1] += redc_lazy(__umul64hi(x1, ra.y), x1 * ra.y, qj, Pj.qneg);
-                    acc[1][2 * h] += redc_lazy(__umul64hi(x0, rb.x), x0 * rb.x, qj, Pj.qneg);
-                    acc[1][2 * h + 1] += redc_lazy(__umul64hi(x1, rb.y), x1 * rb.y, qj, Pj.qneg);
+                    acc[0][e] += redc_lazy(__umul64hi(x, ra), x * ra, qj, Pj.qneg);
+                    acc[1][e] += redc_lazy(__umul64hi(x, rb), x * rb, qj, Pj.qneg);
                 }
             }
         }
@@ -464,28 +648,24 @@ __device__ __noinline__ void ext_product(const DevCtx& C, const u64* __restrict_
             for (int pp = 0; pp < NP; pp++) {
                 const int comp = comps[pp], rho = rhos[pp];
                 const int row = comp == 1 ? rho : C.dnum + rho;
-                const ulonglong2* Ra =
-                    (const ulonglong2*)(rgsw + ((size_t)(row * 2 + 0) * r + j) * N + E * tid);
-                const ulonglong2* Rb =
-                    (const ulonglong2*)(rgsw + ((size_t)(row * 2 + 1) * r + j) * N + E * tid);
+                const u64* Ra = rgsw + ((size_t)(row * 2 + 0) * r + j) * N + tid;
+                const u64* Rb = rgsw + ((size_t)(row * 2 + 1) * r + j) * N + tid;
 #pragma unroll
-                for (int h = 0; h < E / 2; h++) {
-                    const ulonglong2 ra = __ldg(Ra + h), rb = __ldg(Rb + h);
-                    const u64 x0 = v[pp][2 * h], x1 = v[pp][2 * h + 1];
-                    acc[0][2 * h] += redc_lazy(__umul64hi(x0, ra.x), x0 * ra.x, qj, Pj.qneg);
-                    acc[0][2 * h + 1] += redc_lazy(__umul64hi(x1, ra.y), x1 * ra.y, qj, Pj.qneg);
-                    acc[1][2 * h] += redc_lazy(__umul64hi(x0, rb.x), x0 * rb.x, qj, Pj.qneg);
-                    acc[1][2 * h + 1] += redc_lazy(__umul64hi(x1, rb.y), x1 * rb.y, qj, Pj.qneg);
+                for (int e = 0; e < E; e++) {
+                    const u64 ra = __ldg(Ra + e * T), rb = __ldg(Rb + e * T);
+                    const u64 x = v[pp][e];
+                    acc[0][e] += redc_lazy(__umul64hi(x, ra), x * ra, qj, Pj.qneg);
+                    acc[1][e] += redc_lazy(__umul64hi(x, rb), x * rb, qj, Pj.qneg);
                 }
                 if (derive_base && rho == j) {
                     // the base's evaluation form: D_j / (Psi^(+-2^t) - 1)
                     const ulonglong2* ri =
-                        C.rot_inv + (((size_t)j * 2 + nt.rot_sign) * C.log_n + nt.rot_t) * N + E * tid;
-                    u64* bn = nt.dst_ntt + ((size_t)comp * r + j) * N + E * tid;
+                        C.rot_inv + (((size_t)j * 2 + nt.rot_sign) * C.log_n + nt.rot_t) * N + tid;
+                    u64* bn = nt.dst_ntt + ((size_t)comp * r + j) * N + tid;
 #pragma unroll
                     for (int e = 0; e < E; e++) {
-                        const ulonglong2 w = __ldg(ri + e);
-                        bn[e] = shoup_mul_lazy(v[pp][e], w.x, w.y, qj);
+                        const ulonglong2 w = __ldg(ri + e * T);
+                        bn[e * T] = shoup_mul_lazy(v[pp][e], w.x, w.y, qj);
                     }
                 }
             }
@@ -494,14 +674,13 @@ __device__ __noinline__ void ext_product(const DevCtx& C, const u64* __restrict_
             // evaluation form of the output: (base +) C [x] D, fully reduced
 #pragma unroll
             for (int oc = 0; oc < 2; oc++) {
-                u64* dn = nt.dst_ntt + ((size_t)oc * r + j) * N + E * tid;
+                u64* dn = nt.dst_ntt + ((size_t)oc * r + j) * N + tid;
                 const u64* bn = derive_base ? dn
-                                : (base_given ? nt.src_ntt + ((size_t)oc * r + j) * N + E * tid
-                                              : nullptr);
+                                : (base_given ? nt.src_ntt + ((size_t)oc * r + j) * N + tid : nullptr);
 #pragma unroll
                 for (int e = 0; e < E; e++) {
-                    u64 val = acc[oc][e] + (bn ? bn[e] : 0);
-                    dn[e] = reduce64(val, Pj);
+                    u64 val = acc[oc][e] + (bn ? bn[e * T] : 0);
+                    dn[e * T] = reduce64(val, Pj);
                 }
             }
         }
@@ -556,7 +735,7 @@ __device__ __noinline__ void ext_product(const DevCtx& C, const u64* __restrict_
 // one polynomial at N = 8192 (1024-thread blocks would leave 64 registers).
 template <int LOGN>
 struct ExtCfg {
-    static constexpr int LOGE = LOGN >= 13 ? 4 : 3;
+    static constexpr int LOGE = ext_loge(LOGN);
     static constexpr int NP = LOGN >= 13 ? 1 : 2;
     static constexpr int T = Ring<LOGN, LOGE>::T;
     static constexpr int MINB = (512 / T) > 16 ? 16 : ((512 / T) < 1 ? 1 : (512 / T));

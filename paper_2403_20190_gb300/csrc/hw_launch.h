@@ -12,6 +12,7 @@ struct LaunchInfo {
     int log_n, n, r, k0, k1, n_classes, n_data, n_slots, L, dnum;
     size_t rlwe_words, lwe_words, rgsw_words, sample_words, model_words;
     int sm_count;
+    int small_q;  // every q_i < 2^30: the 32-bit transform tables exist
     unsigned long long* launches;  // launch counter
 };
 

@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(Geo<LOGN>::T) k_keygen(const DevCtx* __restric
     ntt_fwd1<LOGN>(v, xc, C, j);
 #pragma unroll
     for (int e = 0; e < 16; e++)
-        key[(size_t)(C.r + j) * N + 16 * tid + e] = to_mont(reduce_full(v[e], P), P);
+        key[(size_t)(C.r + j) * N + eval_addr(16 * tid + e, LOGN)] = to_mont(reduce_full(v[e], P), P);
 }
 
 // ---------------------------------------------------------------------------
@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(ExtCfg<LOGN>::T, ExtCfg<LOGN>::MINB)
         u64* db = dst_row + (size_t)(1 * r + j) * N;
 #pragma unroll
         for (int e = 0; e < E; e++) {
-            const int pos = E * tid + e;
+            const int pos = e * T + tid;  // evaluation position E*tid + e, thread-major
             u64 a = reduce_full(v[0][e], P);
             u64 b = add_mod(mont_mul(a, sM[pos], P), reduce_full(v[1][e], P), q);
             // the evaluation form of the constant polynomial g is g everywhere
@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(Geo<LOGN>::T)
     ntt_fwd1<LOGN>(v, xc, C, j);
 #pragma unroll
     for (int e = 0; e < 16; e++)
-        v[e] = shoup_mul_lazy(mont_mul(v[e], key[(size_t)(r + j) * N + 16 * tid + e], P), C.n_inv[j],
+        v[e] = shoup_mul_lazy(mont_mul(v[e], key[(size_t)(r + j) * N + eval_addr(16 * tid + e, LOGN)], P), C.n_inv[j],
                               C.n_inv_s[j], P.q);
     ntt_inv1<LOGN>(v, xc, C, j);
     u64* dst = ph + (t * r + j) * N;
@@ -384,7 +384,8 @@ __global__ void __launch_bounds__(Geo<LOGN>::T)
     u64 v[16];
 #pragma unroll
     for (int e = 0; e < 16; e++)
-        v[e] = shoup_mul_lazy(from_mont(in[poly * N + 16 * tid + e], P), C.n_inv[j], C.n_inv_s[j], P.q);
+        v[e] = shoup_mul_lazy(from_mont(in[poly * N + eval_addr(16 * tid + e, LOGN)], P), C.n_inv[j],
+                              C.n_inv_s[j], P.q);
     ntt_inv1<LOGN>(v, xc, C, j);
 #pragma unroll
     for (int kk = 0; kk < 16; kk++) out[poly * N + tid + kk * T] = v[kk] >= P.q ? v[kk] - P.q : v[kk];
@@ -405,20 +406,85 @@ __global__ void __launch_bounds__(Geo<LOGN>::T)
     const PrimeConst P = C.P[j];
     u64* p = poly + t * N;
     u64 v[16];
-    // every read happens before the first exchange barrier, every write
-    // after the last one, so the transform can run in place
+    // Positions 16*tid + e go through warp transposes so global accesses are
+    // coalesced: the store uses the exchange buffer the last exchange did
+    // not (read two exchanges ago, before a barrier); the load uses b1 and
+    // the transform's first exchange then takes b0.  Every global read
+    // precedes the first barrier and every write follows the last one, so
+    // the transform runs in place.
     if (!inverse) {
 #pragma unroll
         for (int kk = 0; kk < 16; kk++) v[kk] = p[tid + kk * T];
         ntt_fwd1<LOGN>(v, xc, C, j);
 #pragma unroll
-        for (int e = 0; e < 16; e++) p[16 * tid + e] = reduce_full(v[e], P);
-    } else {
+        for (int e = 0; e < 16; e++) v[e] = reduce_full(v[e], P);
+        if constexpr (T >= 32) {
+            warp_store_positions<16>(p, v, xc.next());
+        } else {
 #pragma unroll
-        for (int e = 0; e < 16; e++) v[e] = shoup_mul_lazy(p[16 * tid + e], C.n_inv[j], C.n_inv_s[j], P.q);
+            for (int e = 0; e < 16; e++) p[16 * tid + e] = v[e];
+        }
+    } else {
+        if constexpr (T >= 32) {
+            warp_load_positions<16>(p, v, xc.b1);
+        } else {
+#pragma unroll
+            for (int e = 0; e < 16; e++) v[e] = p[16 * tid + e];
+        }
+#pragma unroll
+        for (int e = 0; e < 16; e++) v[e] = shoup_mul_lazy(v[e], C.n_inv[j], C.n_inv_s[j], P.q);
         ntt_inv1<LOGN>(v, xc, C, j);
 #pragma unroll
         for (int kk = 0; kk < 16; kk++) p[tid + kk * T] = v[kk] >= P.q ? v[kk] - P.q : v[kk];
+    }
+}
+
+// The same batched transform in 32-bit arithmetic (every q_i < 2^30): same
+// evaluation order and results, about a third of the integer instructions.
+template <int LOGN>
+__global__ void __launch_bounds__(Ring<LOGN>::T)
+    k_ntt_batch32(const DevCtx* __restrict__ Cp, u64* __restrict__ poly, int inverse) {
+    extern __shared__ u64 smem[];
+    constexpr int N = Ring<LOGN>::N, T = Ring<LOGN>::T, PD = Ring<LOGN>::PADDED;
+    // 32-bit exchanges use the first half of each 64-bit buffer; the warp
+    // transposes stage 64-bit words in a whole buffer
+    Xchg xc{smem, smem + PD, PD, 0};
+    const DevCtx& C = *Cp;
+    const int tid = threadIdx.x;
+    const size_t t = blockIdx.x;
+    const int j = (int)(t % C.r);
+    const u32 q = (u32)C.P[j].q, q2 = 2 * q;
+    u64* p = poly + t * N;
+    u32 v[1][16];
+    if (!inverse) {
+#pragma unroll
+        for (int kk = 0; kk < 16; kk++) v[0][kk] = (u32)p[tid + kk * T];
+        fwd_from32<LOGN, 4, 1, 0>(v, xc, C.tw32_fwd + (size_t)j * N, q, q2);
+        u64 o[16];
+#pragma unroll
+        for (int e = 0; e < 16; e++) {
+            u32 x = v[0][e] >= q2 ? v[0][e] - q2 : v[0][e];
+            o[e] = x >= q ? x - q : x;
+        }
+        if constexpr (T >= 32) {
+            warp_store_positions<16>(p, o, xc.next());
+        } else {
+#pragma unroll
+            for (int e = 0; e < 16; e++) p[16 * tid + e] = o[e];
+        }
+    } else {
+        u64 o[16];
+        if constexpr (T >= 32) {
+            warp_load_positions<16>(p, o, xc.b1);
+        } else {
+#pragma unroll
+            for (int e = 0; e < 16; e++) o[e] = p[16 * tid + e];
+        }
+#pragma unroll
+        for (int e = 0; e < 16; e++) v[0][e] = shoup32_lazy((u32)o[e], C.n_inv32[j], C.n_inv32_s[j], q);
+        inv_from32<LOGN, 4, 1, 0>(v, xc, C.tw32_inv + (size_t)j * N, q, q2);
+#pragma unroll
+        for (int kk = 0; kk < 16; kk++) p[tid + kk * T] = v[0][kk] >= q ? v[0][kk] - q : v[0][kk];
     }
 }
 
@@ -534,6 +600,16 @@ cudaError_t launch_export_rgsw(const LaunchInfo& li, const uint64_t* rgsw, size_
 cudaError_t launch_ntt_batch(const LaunchInfo& li, uint64_t* poly, size_t count, int inverse,
                              cudaStream_t st) {
     if (count == 0) return cudaSuccess;
+    if (li.small_q) {
+#define B(L)                                                                                  \
+    case L:                                                                                   \
+        k_ntt_batch32<L><<<(unsigned)count, Geo<L>::T, Geo<L>::XCHG_BYTES, st>>>(li.dctx, poly, \
+                                                                               inverse);      \
+        break;
+        HW_DISPATCH(li.log_n, B)
+#undef B
+        return HW_LAUNCHED();
+    }
 #define B(L)                                                                                       \
     case L:                                                                                        \
         k_ntt_batch<L><<<(unsigned)count, Geo<L>::T, Geo<L>::XCHG_BYTES, st>>>(li.dctx, poly, inverse); \
@@ -555,7 +631,8 @@ cudaError_t hw_kernels_init(int log_n) {
     A(k_encrypt, L, encrypt_smem<L>())                \
     A(k_rlwe_phase, L, Geo<L>::XCHG_BYTES)            \
     A(k_export_rgsw, L, Geo<L>::XCHG_BYTES)           \
-    A(k_ntt_batch, L, Geo<L>::XCHG_BYTES)
+    A(k_ntt_batch, L, Geo<L>::XCHG_BYTES)            \
+    A(k_ntt_batch32, L, Geo<L>::XCHG_BYTES)
     HW_FOR_EACH_LOGN(X)
 #undef X
 #undef A

@@ -139,6 +139,50 @@ def test_ntt_roundtrip_and_edge_values():
     assert np.array_equal(u64(dev).reshape(count, n), x)
 
 
+def _library_root(q, log_n):
+    """The library's documented root choice: psi = x^((q-1)/2N) for the
+    first odd x >= 3 with psi^N = -1."""
+    n = 1 << log_n
+    x = 3
+    while True:
+        psi = pow(x, (q - 1) // (2 * n), q)
+        if pow(psi, n, q) == q - 1:
+            return psi
+        x += 2
+
+
+@pytest.mark.parametrize("name", ["cfg1", "cfg2", "cfg4"])
+def test_ntt_is_evaluation_at_odd_powers(name):
+    """The batched forward transform (32-bit arithmetic for cfg1's 30-bit
+    prime, 64-bit otherwise) puts a(psi^(2 brv(pos) + 1)) at position pos."""
+    from paper_2403_20190_gb300 import binding as B
+    cfg = get_config(name)
+    sess = session(cfg)
+    sz = sess.sz
+    n, r, log_n = sz["n"], sz["r"], cfg.log_n
+    rng = np.random.default_rng(1)
+    x = np.zeros((r, n), dtype=np.uint64)
+    for j in range(r):
+        x[j] = rng.integers(0, sz["q"][j], size=n, dtype=np.uint64)
+    dev = torch.from_numpy(x.view(np.int64).copy()).to(sess.device)
+    B.hw_ntt_forward(sess.ctx, dev, r)
+    out = u64(dev).reshape(r, n)
+    for j in range(r):
+        q = sz["q"][j]
+        psi = _library_root(q, log_n)
+        a = [int(v) for v in x[j]]
+        for pos in (0, 1, n // 2 + 3, n - 1):
+            b = int(format(pos, f"0{log_n}b")[::-1], 2)
+            w = pow(psi, 2 * b + 1, q)
+            acc, p = 0, 1
+            for c in a:
+                acc = (acc + c * p) % q
+                p = p * w % q
+            assert int(out[j, pos]) == acc
+    B.hw_ntt_inverse(sess.ctx, dev, r)
+    assert np.array_equal(u64(dev).reshape(r, n), x)
+
+
 @pytest.mark.parametrize("name,n_train,n_test,rams", [
     ("cfg1", 6, 3, [0, 13, 29]),
     ("cfg2", 3, 2, [0, 77, 130]),
