@@ -507,17 +507,23 @@ def serve_leg(args, local):
     models = {nm: ResidentModel(c, local, key_seed=c.key_seed) for nm, c in cfgs.items()}
     reqs = poisson_stream(cfgs, n_requests=args.serve_requests, rate=200.0, seed=2024,
                           max_samples=SERVE_MAX)
+    from paper_2403_20190_gb300.arena import DeviceArena
     budget = 120 << 30
+    arena = DeviceArena(budget, torch.device("cuda", local))  # shared by both modes
     warm = copy.deepcopy(reqs[:4])
-    Server(models, budget).run(warm, realtime=False)
+    Server(models, arena=arena).run(warm, realtime=False)
     base = copy.deepcopy(reqs)
-    batched = Server(models, budget, n_streams=4).run(copy.deepcopy(reqs), realtime=True)
-    alone = Server(models, budget).run_one_at_a_time(base)
+    srv = Server(models, n_streams=2, arena=arena)
+    costs = srv.calibrate()  # startup, outside both timed runs
+    batched = srv.run(copy.deepcopy(reqs), realtime=True)
+    alone = Server(models, arena=arena).run_one_at_a_time(base)
     out = {"requests": len(reqs), "rate_per_s": 200.0, "hbm_budget_gb": budget / 2**30,
            "batched": latency_stats(batched), "one_at_a_time": latency_stats(alone),
            "mix": {nm: sum(1 for r in reqs if r.cfg_name == nm) for nm in cfgs},
+           "policy": "2 streams, shortest expected batch first with aging 1.0, device arena",
+           "calibrated_ms_per_sample": {f"{k[0]}/{k[1]}": round(v * 1e3, 3) for k, v in costs.items()},
            "max_samples_per_request": SERVE_MAX}
-    del models
+    del models, arena
     torch.cuda.empty_cache()
     return out
 

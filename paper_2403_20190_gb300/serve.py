@@ -12,6 +12,19 @@ model per configuration resident in HBM and runs a loop that
   * retires batches whose completion events have fired and records each
     request's latency (arrival to completion).
 
+Memory: every batch takes one chunk of a device arena allocated up front
+(arena.py) and carves its buffers from it, so admission by footprint is
+admission by placement and the loop never calls the CUDA allocator.
+
+Order: among pending requests the server launches the group with the least
+expected GPU time, less the age of its oldest request (shortest expected
+batch first with aging, so no request waits forever).  Expected times are
+per-sample costs per (configuration, kind): calibrate() times one
+single-sample batch of each alone, and batches that ran with nothing else
+on the GPU refine them (a batch that overlapped others is slowed by them
+and says little about its own cost); before any measurement they come from
+the encrypted-sample size.
+
 Semantics within a serving window: inference requests answer with the model
 as it stood when the window opened; training requests accumulate into a
 per-model delta that is added into the model when the window closes.
@@ -20,6 +33,7 @@ samples and seed), never on what it was batched with, and the closing model
 equals sequential training of all train requests (addition mod q commutes).
 """
 import collections
+import copy
 import time
 from dataclasses import dataclass, field
 
@@ -27,6 +41,7 @@ import numpy as np
 import torch
 
 from . import binding as B
+from .arena import DeviceArena, align_up
 from .merge import add_models
 from .session import Session
 
@@ -60,17 +75,35 @@ class ResidentModel:
     def per_sample_bytes(self):
         return self.sess.sz["sample_words"] * 8
 
+    def layout(self, kind, n):
+        """The buffers one batch of n samples holds while in flight, in the
+        order they are carved: (name, element count, dtype)."""
+        sz, l = self.sess.sz, self.cfg.n_classes
+        out = [("values", n * self.cfg.n_values, torch.uint8),
+               ("bits", n * sz["n_data"], torch.uint8),
+               ("rgsw", n * sz["sample_words"], torch.int64)]
+        if kind == "train":
+            out += [("labels", n, torch.int32),
+                    ("scratch", B.hw_train_scratch_words(self.sess.ctx, n), torch.int64)]
+        else:
+            out += [("resp", n * sz["resp_words"], torch.int64),
+                    ("sums", n * sz["sums_words"], torch.int64),
+                    ("scratch", B.hw_infer_scratch_words(self.sess.ctx, n), torch.int64),
+                    ("counts", n * l * sz["k0"], torch.int64),
+                    ("scores", n * l, torch.int64),
+                    ("labels_out", n, torch.int32)]
+        return out
+
     def footprint(self, kind, n):
         """Device bytes one batch of n samples holds while in flight."""
-        sz = self.sess.sz
-        b = n * sz["sample_words"] * 8 + n * sz["n_data"]
-        if kind == "train":
-            b += B.hw_train_scratch_words(self.sess.ctx, n) * 8
-        else:
-            b += n * (sz["resp_words"] + sz["sums_words"]) * 8
-            b += B.hw_infer_scratch_words(self.sess.ctx, n) * 8
-            b += n * self.cfg.n_classes * (sz["k0"] + 1) * 8 + n * 4
-        return b
+        return sum(align_up(c * torch.empty((), dtype=d).element_size()) for _, c, d in self.layout(kind, n))
+
+    def prior_cost(self, kind):
+        """Expected GPU seconds per sample before any measurement: encrypted
+        bytes over an assumed 1 GB/s of external-product throughput, times
+        the class count for inference."""
+        c = self.sess.sz["sample_words"] * 8 / 1e9
+        return c * (self.cfg.n_classes if kind == "infer" else 1)
 
     def close_window(self):
         q, n = self.sess.sz["q"], self.sess.sz["n"]
@@ -79,126 +112,166 @@ class ResidentModel:
 
 
 class _Batch:
-    def __init__(self, rm, kind, reqs, stream, footprint):
-        self.rm, self.kind, self.reqs, self.stream, self.footprint = rm, kind, reqs, stream, footprint
-        self.event = torch.cuda.Event()
-        self.keep = []  # buffers alive until the batch retires
+    def __init__(self, rm, kind, reqs, stream, chunk):
+        self.rm, self.kind, self.reqs, self.stream, self.chunk = rm, kind, reqs, stream, chunk
+        self.start = torch.cuda.Event(enable_timing=True)
+        self.event = torch.cuda.Event(enable_timing=True)
+        self.bufs = {}
+        self.solo = True  # nothing else ran on the GPU during its lifetime
 
 
 class Server:
-    def __init__(self, models: dict, hbm_budget_bytes: int, n_streams: int = 4,
-                 max_batch_samples: int = 256, keep_responses: bool = False):
+    def __init__(self, models: dict, hbm_budget_bytes: int = None, n_streams: int = 2,
+                 max_batch_samples: int = 256, keep_responses: bool = False, arena=None,
+                 aging: float = 1.0):
+        """models: name -> ResidentModel.  The arena (or a new one of
+        hbm_budget_bytes on the models' device) holds every batch in flight."""
         self.models = models
-        self.budget = hbm_budget_bytes
-        self.free = hbm_budget_bytes
+        if arena is None:
+            dev = next(iter(models.values())).sess.device
+            arena = DeviceArena(hbm_budget_bytes, dev)
+        self.arena = arena
+        self.budget = arena.size
         self.streams = [torch.cuda.Stream() for _ in range(n_streams)]
         self.max_batch = max_batch_samples
         self.keep_responses = keep_responses
+        self.aging = aging
+        self.cost = {}  # (cfg name, kind) -> smoothed GPU seconds per sample
+
+    @property
+    def free(self):
+        return self.arena.free_bytes
 
     # ------------------------------------------------------------------ launch
-    def _launch(self, rm, kind, reqs, stream):
+    def _launch(self, rm, kind, reqs, stream, chunk):
         s = rm.sess
         sz = s.sz
         n = sum(r.n for r in reqs)
-        b = _Batch(rm, kind, reqs, stream, rm.footprint(kind, n))
+        b = _Batch(rm, kind, reqs, stream, chunk)
+        buf = b.bufs
+        for name, count, dtype in rm.layout(kind, n):
+            buf[name] = chunk.take(count, dtype)
         with torch.cuda.stream(stream):
-            rgsw = s.words(n * sz["sample_words"], zero=False)
-            b.keep.append(rgsw)
+            b.start.record(stream)
+            vals = buf["values"].view(n, rm.cfg.n_values)
             off = 0
             for r in reqs:
-                vals = torch.from_numpy(r.values).to(s.device, non_blocking=False)
-                bits = torch.empty((r.n, sz["n_data"]), dtype=torch.uint8, device=s.device)
-                B.hw_encode(s.ctx, vals, r.n, bits, stream)
-                lab = None
+                vals[off:off + r.n].copy_(torch.from_numpy(r.values))
                 if kind == "train":
-                    lab = torch.from_numpy(r.labels.astype(np.int32)).to(s.device)
-                    b.keep.append(lab)
-                dst = rgsw[off * sz["sample_words"]:(off + r.n) * sz["sample_words"]]
+                    buf["labels"][off:off + r.n].copy_(torch.from_numpy(r.labels.astype(np.int32)))
+                off += r.n
+            B.hw_encode(s.ctx, vals, n, buf["bits"], stream)
+            off = 0
+            for r in reqs:
+                w = sz["sample_words"]
                 # each request is encrypted under its own seed, sample indices
                 # counted from 0, whatever it is batched with
-                B.hw_encrypt_sample(s.ctx, rm.key, bits, lab, r.n, r.seed, 0, dst, stream)
-                b.keep += [vals, bits]
+                lab = buf["labels"][off:off + r.n] if kind == "train" else None
+                B.hw_encrypt_sample(s.ctx, rm.key, buf["bits"][off * sz["n_data"]:], lab, r.n, r.seed, 0,
+                                    buf["rgsw"][off * w:(off + r.n) * w], stream)
                 off += r.n
             if kind == "train":
-                scratch = s.words(B.hw_train_scratch_words(s.ctx, n), zero=False)
-                B.hw_train_accumulate(s.ctx, rm.delta, rgsw, n, scratch, stream)
-                b.keep.append(scratch)
+                B.hw_train_accumulate(s.ctx, rm.delta, buf["rgsw"], n, buf["scratch"], stream)
             else:
-                resp, sums, scr = s.infer_buffers(n)
-                B.hw_infer(s.ctx, rm.model, rgsw, n, resp, sums, scr, stream)
+                B.hw_infer(s.ctx, rm.model, buf["rgsw"], n, buf["resp"], buf["sums"], buf["scratch"], stream)
                 l, k0 = rm.cfg.n_classes, sz["k0"]
-                counts = torch.empty(n * l * k0, dtype=torch.int64, device=s.device)
-                B.hw_decrypt(s.ctx, rm.key, B.HW_DEC_LWE, resp, n * l * k0, counts, stream)
-                scores = torch.empty(n * l, dtype=torch.int64, device=s.device)
-                labels = torch.empty(n, dtype=torch.int32, device=s.device)
-                B.hw_pdact(s.ctx, counts, n, scores, labels, stream)
-                b.keep += [resp, sums, scr, counts, scores]
-                b.labels = labels
-                b.resp = resp
+                B.hw_decrypt(s.ctx, rm.key, B.HW_DEC_LWE, buf["resp"], n * l * k0, buf["counts"], stream)
+                B.hw_pdact(s.ctx, buf["counts"], n, buf["scores"], buf["labels_out"], stream)
             b.event.record(stream)
         return b
 
     def _retire(self, b, now):
         if b.kind == "infer":
-            lab = b.labels.cpu().numpy()
+            lab = b.bufs["labels_out"].cpu().numpy()
             off = 0
             for r in b.reqs:
                 r.labels_out = lab[off:off + r.n].copy()
                 if self.keep_responses:
                     rw = b.rm.sess.sz["resp_words"]
-                    r.resp = b.resp[off * rw:(off + r.n) * rw].clone()
+                    r.resp = b.bufs["resp"][off * rw:(off + r.n) * rw].clone()
                 off += r.n
         for r in b.reqs:
             r.t_done = now
-        self.free += b.footprint
-        b.keep.clear()
+        if b.solo:
+            n = sum(r.n for r in b.reqs)
+            key = (b.rm.cfg.name, b.kind)
+            per = b.start.elapsed_time(b.event) / 1e3 / n
+            self.cost[key] = per if key not in self.cost else 0.5 * self.cost[key] + 0.5 * per
+        b.bufs.clear()
+        self.arena.release(b.chunk)
+
+    def expected(self, rm, kind, n):
+        """Expected GPU seconds of a batch of n samples."""
+        per = self.cost.get((rm.cfg.name, kind))
+        return n * (per if per is not None else rm.prior_cost(kind))
+
+    def _groups(self, pending):
+        """Candidate batches: per (configuration, kind), pending requests in
+        arrival order up to the batch limit."""
+        groups = {}
+        for r in pending:
+            key = (r.cfg_name, r.kind)
+            g = groups.setdefault(key, [[], 0])
+            if g[1] + r.n > self.max_batch and g[0]:
+                continue
+            g[0].append(r)
+            g[1] += r.n
+        return groups
 
     # -------------------------------------------------------------------- loop
     def run(self, requests, realtime=True):
-        """Serve the requests (sorted by arrival); returns them completed.
-        With realtime, a request is only visible once its arrival time has
-        passed on the wall clock."""
+        """Serve the requests; returns them completed.  With realtime, a
+        request is only visible once its arrival time has passed on the wall
+        clock."""
         reqs = sorted(requests, key=lambda r: r.t_arrive)
         for r in reqs:
             if self.models[r.cfg_name].footprint(r.kind, r.n) > self.budget:
                 raise ValueError(f"request {r.rid} can never fit the HBM budget")
         arrivals = collections.deque(reqs)
-        pending = collections.deque()
+        pending = []
         inflight = []
         t0 = time.perf_counter()
         while arrivals or pending or inflight:
             now = time.perf_counter() - t0
             while arrivals and (not realtime or arrivals[0].t_arrive <= now):
                 pending.append(arrivals.popleft())
-            # retire finished batches
             for b in [b for b in inflight if b.event.query()]:
                 inflight.remove(b)
                 self._retire(b, time.perf_counter() - t0)
-            # admit: the oldest pending request picks the (config, kind); every
-            # pending request of that kind that fits joins its batch
             busy = {id(b.stream) for b in inflight}
             free_streams = [s for s in self.streams if id(s) not in busy]
             launched = False
             while pending and free_streams:
-                head = pending[0]
-                rm = self.models[head.cfg_name]
-                group, n = [], 0
-                for r in list(pending):
-                    if r.cfg_name != head.cfg_name or r.kind != head.kind:
-                        continue
-                    if n + r.n > self.max_batch and group:
-                        continue
-                    if rm.footprint(r.kind, n + r.n) > self.free:
-                        continue
-                    group.append(r)
-                    n += r.n
-                if not group:
-                    break  # the head waits for memory
+                now = time.perf_counter() - t0
+                ranked = []
+                for (nm, kind), (group, n) in self._groups(pending).items():
+                    rm = self.models[nm]
+                    oldest = min(r.t_arrive for r in group)
+                    score = self.expected(rm, kind, n) - self.aging * (now - oldest)
+                    ranked.append((score, oldest, nm, kind, group))
+                ranked.sort(key=lambda x: (x[0], x[1]))
+                placed = None
+                for _, _, nm, kind, group in ranked:
+                    rm = self.models[nm]
+                    # shrink the group (newest first) until it can be placed
+                    while group:
+                        chunk = self.arena.alloc(rm.footprint(kind, sum(r.n for r in group)))
+                        if chunk is not None:
+                            placed = (rm, kind, group, chunk)
+                            break
+                        group = group[:-1]
+                    if placed:
+                        break
+                if placed is None:
+                    break  # everything waits for memory
+                rm, kind, group, chunk = placed
                 for r in group:
                     pending.remove(r)
-                fp = rm.footprint(head.kind, n)
-                self.free -= fp
-                inflight.append(self._launch(rm, head.kind, group, free_streams.pop(0)))
+                for o in inflight:
+                    o.solo = False
+                b = self._launch(rm, kind, group, free_streams.pop(0), chunk)
+                b.solo = not inflight
+                inflight.append(b)
                 launched = True
             if not launched and not any(b.event.query() for b in inflight):
                 if inflight:
@@ -207,6 +280,35 @@ class Server:
                     time.sleep(max(0.0, min(0.002, arrivals[0].t_arrive - now)))
         torch.cuda.synchronize()
         return reqs
+
+    def calibrate(self, kinds=("train", "infer")):
+        """Time one single-sample batch of every (model, kind) alone and take
+        it as the expected per-sample cost.  Training runs into a temporary
+        delta from the arena, so the resident models do not change."""
+        for nm, rm in self.models.items():
+            cfg = rm.cfg
+            for kind in kinds:
+                req = Request(rid=-1, t_arrive=0.0, cfg_name=nm, kind=kind,
+                              values=np.zeros((1, cfg.n_values), dtype=np.uint8),
+                              labels=np.zeros(1, dtype=np.int64) if kind == "train" else None, seed=1)
+                target, tmp = rm, None
+                if kind == "train":
+                    tmp = self.arena.alloc(rm.sess.sz["model_words"] * 8)
+                    if tmp is None:
+                        continue
+                    target = copy.copy(rm)
+                    target.delta = tmp.take(rm.sess.sz["model_words"], torch.int64)
+                chunk = self.arena.alloc(rm.footprint(kind, 1))
+                if chunk is None:
+                    if tmp is not None:
+                        self.arena.release(tmp)
+                    continue
+                b = self._launch(target, kind, [req], self.streams[0], chunk)
+                b.event.synchronize()
+                self._retire(b, 0.0)
+                if tmp is not None:
+                    self.arena.release(tmp)
+        return dict(self.cost)
 
     def run_one_at_a_time(self, requests):
         """Baseline: requests in arrival order, each alone, one stream, each
@@ -217,10 +319,13 @@ class Server:
             now = time.perf_counter() - t0
             if r.t_arrive > now:
                 time.sleep(r.t_arrive - now)
-            b = self._launch(self.models[r.cfg_name], r.kind, [r], self.streams[0])
+            rm = self.models[r.cfg_name]
+            chunk = self.arena.alloc(rm.footprint(r.kind, r.n))
+            if chunk is None:
+                raise ValueError(f"request {r.rid} can never fit the HBM budget")
+            b = self._launch(rm, r.kind, [r], self.streams[0], chunk)
             b.event.synchronize()
             self._retire(b, time.perf_counter() - t0)
-            self.free = self.budget
         return reqs
 
 

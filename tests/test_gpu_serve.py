@@ -70,6 +70,8 @@ def test_alone_equals_in_the_mix():
     batched = sum(1 for r in done if r.kind == "infer")
     assert batched > 0 and any(r.kind == "train" for r in done)
 
+    from paper_2403_20190_gb300.arena import DeviceArena
+    arena = DeviceArena(8 << 30, torch.device("cuda", 0))
     alone_models = _models(cfgs, pretrain=False)
     for nm in cfgs:
         alone_models[nm].model.copy_(base[nm])
@@ -77,7 +79,7 @@ def test_alone_equals_in_the_mix():
     for r in done:
         rm = alone_models[r.cfg_name]
         rm.delta.zero_()
-        srv1 = Server(alone_models, hbm_budget_bytes=8 << 30, n_streams=1, keep_responses=True)
+        srv1 = Server(alone_models, n_streams=1, keep_responses=True, arena=arena)
         import copy
         r1 = copy.copy(r)
         r1.t_done = r1.labels_out = r1.resp = None
@@ -112,7 +114,7 @@ def test_admission_respects_the_budget():
             for i in range(3)]
     srv.run(reqs, realtime=False)
     assert all(r.t_done is not None for r in reqs)
-    assert srv.free == srv.budget
+    assert srv.free == srv.budget and not srv.arena.fl.used
     with pytest.raises(ValueError):
         Server(models, hbm_budget_bytes=one - 1).run(
             [Request(rid=9, t_arrive=0.0, cfg_name="cfg1", kind="train", values=v, labels=lab, seed=1)],
