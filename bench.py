@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--no-ntt", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=40)
+    ap.add_argument("--geometry", default="auto", choices=["auto", "default"],
+                    help="kernel geometry: autotuned (cached per GPU and parameters) or the library default")
     return ap.parse_args()
 
 
@@ -255,7 +257,16 @@ def gpu_arm(args, ws, rank, local, pg):
     libbuild.build()
     torch.cuda.set_device(local)
     cfg = get_config(args.config)
-    sess = Session(cfg, local)
+    tune = None
+    geometry = None
+    if args.geometry == "auto":
+        from paper_2403_20190_gb300.tuning import tuned_geometry
+        t0 = time.perf_counter()
+        geometry, entries, cached = tuned_geometry(cfg, local)
+        tune = {"cached": cached, "seconds": round(time.perf_counter() - t0, 2), "candidates": entries}
+    sess = Session(cfg, local, geometry=geometry)
+    if tune is not None:
+        tune["chosen"] = sess.geometry
     dev = sess.device
     bsz = args.batch or DEFAULT_BATCH.get(args.config, 16)
     sz = sess.sz
@@ -416,12 +427,14 @@ def gpu_arm(args, ws, rank, local, pg):
             t = e0.elapsed_time(e1) / reps / 1000.0
             gbs = 2.0 * count * nn * 8 / t / 1e9
             del polys
+            g = ctx_sess.geometry
             return {"gbs": gbs, "frac_of_hbm": gbs / pk["hbm_gbs"], "polys": count, "n": nn,
-                    "prime_bits": ctx_sess.cfg.prime_bits, "ms_per_launch": t * 1000.0}
+                    "prime_bits": ctx_sess.cfg.prime_bits, "ms_per_launch": t * 1000.0,
+                    "variant": f"radix {1 << g['ntt_loge']}, {32 * g['ntt_limbs']}-bit words"}
         ntt = {"peak_gbs": pk["hbm_gbs"], "peak_kind": pk_kind,
                args.config: ntt_rate(sess, 65536 if sz["n"] <= 4096 else 32768)}
         if args.config != "cfg1":
-            s1 = Session(get_config("cfg1"), local)
+            s1 = Session(get_config("cfg1"), local, geometry="auto" if args.geometry == "auto" else None)
             ntt["cfg1"] = ntt_rate(s1, 262144)
             del s1
 
@@ -477,6 +490,8 @@ def gpu_arm(args, ws, rank, local, pg):
             "phases_ms": ph,
             "roofline": roofline,
             "ntt": ntt,
+            "geometry": sess.geometry,
+            "autotune": tune,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,

@@ -94,6 +94,61 @@ typedef struct hw_sizes {
  * readings of Section 2.4 (Setup) listed with the project's design notes. */
 int hw_create(const hw_params* params, int cuda_device, hw_ctx** out);
 int hw_destroy(hw_ctx* ctx);
+
+/* Kernel geometry of a context.  It has no counterpart in the paper and
+ * changes no result: every geometry produces the same canonical
+ * ciphertexts, models, responses and transforms (only the internal
+ * evaluation layout of RGSW rows and keys follows ext_loge, so those are
+ * valid only within contexts of the same geometry).  0 in a field means the
+ * library's default. */
+typedef struct hw_geometry {
+    int32_t ext_loge;          /* external product: 2^ext_loge residues per thread (radix of the
+                                  in-register transform stages); 3 or 4 */
+    int32_t ext_np;            /* external product: polynomials transformed together per block, 1 or 2 */
+    int32_t ext_blocks_per_sm; /* resident blocks per SM of the persistent training / inference
+                                  kernels; 0 = as many as fit (resolved on return) */
+    int32_t ntt_loge;          /* hw_ntt_forward/inverse: 2^ntt_loge residues per thread; 3 or 4 */
+    int32_t ntt_limbs;         /* hw_ntt_forward/inverse: 32-bit words per residue in the arithmetic:
+                                  1 (only when every q_i < 2^30) or 2 */
+    int32_t reserved[3];
+} hw_geometry;
+
+/* hw_create with a chosen geometry (NULL = defaults).  HW_EINVAL if the
+ * (ext_loge, ext_np) pair is not built for this ring size or a field is
+ * out of range; hw_list_geometries() gives the pairs that are built. */
+int hw_create_tuned(const hw_params* params, const hw_geometry* geometry, int cuda_device,
+                    hw_ctx** out);
+/* The context's geometry with every default resolved. */
+int hw_get_geometry(const hw_ctx* ctx, hw_geometry* out);
+/* The external-product geometries built for params->log_n (ext_loge,
+ * ext_np set; other fields 0), default first.  Host only: needs no GPU.
+ * Writes min(*count, max) entries; *count = the number available. */
+int hw_list_geometries(const hw_params* params, hw_geometry* out_host, size_t max, size_t* count);
+
+/* One measured candidate of hw_autotune (milliseconds; -1 = not measured). */
+typedef struct hw_tune_entry {
+    hw_geometry geometry;
+    double ms_encrypt; /* encrypt n_probe training + n_probe test samples */
+    double ms_train;   /* hw_train_accumulate of n_probe samples */
+    double ms_infer;   /* hw_infer of n_probe samples */
+    double ms_ntt;     /* forward + inverse transform of the probe polynomials */
+    int32_t status;    /* HW_OK, or the error this candidate met */
+    int32_t reserved;
+} hw_tune_entry;
+
+/* Autotuner (no counterpart in the paper): times every built external-
+ * product geometry (and, where it matters, a halved resident-block count)
+ * on one step of n_probe training and n_probe test samples -- encryption,
+ * training, inference -- and every batched-NTT variant on a batch of
+ * polynomials larger than L2, each `reps` times (best time kept), on
+ * synthetic inputs in buffers it allocates and frees itself.  *best gets
+ * the fastest step geometry combined with the fastest NTT variant;
+ * entries_host (may be NULL) gets up to max_entries candidates and
+ * *n_entries their number.  Synchronous; uses the whole GPU while it runs.
+ * HW_ENOMEM if the probe does not fit in device memory. */
+int hw_autotune(const hw_params* params, int cuda_device, size_t n_probe, int32_t reps,
+                hw_geometry* best, hw_tune_entry* entries_host, size_t max_entries,
+                size_t* n_entries);
 int hw_get_sizes(const hw_ctx* ctx, hw_sizes* out);
 /* Host copy of the server's index tables: ram_slot[k0*a] gives, for RAM j and
  * address bit i, the encrypted bit slot it reads (-1: constant 0). */

@@ -35,6 +35,19 @@ class HwSizes(ctypes.Structure):
             "resp_words", "sums_words")]
 
 
+GEOMETRY_FIELDS = ("ext_loge", "ext_np", "ext_blocks_per_sm", "ntt_loge", "ntt_limbs")
+
+
+class HwGeometry(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_int32) for name in GEOMETRY_FIELDS] + [("reserved", ctypes.c_int32 * 3)]
+
+
+class HwTuneEntry(ctypes.Structure):
+    _fields_ = [("geometry", HwGeometry), ("ms_encrypt", ctypes.c_double), ("ms_train", ctypes.c_double),
+                ("ms_infer", ctypes.c_double), ("ms_ntt", ctypes.c_double), ("status", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
 class HwError(RuntimeError):
     pass
 
@@ -44,6 +57,12 @@ _SZ = ctypes.c_size_t
 _U64 = ctypes.c_uint64
 _SIGS = {
     "hw_create": (ctypes.c_int, [ctypes.POINTER(HwParams), ctypes.c_int, ctypes.POINTER(_VP)]),
+    "hw_create_tuned": (ctypes.c_int, [ctypes.POINTER(HwParams), ctypes.POINTER(HwGeometry), ctypes.c_int,
+                                       ctypes.POINTER(_VP)]),
+    "hw_get_geometry": (ctypes.c_int, [_VP, ctypes.POINTER(HwGeometry)]),
+    "hw_list_geometries": (ctypes.c_int, [ctypes.POINTER(HwParams), _VP, _SZ, ctypes.POINTER(_SZ)]),
+    "hw_autotune": (ctypes.c_int, [ctypes.POINTER(HwParams), ctypes.c_int, _SZ, ctypes.c_int32,
+                                   ctypes.POINTER(HwGeometry), _VP, _SZ, ctypes.POINTER(_SZ)]),
     "hw_destroy": (ctypes.c_int, [_VP]),
     "hw_get_sizes": (ctypes.c_int, [_VP, ctypes.POINTER(HwSizes)]),
     "hw_get_ram_slots": (ctypes.c_int, [_VP, _VP, _SZ]),
@@ -136,12 +155,67 @@ def params_from_config(cfg) -> HwParams:
     return p
 
 
+def _params(params):
+    return params if isinstance(params, HwParams) else params_from_config(params)
+
+
+def _geometry(d) -> HwGeometry:
+    g = HwGeometry()
+    for name in GEOMETRY_FIELDS:
+        setattr(g, name, int((d or {}).get(name, 0)))
+    return g
+
+
+def _geometry_dict(g: HwGeometry) -> dict:
+    return {name: int(getattr(g, name)) for name in GEOMETRY_FIELDS}
+
+
 def hw_create(params, device: int = 0) -> Ctx:
-    if not isinstance(params, HwParams):
-        params = params_from_config(params)
     h = _VP()
-    _check(load().hw_create(ctypes.byref(params), device, ctypes.byref(h)), "hw_create")
+    _check(load().hw_create(ctypes.byref(_params(params)), device, ctypes.byref(h)), "hw_create")
     return Ctx(h, device)
+
+
+def hw_create_tuned(params, geometry: dict, device: int = 0) -> Ctx:
+    """geometry: dict with any of GEOMETRY_FIELDS (missing or 0 = default)."""
+    h = _VP()
+    g = _geometry(geometry)
+    _check(load().hw_create_tuned(ctypes.byref(_params(params)), ctypes.byref(g), device, ctypes.byref(h)),
+           "hw_create_tuned")
+    return Ctx(h, device)
+
+
+def hw_get_geometry(ctx) -> dict:
+    g = HwGeometry()
+    _check(load().hw_get_geometry(ctx.handle, ctypes.byref(g)), "hw_get_geometry")
+    return _geometry_dict(g)
+
+
+def hw_list_geometries(params) -> list:
+    p = _params(params)
+    n = _SZ(0)
+    _check(load().hw_list_geometries(ctypes.byref(p), None, 0, ctypes.byref(n)), "hw_list_geometries")
+    buf = (HwGeometry * max(1, n.value))()
+    _check(load().hw_list_geometries(ctypes.byref(p), ctypes.cast(buf, _VP), n.value, ctypes.byref(n)),
+           "hw_list_geometries")
+    return [_geometry_dict(buf[k]) for k in range(n.value)]
+
+
+def hw_autotune(params, device: int = 0, n_probe: int = 4, reps: int = 2):
+    """Returns (best geometry dict, list of measured candidates)."""
+    p = _params(params)
+    best = HwGeometry()
+    cap = 64
+    buf = (HwTuneEntry * cap)()
+    n = _SZ(0)
+    _check(load().hw_autotune(ctypes.byref(p), device, n_probe, reps, ctypes.byref(best), ctypes.cast(buf, _VP),
+                              cap, ctypes.byref(n)), "hw_autotune")
+    entries = []
+    for k in range(min(n.value, cap)):
+        e = buf[k]
+        entries.append(dict(geometry=_geometry_dict(e.geometry), ms_encrypt=e.ms_encrypt, ms_train=e.ms_train,
+                            ms_infer=e.ms_infer, ms_ntt=e.ms_ntt, status=int(e.status)))
+    return _geometry_dict(best), entries
 
 
 def hw_get_sizes(ctx) -> dict:

@@ -48,6 +48,7 @@ struct hw_ctx {
     u64* phase_scratch;   // decryption phases, chunk * r * N words
     size_t phase_chunk;
     LaunchInfo li;
+    hw_geometry geom;     // resolved kernel geometry
     unsigned long long launches;
     std::vector<int32_t> ram_slot;
 };
@@ -139,7 +140,36 @@ static int ilog2_ceil(int l) {
 }
 
 // ------------------------------------------------------------------ create
+// Fills the defaults of a geometry and checks it against what is built.
+static int resolve_geometry(const hw_params* p, const hw_geometry* g, hw_geometry* out) {
+    hw_geometry G;
+    memset(&G, 0, sizeof(G));
+    if (g) G = *g;
+    const int log_n = p->log_n;
+    const bool small_q = p->prime_bits <= 30;
+    if (G.ext_loge == 0) G.ext_loge = default_ext_loge(log_n);
+    if (G.ext_np == 0) G.ext_np = default_ext_np(log_n);
+    if (G.ntt_loge == 0) G.ntt_loge = 4;
+    if (G.ntt_limbs == 0) G.ntt_limbs = small_q ? 1 : 2;
+    if (!hw_ext_find(log_n, G.ext_loge, G.ext_np))
+        return fail(HW_EINVAL, "external-product geometry (loge %d, np %d) is not built for log_n %d",
+                    G.ext_loge, G.ext_np, log_n);
+    if (G.ext_blocks_per_sm < 0 || G.ext_blocks_per_sm > 32)
+        return fail(HW_EINVAL, "ext_blocks_per_sm must be 0..32");
+    if (G.ntt_loge != 3 && G.ntt_loge != 4) return fail(HW_EINVAL, "ntt_loge must be 3 or 4");
+    if (G.ntt_limbs != 1 && G.ntt_limbs != 2) return fail(HW_EINVAL, "ntt_limbs must be 1 or 2");
+    if (G.ntt_limbs == 1 && !small_q)
+        return fail(HW_EINVAL, "32-bit transform arithmetic needs every prime below 2^30");
+    *out = G;
+    return HW_OK;
+}
+
 extern "C" int hw_create(const hw_params* p, int cuda_device, hw_ctx** out) {
+    return hw_create_tuned(p, nullptr, cuda_device, out);
+}
+
+extern "C" int hw_create_tuned(const hw_params* p, const hw_geometry* g, int cuda_device,
+                               hw_ctx** out) {
     if (!p || !out) return fail(HW_EINVAL, "hw_create: null argument");
     *out = nullptr;
     if (p->log_n < 6 || p->log_n > 13) return fail(HW_EINVAL, "log_n must be in [6, 13]");
@@ -154,6 +184,9 @@ extern "C" int hw_create(const hw_params* p, int cuda_device, hw_ctx** out) {
     if (p->hash_h3 && (p->tuple_bits < 1 || p->tuple_bits > 32))
         return fail(HW_EINVAL, "tuple_bits must be 1..32");
     if (p->act < 0 || p->act > 2) return fail(HW_EINVAL, "act must be HW_ACT_*");
+    hw_geometry G;
+    if (int rc = resolve_geometry(p, g, &G)) return rc;
+    const int ext_loge = G.ext_loge;
 
     hw_ctx* c = new hw_ctx();
     memset(&c->host, 0, sizeof(DevCtx));
@@ -349,7 +382,7 @@ extern "C" int hw_create(const hw_params* p, int cuda_device, hw_ctx** out) {
                 // thread-major: position pos of a row sits at eval_addr(pos)
                 const size_t row = k / n;
                 const int pos = (int)(k % n);
-                size_t o = 2 * ((size_t)i * 2 * log_n * n + row * n + eval_addr(pos, log_n));
+                size_t o = 2 * ((size_t)i * 2 * log_n * n + row * n + eval_addr(pos, log_n, ext_loge));
                 rot[o] = dv[k];
                 rot[o + 1] = shoup(dv[k], q[i]);
                 rinv[o] = dk;
@@ -446,8 +479,15 @@ extern "C" int hw_create(const hw_params* p, int cuda_device, hw_ctx** out) {
         H.tw32_fwd = small_q ? t32 : nullptr;
         H.tw32_inv = small_q ? t32 + (size_t)r * n : nullptr;
     }
+    H.ext_loge = G.ext_loge;
+    H.ext_np = G.ext_np;
     c->dctx = (DevCtx*)put(&H, sizeof(DevCtx));
-    e = hw_kernels_init(log_n);
+    LaunchInfo& li = c->li;
+    li.log_n = log_n;
+    li.ext = hw_ext_find(log_n, G.ext_loge, G.ext_np);
+    li.ntt_loge = G.ntt_loge;
+    li.ntt_limbs = G.ntt_limbs;
+    e = hw_kernels_init(li);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         cudaFree(c->tables);
@@ -480,7 +520,6 @@ extern "C" int hw_create(const hw_params* p, int cuda_device, hw_ctx** out) {
 
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, cuda_device);
-    LaunchInfo& li = c->li;
     li.dctx = c->dctx;
     li.log_n = log_n;
     li.n = n;
@@ -500,7 +539,42 @@ extern "C" int hw_create(const hw_params* p, int cuda_device, hw_ctx** out) {
     li.sm_count = sms;
     li.small_q = p->prime_bits <= 30 ? 1 : 0;
     li.launches = &c->launches;
+    {
+        int occ = li.ext->occupancy();
+        if (G.ext_blocks_per_sm > 0 && G.ext_blocks_per_sm < occ) occ = G.ext_blocks_per_sm;
+        G.ext_blocks_per_sm = occ;
+        li.ext_grid = occ * sms;
+    }
+    c->geom = G;
     *out = c;
+    return HW_OK;
+}
+
+extern "C" int hw_get_geometry(const hw_ctx* c, hw_geometry* out) {
+    if (!c || !out) return fail(HW_EINVAL, "hw_get_geometry: null argument");
+    *out = c->geom;
+    return HW_OK;
+}
+
+extern "C" int hw_list_geometries(const hw_params* p, hw_geometry* out, size_t max, size_t* count) {
+    if (!p || !count) return fail(HW_EINVAL, "hw_list_geometries: null argument");
+    if (p->log_n < 6 || p->log_n > 13) return fail(HW_EINVAL, "log_n must be in [6, 13]");
+    int nt = 0;
+    const ExtOps* t = hw_ext_table(p->log_n, &nt);
+    const int d_loge = default_ext_loge(p->log_n), d_np = default_ext_np(p->log_n);
+    size_t k = 0;
+    auto emit = [&](int loge, int np) {
+        if (out && k < max) {
+            memset(&out[k], 0, sizeof(hw_geometry));
+            out[k].ext_loge = loge;
+            out[k].ext_np = np;
+        }
+        k++;
+    };
+    emit(d_loge, d_np);
+    for (int i = 0; i < nt; i++)
+        if (!(t[i].loge == d_loge && t[i].np == d_np)) emit(t[i].loge, t[i].np);
+    *count = k;
     return HW_OK;
 }
 
@@ -539,13 +613,13 @@ extern "C" const char* hw_last_error(void) { return g_last_error.c_str(); }
 // forms (inference), plus the evaluation forms of the k1 tree slots (training).
 extern "C" size_t hw_train_scratch_words(const hw_ctx* c, size_t n) {
     if (!c) return 0;
-    return n * c->sz.model_words + (size_t)hw_ext_grid(c->li) * (4 + c->sz.k1) * c->sz.rlwe_words;
+    return n * c->sz.model_words + (size_t)c->li.ext_grid * (4 + c->sz.k1) * c->sz.rlwe_words;
 }
 
 extern "C" size_t hw_infer_scratch_words(const hw_ctx* c, size_t n) {
     if (!c) return 0;
     (void)n;
-    return (size_t)hw_ext_grid(c->li) * 4 * c->sz.rlwe_words;
+    return (size_t)c->li.ext_grid * 4 * c->sz.rlwe_words;
 }
 
 #define CHECK_CTX(c)                                                   \
@@ -585,7 +659,7 @@ extern "C" int hw_train_accumulate(hw_ctx* c, uint64_t* model, const uint64_t* r
     size_t need = hw_train_scratch_words(c, n);
     if (scratch_words < need)
         return fail(HW_ENOMEM, "hw_train_accumulate: scratch has %zu words, needs %zu", scratch_words, need);
-    int grid = hw_ext_grid(c->li);
+    int grid = c->li.ext_grid;
     u64* out = scratch;
     u64* acc = scratch + n * c->sz.model_words;
     cudaStream_t st = (cudaStream_t)stream;
@@ -603,7 +677,7 @@ extern "C" int hw_infer(hw_ctx* c, const uint64_t* model, const uint64_t* rgsw, 
     size_t need = hw_infer_scratch_words(c, n);
     if (scratch_words < need)
         return fail(HW_ENOMEM, "hw_infer: scratch has %zu words, needs %zu", scratch_words, need);
-    int grid = hw_ext_grid(c->li);
+    int grid = c->li.ext_grid;
     cudaStream_t st = (cudaStream_t)stream;
     CUDA_TRY(launch_vp_infer(c->li, model, rgsw, n, resp, scratch, grid, st));
     CUDA_TRY(launch_class_sums(c->li, resp, n, sums, st));

@@ -30,10 +30,10 @@ def main():
     print("#include <cstdint>")
     print(f"#define HW_CDT_LEN {len(t)}")
     print(f"#define HW_CDT_SUPPORT {SUPPORT}")
-    print("static const uint64_t hw_cdt_table[HW_CDT_LEN] = {")
-    for i in range(0, len(t), 3):
-        print("    " + ", ".join(f"{v}ULL" for v in t[i:i + 3]) + ",")
-    print("};")
+    print("#define HW_CDT_VALUES \\")
+    rows = [", ".join(f"{v}ULL" for v in t[i:i + 3]) for i in range(0, len(t), 3)]
+    for k, row in enumerate(rows):
+        print("    " + row + (", \\" if k + 1 < len(rows) else ""))
 
 
 if __name__ == "__main__":

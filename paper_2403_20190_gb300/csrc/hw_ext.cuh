@@ -1,0 +1,364 @@
+// hw_ext.cuh -- the kernels built on the external product, templated on the
+// context's geometry (2^LOGE residues per thread, NP polynomials per
+// transform): RGSW encryption, IVP training and VP inference.  Each ring
+// size's translation unit instantiates its geometries and exposes them as a
+// table of launchers (ExtOps) that the context picks from.
+#pragma once
+#include "cdt_table.h"
+#include "hw_internal.cuh"
+#include "hw_launch.h"
+
+// The thresholds live in constant memory, statically initialised in every
+// translation unit that samples (all threads read the same entry).
+static __constant__ u64 c_cdt[HW_CDT_LEN] = {HW_CDT_VALUES};
+
+// Discrete Gaussian G(sigma) by inversion of the cumulative table on the top
+// 63 bits of a uniform word: -19 plus the number of thresholds <= u.
+__device__ __forceinline__ int gaussian_from_word(u64 w) {
+    const u64 u = w >> 1;
+    int cnt = 0;
+#pragma unroll
+    for (int t = 0; t < HW_CDT_LEN; t++) cnt += (u >= c_cdt[t]) ? 1 : 0;
+    return cnt - HW_CDT_SUPPORT;
+}
+
+// Encrypted bit slot that drives LUT-index bit t of RAM j: label bits first
+// (slots 0..L-1), then the RAM's tuple bits; -1 for a constant-0 bit.
+__device__ __forceinline__ int bit_slot(const DevCtx& C, int j, int t) {
+    return t < C.L ? t : C.ram_slot[(size_t)j * C.a + (t - C.L)];
+}
+
+// ---------------------------------------------------------------------------
+// EncRGSW.  One block per (sample, bit slot, row).  Row rho < dnum encrypts
+// (a, a*s + e + m*g_rho), row dnum+rho encrypts (a + m*g_rho, a*s + e); the
+// gadget value g_rho sits at prime rho/dpp only.  a is uniform per prime
+// (two 64-bit words -> 128-bit value mod q), e is one integer polynomial for
+// all primes.  Rows are stored in evaluation form, Montgomery representation.
+// ---------------------------------------------------------------------------
+template <int LOGN, int LOGE, int NP>
+__global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP>::T, ExtCfg<LOGN, LOGE, NP>::MINB)
+    k_encrypt(const DevCtx* __restrict__ Cp, const u64* __restrict__ key,
+              const uint8_t* __restrict__ bits, const uint32_t* __restrict__ labels, int slot0,
+              int n_enc_slots, u64 seed, u64 first, u64* __restrict__ out) {
+    using X = ExtCfg<LOGN, LOGE, NP>;
+    constexpr int N = Ring<LOGN>::N, E = 1 << LOGE, T = X::T;
+    extern __shared__ u64 smem[];
+    Xchg xc{smem, smem + NP * X::PADDED, X::PADDED, 0};
+    u64* A = smem + 2 * NP * X::PADDED;
+    int8_t* ebuf = (int8_t*)(A + N);
+    const DevCtx& C = *Cp;
+    const int r = C.r, tid = threadIdx.x;
+    const int rows = 2 * C.dnum;
+    const size_t bid = blockIdx.x;
+    const int row = (int)(bid % rows);
+    const size_t rest = bid / rows;
+    const int slot = slot0 + (int)(rest % n_enc_slots);
+    const size_t i = rest / n_enc_slots;
+    const int bit = slot < C.L ? (int)((labels[i] >> slot) & 1u)
+                               : (int)bits[i * C.n_data + (slot - C.L)];
+    const u64 stream = (first + i) * (u64)C.n_slots + (u64)slot;
+    for (int c0 = tid; c0 < N / 4; c0 += T) {
+        Philox4 w = hw_draw(seed, HW_TAG_RGSW_E, (u64)c0, (u64)row, stream);
+#pragma unroll
+        for (int t = 0; t < 4; t++) ebuf[4 * c0 + t] = (int8_t)gaussian_from_word(w.v[t]);
+    }
+    const int rho = row % C.dnum;
+    const int gi = rho / C.dpp;
+    u64* dst_row = out + i * C.sample_words + (size_t)slot * C.rgsw_words + (size_t)row * C.rlwe_words;
+    for (int j = 0; j < r; j++) {
+        const PrimeConst P = C.P[j];
+        const u64 q = P.q;
+        __syncthreads();  // A is free; ebuf is complete
+        for (int c0 = tid; c0 < N / 2; c0 += T) {
+            Philox4 w = hw_draw(seed, HW_TAG_RGSW_A, (u64)c0, (u64)(row * r + j), stream);
+            A[2 * c0] = reduce128(w.v[0], w.v[1], P);
+            A[2 * c0 + 1] = reduce128(w.v[2], w.v[3], P);
+        }
+        __syncthreads();
+        // a and e transformed together (NP == 2) or one after the other
+        u64 v[2][E];
+#pragma unroll
+        for (int kk = 0; kk < E; kk++) {
+            const int x = tid + kk * T;
+            v[0][kk] = A[x];
+            v[1][kk] = from_signed((int64_t)ebuf[x], q);
+        }
+        if constexpr (NP == 2) {
+            ntt_fwd<LOGN, LOGE, 2>(v, xc, C, j);
+        } else {
+            ntt_fwd<LOGN, LOGE, 1>(reinterpret_cast<u64(&)[1][E]>(v[0]), xc, C, j);
+            ntt_fwd<LOGN, LOGE, 1>(reinterpret_cast<u64(&)[1][E]>(v[1]), xc, C, j);
+        }
+        const u64 g = (bit && j == gi) ? C.gconst[rho] : 0;
+        const u64* sM = key + (size_t)(r + j) * N;
+        u64* da = dst_row + (size_t)(0 * r + j) * N;
+        u64* db = dst_row + (size_t)(1 * r + j) * N;
+#pragma unroll
+        for (int e = 0; e < E; e++) {
+            const int pos = e * T + tid;  // evaluation position E*tid + e, thread-major
+            u64 a = reduce_full(v[0][e], P);
+            u64 b = add_mod(mont_mul(a, sM[pos], P), reduce_full(v[1][e], P), q);
+            // the evaluation form of the constant polynomial g is g everywhere
+            if (row < C.dnum)
+                b = add_mod(b, g, q);
+            else
+                a = add_mod(a, g, q);
+            da[pos] = to_mont(a, P);
+            db[pos] = to_mont(b, P);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// IVP training.  One thread block per work item (sample i, RAM j), persistent
+// over items.  For each item: acc = (0, Delta); for each rotation bit t in
+// z..L+a-1 with an encrypted control C_t: acc <- acc + C_t [x] (acc X^{2^(t-z)}
+// - acc) (BlindRotate with weights -2^k); then the CDEMUX tree over bits
+// 0..z-1, level i splitting L_j into (L_j - C_i [x] L_j, C_i [x] L_j).
+// Outputs: out[item][slot] for every stored ciphertext index.
+// Per-block scratch: two accumulators, their evaluation forms, and the
+// evaluation forms of the k1 tree slots.
+// ---------------------------------------------------------------------------
+template <int LOGN, int LOGE, int NP>
+__global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP>::T, ExtCfg<LOGN, LOGE, NP>::MINB)
+    k_ivp_train(const DevCtx* __restrict__ Cp, const u64* __restrict__ rgsw, int n_items,
+                u64* __restrict__ out, u64* __restrict__ scratch) {
+    using X = ExtCfg<LOGN, LOGE, NP>;
+    extern __shared__ u64 smem[];
+    Xchg xc{smem, smem + NP * X::PADDED, X::PADDED, 0};
+    const DevCtx& C = *Cp;
+    const int tid = threadIdx.x, T = blockDim.x;
+    const size_t rl = C.rlwe_words;
+    u64* blk = scratch + (size_t)blockIdx.x * (4 + C.k1) * rl;
+    u64* acc[2] = {blk, blk + rl};
+    u64* accn[2] = {blk + 2 * rl, blk + 3 * rl};
+    u64* tn = blk + 4 * rl;  // evaluation forms of the tree slots
+    const int kbits = C.L + C.a;
+    for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+        const int i = item / C.k0, j = item % C.k0;
+        const u64* sample = rgsw + (size_t)i * C.sample_words;
+        u64* Lout = out + (size_t)item * C.k1 * rl;
+        // last encrypted rotation bit: its CMUX writes straight into slot 0
+        int last = -1;
+        for (int t = C.z; t < kbits; t++)
+            if (bit_slot(C, j, t) >= 0) last = t;
+        // acc = trivial RLWE (0, Delta * 1); its evaluation form is Delta everywhere in b
+        u64* first_dst = last >= 0 ? acc[0] : Lout;
+        u64* first_ntt = last >= 0 ? accn[0] : tn;
+        for (size_t w = tid; w < rl; w += T) {
+            size_t comp = w / ((size_t)C.r * C.n), rem = w % ((size_t)C.r * C.n);
+            int p = (int)(rem / C.n), x = (int)(rem % C.n);
+            first_dst[w] = (comp == 1 && x == 0) ? C.delta[p] : 0;
+            first_ntt[w] = comp == 1 ? C.delta[p] : 0;
+        }
+        __syncthreads();
+        int cur = 0;
+        for (int t = C.z; t < kbits; t++) {
+            int slot = bit_slot(C, j, t);
+            if (slot < 0) continue;  // constant-0 control: the CMUX keeps acc
+            const int w = 1 << (t - C.z);
+            u64* dst = (t == last) ? Lout : acc[cur ^ 1];
+            u64* dstn = (t == last) ? tn : accn[cur ^ 1];
+            int nslot = -1;  // the next encrypted control (rotation bit or first tree gate)
+            for (int t2 = t + 1; t2 < kbits && nslot < 0; t2++) nslot = bit_slot(C, j, t2);
+            if (nslot < 0 && C.n_gates > 0) nslot = bit_slot(C, j, C.gate_lvl[0]);
+            ext_product<LOGN, LOGE, NP>(
+                C, sample + (size_t)slot * C.rgsw_words, acc[cur], w, acc[cur], 0, EXT_ADD, dst, xc,
+                ExtNtt{accn[cur], dstn, t - C.z, 0,
+                       nslot >= 0 ? sample + (size_t)nslot * C.rgsw_words : nullptr, 1});
+            cur ^= 1;
+        }
+        // CDEMUX tree (pruned gate list, level by level)
+        for (int g = 0; g < C.n_gates; g++) {
+            const int lvl = C.gate_lvl[g], jj = C.gate_j[g];
+            const int nn = 1 << lvl;
+            const size_t slo = C.slot_of[jj], shi = C.slot_of[jj + nn];
+            u64* lo = Lout + slo * rl;
+            u64* hi = Lout + shi * rl;
+            u64* lon = tn + slo * rl;
+            u64* hin = tn + shi * rl;
+            int slot = bit_slot(C, j, lvl);
+            if (slot < 0) {  // constant-0 control: everything stays in L_j
+                for (size_t w = tid; w < rl; w += T) hi[w] = hin[w] = 0;
+                __syncthreads();
+                continue;
+            }
+            const int nslot = g + 1 < C.n_gates ? bit_slot(C, j, C.gate_lvl[g + 1]) : -1;
+            ext_product<LOGN, LOGE, NP>(
+                C, sample + (size_t)slot * C.rgsw_words, lo, 0, nullptr, 0, EXT_PLAIN, hi, xc,
+                ExtNtt{lon, hin, -1, 0, nslot >= 0 ? sample + (size_t)nslot * C.rgsw_words : nullptr,
+                       1});
+            for (size_t w = tid; w < rl; w += T) {
+                const u64 q = C.P[(w / C.n) % C.r].q;
+                lo[w] = sub_mod(lo[w], hi[w], q);
+                lon[w] = sub_mod(lon[w], hin[w], q);
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// VP inference.  One thread block per item (sample i, RAM j, class c).
+// Label bits are in clear: tree levels driven by label bits select a stored
+// ciphertext directly; a tree level driven by an encrypted address bit (z > L)
+// is a CMUX(C, L_{v+n}, L_v); label bits among the rotation bits are a plain
+// rotation X^-(c >> z).  The encrypted address bits then blind-rotate with
+// weights +2^k (X^-2^k) and the last CMUX writes ExtractLWE(., 0) directly.
+// Per-block scratch: two accumulators and their evaluation forms.
+// ---------------------------------------------------------------------------
+template <int LOGN, int LOGE, int NP>
+__global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP>::T, ExtCfg<LOGN, LOGE, NP>::MINB)
+    k_vp_infer(const DevCtx* __restrict__ Cp, const u64* __restrict__ model,
+               const u64* __restrict__ rgsw, int n_items, u64* __restrict__ resp,
+               u64* __restrict__ scratch) {
+    using X = ExtCfg<LOGN, LOGE, NP>;
+    extern __shared__ u64 smem[];
+    Xchg xc{smem, smem + NP * X::PADDED, X::PADDED, 0};
+    const DevCtx& C = *Cp;
+    const int tid = threadIdx.x, T = blockDim.x;
+    const size_t rl = C.rlwe_words;
+    const int two_n = 2 * C.n;
+    u64* blk = scratch + (size_t)blockIdx.x * 4 * rl;
+    u64* acc[2] = {blk, blk + rl};
+    u64* accn[2] = {blk + 2 * rl, blk + 3 * rl};
+    const int kbits = C.L + C.a;
+    const int l = C.n_classes;
+    for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+        const int c = item % l;
+        const int ij = item / l;
+        const int i = ij / C.k0, j = ij % C.k0;
+        const u64* sample = rgsw + (size_t)i * C.sample_words;
+        const u64* Hj = model + (size_t)j * C.k1 * rl;
+        // items run class-fastest (the l classes of a (sample, RAM) share its
+        // RGSW bits); responses are stored [sample][class][RAM]
+        u64* lwe = resp + (((size_t)i * l + c) * C.k0 + j) * C.lwe_words;
+        const u64* src;
+        const u64* srcn = nullptr;  // evaluation form of src, once known
+        int e0;
+        if (C.z <= C.L) {
+            src = Hj + (size_t)C.slot_of[c & ((1 << C.z) - 1)] * rl;
+            const int R = c >> C.z;  // clear label bits among the rotation bits
+            e0 = (two_n - R) % two_n;
+        } else {
+            // one encrypted tree level (bit z-1, an address bit): CMUX(C, L_{v+n}, L_v)
+            const int nn = 1 << (C.z - 1);
+            const u64* lo = Hj + (size_t)C.slot_of[c] * rl;
+            const u64* hi = Hj + (size_t)C.slot_of[c + nn] * rl;
+            const int slot = bit_slot(C, j, C.z - 1);
+            if (slot < 0) {
+                src = lo;
+            } else {
+                ext_product<LOGN, LOGE, NP>(C, sample + (size_t)slot * C.rgsw_words, hi, 0, lo,
+                                                  0, EXT_ADD, acc[0], xc,
+                                                  ExtNtt{nullptr, nullptr, -1, 0, nullptr, 0});
+                src = acc[0];
+            }
+            e0 = 0;
+        }
+        int last = -1;
+        for (int t = (C.z > C.L ? C.z : C.L); t < kbits; t++)
+            if (bit_slot(C, j, t) >= 0) last = t;
+        if (last < 0) {  // nothing encrypted left: extract src * X^e0
+            for (int jp = 0; jp < C.r; jp++) {
+                const u64 q = C.P[jp].q;
+                const u64* pa = src + (size_t)jp * C.n;
+                const u64* pb = src + (size_t)(C.r + jp) * C.n;
+                u64* lw = lwe + (size_t)jp * (C.n + 1);
+                for (int y = tid; y < C.n; y += T) {
+                    u64 va = rot_read(pa, y, e0, C.n, q);
+                    if (y == 0)
+                        lw[0] = va;
+                    else
+                        lw[C.n - y] = neg_mod(va, q);
+                }
+                if (tid == 0) lw[C.n] = rot_read(pb, 0, e0, C.n, q);
+            }
+            __syncthreads();
+            continue;
+        }
+        int cur = (src == acc[0]) ? 0 : 1;  // acc[cur ^ 1] is free
+        for (int t = (C.z > C.L ? C.z : C.L); t < kbits; t++) {
+            int slot = bit_slot(C, j, t);
+            if (slot < 0) continue;
+            const int w = 1 << (t - C.z);
+            const int eA = (e0 + two_n - w) % two_n;
+            // the l classes of a (sample, RAM) share its RGSW bits: only the
+            // class-0 block asks L2 for the next one
+            int nslot = -1;
+            if (c == 0)
+                for (int t2 = t + 1; t2 < kbits && nslot < 0; t2++) nslot = bit_slot(C, j, t2);
+            const ExtNtt nt{srcn, t == last ? nullptr : accn[cur ^ 1], t - C.z, 1,
+                            nslot >= 0 ? sample + (size_t)nslot * C.rgsw_words : nullptr, 0};
+            if (t == last) {
+                ext_product<LOGN, LOGE, NP>(C, sample + (size_t)slot * C.rgsw_words, src, eA, src,
+                                                  e0, EXT_LWE, lwe, xc, nt);
+            } else {
+                ext_product<LOGN, LOGE, NP>(C, sample + (size_t)slot * C.rgsw_words, src, eA, src,
+                                                  e0, EXT_ADD, acc[cur ^ 1], xc, nt);
+                src = acc[cur ^ 1];
+                srcn = accn[cur ^ 1];
+                cur ^= 1;
+            }
+            e0 = 0;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Launch table of one geometry
+// ---------------------------------------------------------------------------
+template <int LOGN, int LOGE, int NP>
+struct ExtVariant {
+    using X = ExtCfg<LOGN, LOGE, NP>;
+    static constexpr size_t ENC_SMEM = X::XCHG_BYTES + (size_t)Ring<LOGN>::N * 9;
+
+    static cudaError_t init() {
+        cudaError_t e = cudaFuncSetAttribute(k_encrypt<LOGN, LOGE, NP>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ENC_SMEM);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_ivp_train<LOGN, LOGE, NP>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)X::XCHG_BYTES);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_vp_infer<LOGN, LOGE, NP>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)X::XCHG_BYTES);
+        return e;
+    }
+    // resident blocks per SM of the persistent kernels (the smaller of the two)
+    static int occupancy() {
+        int a = 0, b = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_ivp_train<LOGN, LOGE, NP>, X::T, X::XCHG_BYTES);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_vp_infer<LOGN, LOGE, NP>, X::T, X::XCHG_BYTES);
+        int o = a < b ? a : b;
+        return o < 1 ? 1 : o;
+    }
+    static cudaError_t encrypt(const LaunchInfo& li, const uint64_t* key, const uint8_t* bits,
+                               const uint32_t* labels, int slot0, int n_enc, unsigned blocks,
+                               uint64_t seed, uint64_t first, uint64_t* out, cudaStream_t st) {
+        k_encrypt<LOGN, LOGE, NP><<<blocks, X::T, ENC_SMEM, st>>>(li.dctx, key, bits, labels, slot0, n_enc,
+                                                                 seed, first, out);
+        return cudaGetLastError();
+    }
+    static cudaError_t ivp(const LaunchInfo& li, const uint64_t* rgsw, int items, uint64_t* out,
+                           uint64_t* acc, int grid, cudaStream_t st) {
+        k_ivp_train<LOGN, LOGE, NP><<<grid, X::T, X::XCHG_BYTES, st>>>(li.dctx, rgsw, items, out, acc);
+        return cudaGetLastError();
+    }
+    static cudaError_t vp(const LaunchInfo& li, const uint64_t* model, const uint64_t* rgsw, int items,
+                          uint64_t* resp, uint64_t* acc, int grid, cudaStream_t st) {
+        k_vp_infer<LOGN, LOGE, NP><<<grid, X::T, X::XCHG_BYTES, st>>>(li.dctx, model, rgsw, items, resp, acc);
+        return cudaGetLastError();
+    }
+    static ExtOps ops() {
+        return ExtOps{LOGE, NP, X::T, X::XCHG_BYTES, ENC_SMEM, &init, &occupancy, &encrypt, &ivp, &vp};
+    }
+};
+
+#define HW_EXT_VARIANT(L, E, P) ExtVariant<L, E, P>::ops(),
+// Defines hw_ext_table_<L>: the geometries instantiated for N = 2^L.
+#define HW_EXT_TABLE(L, LIST)                                 \
+    const ExtOps* hw_ext_table_##L(int* count) {              \
+        static const ExtOps table[] = {LIST};                 \
+        *count = (int)(sizeof(table) / sizeof(table[0]));     \
+        return table;                                         \
+    }

@@ -22,6 +22,7 @@ struct DevCtx {
     int L, a, k0, k1, z, n_slots, n_data, s, n_classes;
     int therm_bits, tuple_bits, hash_h3, n_values, log_p, act, act_arg;
     int n_gates;
+    int ext_loge, ext_np;  // external-product geometry (evaluation layout follows ext_loge)
     PrimeConst P[HW_MAXP];
     u64 n_inv[HW_MAXP], n_inv_s[HW_MAXP];  // N^-1 and its Shoup companion
     u64 delta[HW_MAXP];                    // floor(Q/p) mod q_i
@@ -120,17 +121,18 @@ __device__ __forceinline__ u64 redc_lazy(u64 hi, u64 lo, u64 q, u64 qneg) {
 // last inverse round writes positions tid + k*T (v[k]); the last forward
 // round leaves, and the first inverse round takes, positions 16*tid + e.
 // ---------------------------------------------------------------------------
-// Residues per thread of the external-product geometry (8 below N = 8192,
-// 16 at N = 8192); shared by the kernels and the host tables.
-__host__ __device__ constexpr int ext_loge(int log_n) { return log_n >= 13 ? 4 : 3; }
+// Default external-product geometry: 2^3 residues per thread and two
+// polynomials per transform below N = 8192, 2^4 and one at N = 8192.  A
+// context may choose another instantiated geometry (hw_create_tuned).
+__host__ __device__ constexpr int default_ext_loge(int log_n) { return log_n >= 13 ? 4 : 3; }
+__host__ __device__ constexpr int default_ext_np(int log_n) { return log_n >= 13 ? 1 : 2; }
 
 // Evaluation-form arrays (RGSW rows, the key's evaluation form, rotation
 // tables, evaluation-form copies of ciphertexts) are stored thread-major in
-// the external-product geometry: evaluation position E*t + e lives at
-// address e*T + t (T = N/E threads), so every load and store in that
-// geometry is coalesced.
-__host__ __device__ inline int eval_addr(int pos, int log_n) {
-    const int loge = ext_loge(log_n);
+// the context's external-product geometry: evaluation position E*t + e
+// lives at address e*T + t (E = 2^loge residues per thread, T = N/E
+// threads), so every load and store in that geometry is coalesced.
+__host__ __device__ inline int eval_addr(int pos, int log_n, int loge) {
     const int T = (1 << log_n) >> loge;
     return (pos & ((1 << loge) - 1)) * T + (pos >> loge);
 }
@@ -730,17 +732,23 @@ __device__ __noinline__ void ext_product(const DevCtx& C, const u64* __restrict_
     __syncthreads();  // dst complete for the whole block
 }
 
-// Launch geometry of the external-product kernels: 8 residues per thread
-// with two polynomials per transform below N = 8192; 16 residues per thread,
-// one polynomial at N = 8192 (1024-thread blocks would leave 64 registers).
-template <int LOGN>
+// Launch geometry of the external-product kernels: 2^LOGE residues per
+// thread, NP polynomials transformed together, T = N / 2^LOGE threads.
+template <int LOGN, int LOGE, int NP_>
 struct ExtCfg {
-    static constexpr int LOGE = ext_loge(LOGN);
-    static constexpr int NP = LOGN >= 13 ? 1 : 2;
+    static constexpr int LOGE_ = LOGE;
+    static constexpr int NP = NP_;
     static constexpr int T = Ring<LOGN, LOGE>::T;
-    static constexpr int MINB = (512 / T) > 16 ? 16 : ((512 / T) < 1 ? 1 : (512 / T));
     static constexpr int PADDED = Ring<LOGN, LOGE>::PADDED;
     static constexpr size_t XCHG_BYTES = 2 * (size_t)NP * PADDED * sizeof(u64);
+    // blocks that can be resident per SM by shared memory (227 KiB, 1 KiB
+    // reserved per block) and by a 512-thread target; the register cap the
+    // compiler gets follows from the smaller, so a block that only fits once
+    // per SM is not squeezed into registers it cannot use
+    static constexpr int SMEM_BLOCKS = (int)((227 * 1024) / (XCHG_BYTES + 1024));
+    static constexpr int THR_BLOCKS = (512 / T) < 1 ? 1 : (512 / T);
+    static constexpr int MINB0 = SMEM_BLOCKS < THR_BLOCKS ? SMEM_BLOCKS : THR_BLOCKS;
+    static constexpr int MINB = MINB0 < 1 ? 1 : (MINB0 > 16 ? 16 : MINB0);
 };
 
 // Launch geometry shared by the kernels that run block NTTs.

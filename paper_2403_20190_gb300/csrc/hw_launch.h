@@ -6,6 +6,23 @@
 #include <cstdint>
 
 struct DevCtx;
+struct LaunchInfo;
+
+// Launchers of one external-product geometry (hw_ext.cuh): 2^loge residues
+// per thread, np polynomials per transform, `threads` threads per block.
+struct ExtOps {
+    int loge, np, threads;
+    size_t smem, encrypt_smem;
+    cudaError_t (*init)();   // shared-memory attributes of its kernels
+    int (*occupancy)();      // resident blocks per SM of the IVP / VP kernels
+    cudaError_t (*encrypt)(const LaunchInfo&, const uint64_t* key, const uint8_t* bits,
+                           const uint32_t* labels, int slot0, int n_enc, unsigned blocks,
+                           uint64_t seed, uint64_t first, uint64_t* out, cudaStream_t);
+    cudaError_t (*ivp)(const LaunchInfo&, const uint64_t* rgsw, int items, uint64_t* out,
+                       uint64_t* acc, int grid, cudaStream_t);
+    cudaError_t (*vp)(const LaunchInfo&, const uint64_t* model, const uint64_t* rgsw, int items,
+                      uint64_t* resp, uint64_t* acc, int grid, cudaStream_t);
+};
 
 struct LaunchInfo {
     const DevCtx* dctx;  // device copy of the context
@@ -13,11 +30,20 @@ struct LaunchInfo {
     size_t rlwe_words, lwe_words, rgsw_words, sample_words, model_words;
     int sm_count;
     int small_q;  // every q_i < 2^30: the 32-bit transform tables exist
+    const ExtOps* ext;  // the context's external-product geometry
+    int ext_grid;       // persistent grid of the IVP / VP kernels
+    int ntt_loge;       // hw_ntt_*: 2^ntt_loge residues per thread
+    int ntt_limbs;      // hw_ntt_*: 1 = 32-bit arithmetic, 2 = 64-bit
     unsigned long long* launches;  // launch counter
 };
 
-// Persistent grid size of the IVP / VP kernels for this context.
-int hw_ext_grid(const LaunchInfo& li);
+// Geometry tables, one per ring size (k_ext_*.cu), and lookup.
+#define HW_EXT_TABLE_DECL(L) const ExtOps* hw_ext_table_##L(int* count);
+HW_EXT_TABLE_DECL(6) HW_EXT_TABLE_DECL(7) HW_EXT_TABLE_DECL(8) HW_EXT_TABLE_DECL(9)
+HW_EXT_TABLE_DECL(10) HW_EXT_TABLE_DECL(11) HW_EXT_TABLE_DECL(12) HW_EXT_TABLE_DECL(13)
+#undef HW_EXT_TABLE_DECL
+const ExtOps* hw_ext_table(int log_n, int* count);
+const ExtOps* hw_ext_find(int log_n, int loge, int np);
 
 cudaError_t launch_keygen(const LaunchInfo& li, uint64_t seed, uint64_t* key, cudaStream_t st);
 cudaError_t launch_encode(const LaunchInfo& li, const uint8_t* values, size_t n, uint8_t* bits,
@@ -44,4 +70,6 @@ cudaError_t launch_export_rgsw(const LaunchInfo& li, const uint64_t* rgsw, size_
                                uint64_t* out, cudaStream_t st);
 cudaError_t launch_ntt_batch(const LaunchInfo& li, uint64_t* poly, size_t count, int inverse,
                              cudaStream_t st);
-cudaError_t hw_kernels_init(int log_n);
+// Shared-memory attributes of the context's kernels (its ring size, its
+// external-product geometry and its batched-NTT variant).
+cudaError_t hw_kernels_init(const LaunchInfo& li);

@@ -1,20 +1,7 @@
 // k_crypto.cu -- key generation, client encoding, RGSW encryption,
 // decryption (phase, CRT, rounding), PD-act and transform utilities.
-#include "cdt_table.h"
 #include "hw_internal.cuh"
 #include "hw_launch.h"
-
-__constant__ u64 c_cdt[HW_CDT_LEN];
-
-// Discrete Gaussian G(sigma) by inversion of the cumulative table on the top
-// 63 bits of a uniform word: -19 plus the number of thresholds <= u.
-__device__ __forceinline__ int gaussian_from_word(u64 w) {
-    const u64 u = w >> 1;
-    int cnt = 0;
-#pragma unroll
-    for (int t = 0; t < HW_CDT_LEN; t++) cnt += (u >= c_cdt[t]) ? 1 : 0;
-    return cnt - HW_CDT_SUPPORT;
-}
 
 // ---------------------------------------------------------------------------
 // SecretKeyGen: ternary S_1; key = [r][N] residues, then [r][N] evaluation
@@ -42,7 +29,7 @@ __global__ void __launch_bounds__(Geo<LOGN>::T) k_keygen(const DevCtx* __restric
     ntt_fwd1<LOGN>(v, xc, C, j);
 #pragma unroll
     for (int e = 0; e < 16; e++)
-        key[(size_t)(C.r + j) * N + eval_addr(16 * tid + e, LOGN)] = to_mont(reduce_full(v[e], P), P);
+        key[(size_t)(C.r + j) * N + eval_addr(16 * tid + e, LOGN, C.ext_loge)] = to_mont(reduce_full(v[e], P), P);
 }
 
 // ---------------------------------------------------------------------------
@@ -80,87 +67,6 @@ __global__ void k_encode(const DevCtx* __restrict__ Cp, const uint8_t* __restric
         }
         for (int b = 0; b < C.a; b++)
             bits[i * C.n_data + (size_t)j * C.a + b] = (uint8_t)((h >> b) & 1);
-    }
-}
-
-// ---------------------------------------------------------------------------
-// EncRGSW.  One block per (sample, bit slot, row).  Row rho < dnum encrypts
-// (a, a*s + e + m*g_rho), row dnum+rho encrypts (a + m*g_rho, a*s + e); the
-// gadget value g_rho sits at prime rho/dpp only.  a is uniform per prime
-// (two 64-bit words -> 128-bit value mod q), e is one integer polynomial for
-// all primes.  Rows are stored in evaluation form, Montgomery representation.
-// ---------------------------------------------------------------------------
-template <int LOGN>
-__global__ void __launch_bounds__(ExtCfg<LOGN>::T, ExtCfg<LOGN>::MINB)
-    k_encrypt(const DevCtx* __restrict__ Cp, const u64* __restrict__ key,
-              const uint8_t* __restrict__ bits, const uint32_t* __restrict__ labels, int slot0,
-              int n_enc_slots, u64 seed, u64 first, u64* __restrict__ out) {
-    using X = ExtCfg<LOGN>;
-    constexpr int N = Ring<LOGN>::N, E = 1 << X::LOGE, T = X::T;
-    extern __shared__ u64 smem[];
-    Xchg xc{smem, smem + X::NP * X::PADDED, X::PADDED, 0};
-    u64* A = smem + 2 * X::NP * X::PADDED;
-    int8_t* ebuf = (int8_t*)(A + N);
-    const DevCtx& C = *Cp;
-    const int r = C.r, tid = threadIdx.x;
-    const int rows = 2 * C.dnum;
-    const size_t bid = blockIdx.x;
-    const int row = (int)(bid % rows);
-    const size_t rest = bid / rows;
-    const int slot = slot0 + (int)(rest % n_enc_slots);
-    const size_t i = rest / n_enc_slots;
-    const int bit = slot < C.L ? (int)((labels[i] >> slot) & 1u)
-                               : (int)bits[i * C.n_data + (slot - C.L)];
-    const u64 stream = (first + i) * (u64)C.n_slots + (u64)slot;
-    for (int c0 = tid; c0 < N / 4; c0 += T) {
-        Philox4 w = hw_draw(seed, HW_TAG_RGSW_E, (u64)c0, (u64)row, stream);
-#pragma unroll
-        for (int t = 0; t < 4; t++) ebuf[4 * c0 + t] = (int8_t)gaussian_from_word(w.v[t]);
-    }
-    const int rho = row % C.dnum;
-    const int gi = rho / C.dpp;
-    u64* dst_row = out + i * C.sample_words + (size_t)slot * C.rgsw_words + (size_t)row * C.rlwe_words;
-    for (int j = 0; j < r; j++) {
-        const PrimeConst P = C.P[j];
-        const u64 q = P.q;
-        __syncthreads();  // A is free; ebuf is complete
-        for (int c0 = tid; c0 < N / 2; c0 += T) {
-            Philox4 w = hw_draw(seed, HW_TAG_RGSW_A, (u64)c0, (u64)(row * r + j), stream);
-            A[2 * c0] = reduce128(w.v[0], w.v[1], P);
-            A[2 * c0 + 1] = reduce128(w.v[2], w.v[3], P);
-        }
-        __syncthreads();
-        // a and e transformed together (X::NP == 2) or one after the other
-        u64 v[2][E];
-#pragma unroll
-        for (int kk = 0; kk < E; kk++) {
-            const int x = tid + kk * T;
-            v[0][kk] = A[x];
-            v[1][kk] = from_signed((int64_t)ebuf[x], q);
-        }
-        if constexpr (X::NP == 2) {
-            ntt_fwd<LOGN, X::LOGE, 2>(v, xc, C, j);
-        } else {
-            ntt_fwd<LOGN, X::LOGE, 1>(reinterpret_cast<u64(&)[1][E]>(v[0]), xc, C, j);
-            ntt_fwd<LOGN, X::LOGE, 1>(reinterpret_cast<u64(&)[1][E]>(v[1]), xc, C, j);
-        }
-        const u64 g = (bit && j == gi) ? C.gconst[rho] : 0;
-        const u64* sM = key + (size_t)(r + j) * N;
-        u64* da = dst_row + (size_t)(0 * r + j) * N;
-        u64* db = dst_row + (size_t)(1 * r + j) * N;
-#pragma unroll
-        for (int e = 0; e < E; e++) {
-            const int pos = e * T + tid;  // evaluation position E*tid + e, thread-major
-            u64 a = reduce_full(v[0][e], P);
-            u64 b = add_mod(mont_mul(a, sM[pos], P), reduce_full(v[1][e], P), q);
-            // the evaluation form of the constant polynomial g is g everywhere
-            if (row < C.dnum)
-                b = add_mod(b, g, q);
-            else
-                a = add_mod(a, g, q);
-            da[pos] = to_mont(a, P);
-            db[pos] = to_mont(b, P);
-        }
     }
 }
 
@@ -262,7 +168,7 @@ __global__ void __launch_bounds__(Geo<LOGN>::T)
     ntt_fwd1<LOGN>(v, xc, C, j);
 #pragma unroll
     for (int e = 0; e < 16; e++)
-        v[e] = shoup_mul_lazy(mont_mul(v[e], key[(size_t)(r + j) * N + eval_addr(16 * tid + e, LOGN)], P), C.n_inv[j],
+        v[e] = shoup_mul_lazy(mont_mul(v[e], key[(size_t)(r + j) * N + eval_addr(16 * tid + e, LOGN, C.ext_loge)], P), C.n_inv[j],
                               C.n_inv_s[j], P.q);
     ntt_inv1<LOGN>(v, xc, C, j);
     u64* dst = ph + (t * r + j) * N;
@@ -384,119 +290,17 @@ __global__ void __launch_bounds__(Geo<LOGN>::T)
     u64 v[16];
 #pragma unroll
     for (int e = 0; e < 16; e++)
-        v[e] = shoup_mul_lazy(from_mont(in[poly * N + eval_addr(16 * tid + e, LOGN)], P), C.n_inv[j],
+        v[e] = shoup_mul_lazy(from_mont(in[poly * N + eval_addr(16 * tid + e, LOGN, C.ext_loge)], P), C.n_inv[j],
                               C.n_inv_s[j], P.q);
     ntt_inv1<LOGN>(v, xc, C, j);
 #pragma unroll
     for (int kk = 0; kk < 16; kk++) out[poly * N + tid + kk * T] = v[kk] >= P.q ? v[kk] - P.q : v[kk];
 }
 
-// Batched transform in place: forward takes natural order and leaves the
-// evaluation order; inverse undoes it.  Values are fully reduced.
-template <int LOGN>
-__global__ void __launch_bounds__(Geo<LOGN>::T)
-    k_ntt_batch(const DevCtx* __restrict__ Cp, u64* __restrict__ poly, int inverse) {
-    extern __shared__ u64 smem[];
-    constexpr int N = Ring<LOGN>::N, T = Ring<LOGN>::T;
-    Xchg xc{smem, smem + Ring<LOGN>::PADDED, Ring<LOGN>::PADDED, 0};
-    const DevCtx& C = *Cp;
-    const int tid = threadIdx.x;
-    const size_t t = blockIdx.x;
-    const int j = (int)(t % C.r);
-    const PrimeConst P = C.P[j];
-    u64* p = poly + t * N;
-    u64 v[16];
-    // Positions 16*tid + e go through warp transposes so global accesses are
-    // coalesced: the store uses the exchange buffer the last exchange did
-    // not (read two exchanges ago, before a barrier); the load uses b1 and
-    // the transform's first exchange then takes b0.  Every global read
-    // precedes the first barrier and every write follows the last one, so
-    // the transform runs in place.
-    if (!inverse) {
-#pragma unroll
-        for (int kk = 0; kk < 16; kk++) v[kk] = p[tid + kk * T];
-        ntt_fwd1<LOGN>(v, xc, C, j);
-#pragma unroll
-        for (int e = 0; e < 16; e++) v[e] = reduce_full(v[e], P);
-        if constexpr (T >= 32) {
-            warp_store_positions<16>(p, v, xc.next());
-        } else {
-#pragma unroll
-            for (int e = 0; e < 16; e++) p[16 * tid + e] = v[e];
-        }
-    } else {
-        if constexpr (T >= 32) {
-            warp_load_positions<16>(p, v, xc.b1);
-        } else {
-#pragma unroll
-            for (int e = 0; e < 16; e++) v[e] = p[16 * tid + e];
-        }
-#pragma unroll
-        for (int e = 0; e < 16; e++) v[e] = shoup_mul_lazy(v[e], C.n_inv[j], C.n_inv_s[j], P.q);
-        ntt_inv1<LOGN>(v, xc, C, j);
-#pragma unroll
-        for (int kk = 0; kk < 16; kk++) p[tid + kk * T] = v[kk] >= P.q ? v[kk] - P.q : v[kk];
-    }
-}
-
-// The same batched transform in 32-bit arithmetic (every q_i < 2^30): same
-// evaluation order and results, about a third of the integer instructions.
-template <int LOGN>
-__global__ void __launch_bounds__(Ring<LOGN>::T)
-    k_ntt_batch32(const DevCtx* __restrict__ Cp, u64* __restrict__ poly, int inverse) {
-    extern __shared__ u64 smem[];
-    constexpr int N = Ring<LOGN>::N, T = Ring<LOGN>::T, PD = Ring<LOGN>::PADDED;
-    // 32-bit exchanges use the first half of each 64-bit buffer; the warp
-    // transposes stage 64-bit words in a whole buffer
-    Xchg xc{smem, smem + PD, PD, 0};
-    const DevCtx& C = *Cp;
-    const int tid = threadIdx.x;
-    const size_t t = blockIdx.x;
-    const int j = (int)(t % C.r);
-    const u32 q = (u32)C.P[j].q, q2 = 2 * q;
-    u64* p = poly + t * N;
-    u32 v[1][16];
-    if (!inverse) {
-#pragma unroll
-        for (int kk = 0; kk < 16; kk++) v[0][kk] = (u32)p[tid + kk * T];
-        fwd_from32<LOGN, 4, 1, 0>(v, xc, C.tw32_fwd + (size_t)j * N, q, q2);
-        u64 o[16];
-#pragma unroll
-        for (int e = 0; e < 16; e++) {
-            u32 x = v[0][e] >= q2 ? v[0][e] - q2 : v[0][e];
-            o[e] = x >= q ? x - q : x;
-        }
-        if constexpr (T >= 32) {
-            warp_store_positions<16>(p, o, xc.next());
-        } else {
-#pragma unroll
-            for (int e = 0; e < 16; e++) p[16 * tid + e] = o[e];
-        }
-    } else {
-        u64 o[16];
-        if constexpr (T >= 32) {
-            warp_load_positions<16>(p, o, xc.b1);
-        } else {
-#pragma unroll
-            for (int e = 0; e < 16; e++) o[e] = p[16 * tid + e];
-        }
-#pragma unroll
-        for (int e = 0; e < 16; e++) v[0][e] = shoup32_lazy((u32)o[e], C.n_inv32[j], C.n_inv32_s[j], q);
-        inv_from32<LOGN, 4, 1, 0>(v, xc, C.tw32_inv + (size_t)j * N, q, q2);
-#pragma unroll
-        for (int kk = 0; kk < 16; kk++) p[tid + kk * T] = v[0][kk] >= q ? v[0][kk] - q : v[0][kk];
-    }
-}
-
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
 #define HW_LAUNCHED() ((*li.launches)++, cudaGetLastError())
-
-template <int LOGN>
-static size_t encrypt_smem() {
-    return ExtCfg<LOGN>::XCHG_BYTES + (size_t)Ring<LOGN>::N * 9;
-}
 
 #define HW_DISPATCH(logn, BODY)      \
     switch (logn) {                  \
@@ -533,14 +337,10 @@ cudaError_t launch_encrypt(const LaunchInfo& li, const uint64_t* key, const uint
     const int n_enc = li.n_slots - slot0;
     const size_t blocks = n * (size_t)n_enc * 2 * li.dnum;
     if (blocks >= ((size_t)1 << 31)) return cudaErrorInvalidValue;
-#define B(L)                                                                                    \
-    case L:                                                                                     \
-        k_encrypt<L><<<(unsigned)blocks, ExtCfg<L>::T, encrypt_smem<L>(), st>>>(                \
-            li.dctx, key, bits, labels, slot0, n_enc, seed, first, out);                        \
-        break;
-    HW_DISPATCH(li.log_n, B)
-#undef B
-    return HW_LAUNCHED();
+    cudaError_t e = li.ext->encrypt(li, key, bits, labels, slot0, n_enc, (unsigned)blocks, seed, first,
+                                    out, st);
+    (*li.launches)++;
+    return e;
 }
 
 cudaError_t launch_decrypt_rlwe(const LaunchInfo& li, const uint64_t* key, const uint64_t* ct,
@@ -597,45 +397,26 @@ cudaError_t launch_export_rgsw(const LaunchInfo& li, const uint64_t* rgsw, size_
     return HW_LAUNCHED();
 }
 
-cudaError_t launch_ntt_batch(const LaunchInfo& li, uint64_t* poly, size_t count, int inverse,
-                             cudaStream_t st) {
-    if (count == 0) return cudaSuccess;
-    if (li.small_q) {
-#define B(L)                                                                                  \
-    case L:                                                                                   \
-        k_ntt_batch32<L><<<(unsigned)count, Geo<L>::T, Geo<L>::XCHG_BYTES, st>>>(li.dctx, poly, \
-                                                                               inverse);      \
-        break;
-        HW_DISPATCH(li.log_n, B)
-#undef B
-        return HW_LAUNCHED();
-    }
-#define B(L)                                                                                       \
-    case L:                                                                                        \
-        k_ntt_batch<L><<<(unsigned)count, Geo<L>::T, Geo<L>::XCHG_BYTES, st>>>(li.dctx, poly, inverse); \
-        break;
-    HW_DISPATCH(li.log_n, B)
-#undef B
-    return HW_LAUNCHED();
-}
+extern cudaError_t hw_ntt_kernels_init(const LaunchInfo& li);
 
-extern cudaError_t hw_wisard_kernels_init();
-
-cudaError_t hw_kernels_init(int log_n) {
-    (void)log_n;
-    cudaError_t e = cudaMemcpyToSymbol(c_cdt, hw_cdt_table, sizeof(u64) * HW_CDT_LEN);
+cudaError_t hw_kernels_init(const LaunchInfo& li) {
+    cudaError_t e = cudaSuccess;
 #define A(K, L, BYTES) \
     if (e == cudaSuccess) e = cudaFuncSetAttribute(K<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(BYTES));
-#define X(L)                                          \
-    A(k_keygen, L, Geo<L>::XCHG_BYTES)                \
-    A(k_encrypt, L, encrypt_smem<L>())                \
-    A(k_rlwe_phase, L, Geo<L>::XCHG_BYTES)            \
-    A(k_export_rgsw, L, Geo<L>::XCHG_BYTES)           \
-    A(k_ntt_batch, L, Geo<L>::XCHG_BYTES)            \
-    A(k_ntt_batch32, L, Geo<L>::XCHG_BYTES)
-    HW_FOR_EACH_LOGN(X)
+#define X(L)                                   \
+    case L:                                    \
+        A(k_keygen, L, Geo<L>::XCHG_BYTES)     \
+        A(k_rlwe_phase, L, Geo<L>::XCHG_BYTES) \
+        A(k_export_rgsw, L, Geo<L>::XCHG_BYTES) \
+        break;
+    switch (li.log_n) {
+        HW_FOR_EACH_LOGN(X)
+        default:
+            return cudaErrorInvalidValue;
+    }
 #undef X
 #undef A
-    if (e != cudaSuccess) return e;
-    return hw_wisard_kernels_init();
+    if (e == cudaSuccess) e = li.ext->init();
+    if (e == cudaSuccess) e = hw_ntt_kernels_init(li);
+    return e;
 }

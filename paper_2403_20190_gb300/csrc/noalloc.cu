@@ -78,7 +78,7 @@ extern "C" int hw_infer_static_scratch(hw_ctx* ctx, const uint64_t* model, const
     u64* scratch = nullptr;
     int rc = scratch_address(device, &scratch);
     if (rc != HW_OK) return rc;
-    int grid = hw_ext_grid(li);
+    int grid = li.ext_grid;
     if ((size_t)grid > fit) grid = (int)fit;
     cudaStream_t st = (cudaStream_t)stream;
     // No part of the array has to start at zero: every block writes each of

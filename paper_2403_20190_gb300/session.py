@@ -7,10 +7,19 @@ from . import binding as B
 
 
 class Session:
-    def __init__(self, cfg, device: int = 0):
+    def __init__(self, cfg, device: int = 0, geometry=None):
+        """geometry: None (library defaults), "auto" (autotuned, cached per
+        GPU and parameter set) or a dict of hwisard geometry fields."""
         self.cfg = cfg
         self.device = torch.device("cuda", device)
-        self.ctx = B.hw_create(cfg, device)
+        if geometry == "auto":
+            from .tuning import tuned_geometry
+            geometry = tuned_geometry(cfg, device)[0]
+        if geometry:
+            self.ctx = B.hw_create_tuned(cfg, geometry, device)
+        else:
+            self.ctx = B.hw_create(cfg, device)
+        self.geometry = B.hw_get_geometry(self.ctx)
         self.sz = B.hw_get_sizes(self.ctx)
 
     # --------------------------------------------------------------- buffers

@@ -72,3 +72,35 @@ def test_null_context_is_an_error(lib):
 def test_sources_are_sm103a_only():
     from paper_2403_20190_gb300 import build
     assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_geometry_lists_need_no_gpu(lib):
+    """Every ring size lists its built external-product geometries, the
+    default first; the workload rings offer more than one."""
+    from paper_2403_20190_gb300 import binding
+    from synthdata import get_config
+    expect_default = {6: (3, 2), 10: (3, 2), 12: (3, 2), 13: (4, 1)}
+    for name, log_n, n_min in (("cfg1", 6, 4), ("cfg1", 10, 4), ("cfg2", 12, 4), ("cfg3", 13, 2)):
+        geos = binding.hw_list_geometries(get_config(name, log_n=log_n))
+        assert len(geos) >= n_min
+        assert (geos[0]["ext_loge"], geos[0]["ext_np"]) == expect_default[log_n]
+        pairs = [(g["ext_loge"], g["ext_np"]) for g in geos]
+        assert len(set(pairs)) == len(pairs)
+        for loge, np_ in pairs:
+            assert loge in (3, 4) and np_ in (1, 2)
+
+
+def test_bad_geometries_rejected_before_cuda(lib):
+    from paper_2403_20190_gb300 import binding
+    from synthdata import get_config
+    cases = [(get_config("cfg3"), dict(ext_loge=4, ext_np=2)),   # not built at N = 8192
+             (get_config("cfg2"), dict(ext_loge=5)),
+             (get_config("cfg2"), dict(ntt_loge=5)),
+             (get_config("cfg2"), dict(ntt_limbs=1)),              # 50-bit primes need 64-bit words
+             (get_config("cfg2"), dict(ext_blocks_per_sm=-1))]
+    for cfg, geo in cases:
+        p = binding.params_from_config(cfg)
+        g = binding._geometry(geo)
+        h = ctypes.c_void_p()
+        assert lib.hw_create_tuned(ctypes.byref(p), ctypes.byref(g), 0, ctypes.byref(h)) == -1, geo
+        assert lib.hw_last_error()

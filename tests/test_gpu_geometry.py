@@ -1,0 +1,60 @@
+"""Every kernel geometry the library builds computes the same bits, and the
+autotuner picks one of them.
+
+The geometry (residues per thread, polynomials per transform, resident
+blocks per SM) changes only speed and the internal evaluation layout, so
+each one must reproduce the oracle exactly: full parity on every tiny tree
+shape, sampled parity on the workload rings.  Integer results: tolerance 0.
+"""
+import pytest
+import torch
+
+from synthdata import get_config
+from test_gpu_parity import TINY, tiny_cfg, tiny_full_parity, workload_sampled_parity
+
+pytestmark = pytest.mark.gpu
+
+
+def geometries(cfg):
+    from paper_2403_20190_gb300 import binding
+    return binding.hw_list_geometries(cfg)
+
+
+@pytest.mark.parametrize("name", list(TINY))
+@pytest.mark.parametrize("k", range(4))
+def test_tiny_rings_every_geometry(name, k):
+    geos = geometries(tiny_cfg(name))
+    assert len(geos) == 4
+    tiny_full_parity(name, geos[k])
+
+
+def test_tiny_ring_one_block_per_sm():
+    tiny_full_parity("zgtL", dict(ext_blocks_per_sm=1))
+
+
+@pytest.mark.parametrize("name,n_train,n_test,rams", [
+    ("cfg1", 3, 2, [0, 29]),
+    ("cfg2", 2, 1, [0, 130]),
+    ("cfg3", 1, 1, [146]),
+])
+def test_workload_rings_every_geometry(name, n_train, n_test, rams):
+    for g in geometries(get_config(name))[1:]:  # the default runs in test_gpu_parity
+        workload_sampled_parity(name, n_train, n_test, rams, g)
+        torch.cuda.empty_cache()
+
+
+def test_autotune_picks_a_built_geometry_and_keeps_parity():
+    from paper_2403_20190_gb300 import binding
+    cfg = tiny_cfg("zltL_h3")
+    best, entries = binding.hw_autotune(cfg, 0, n_probe=2, reps=1)
+    built = {(g["ext_loge"], g["ext_np"]) for g in geometries(cfg)}
+    assert (best["ext_loge"], best["ext_np"]) in built
+    step = [e for e in entries if e["ms_train"] >= 0]
+    ntt = [e for e in entries if e["ms_ntt"] >= 0]
+    assert len(step) >= len(built) and all(e["status"] == 0 for e in entries)
+    # 55-bit primes: radix 8 and 16, 64-bit words only
+    assert sorted((e["geometry"]["ntt_loge"], e["geometry"]["ntt_limbs"]) for e in ntt) == [(3, 2), (4, 2)]
+    fastest = min(step, key=lambda e: e["ms_encrypt"] + e["ms_train"] + e["ms_infer"])
+    assert (best["ext_loge"], best["ext_np"], best["ext_blocks_per_sm"]) == (
+        fastest["geometry"]["ext_loge"], fastest["geometry"]["ext_np"], fastest["geometry"]["ext_blocks_per_sm"])
+    tiny_full_parity("zltL_h3", best)

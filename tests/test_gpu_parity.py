@@ -28,9 +28,9 @@ def _built():
     assert torch.cuda.is_available(), "GPU tests need a CUDA device"
 
 
-def session(cfg):
+def session(cfg, geometry=None):
     from paper_2403_20190_gb300.session import Session
-    return Session(cfg, 0)
+    return Session(cfg, 0, geometry=geometry)
 
 
 # every tree shape of the workloads on N = 64 rings (the smallest ring the
@@ -58,8 +58,8 @@ def tiny_cfg(name):
     return get_config("cfg1", data_kind="uniform", act="log", act_arg=0, **TINY[name])
 
 
-def run_pipeline(cfg, n_train, n_test, seed_tr=31, seed_te=41, key_seed=21):
-    sess = session(cfg)
+def run_pipeline(cfg, n_train, n_test, seed_tr=31, seed_te=41, key_seed=21, geometry=None):
+    sess = session(cfg, geometry)
     dev = sess.device
     vals, labels = make_dataset(cfg, "train", n=n_train)
     tvals, _ = make_dataset(cfg, "test", n=n_test)
@@ -78,10 +78,14 @@ def run_pipeline(cfg, n_train, n_test, seed_tr=31, seed_te=41, key_seed=21):
 
 @pytest.mark.parametrize("name", list(TINY))
 def test_tiny_rings_full_parity(name):
+    tiny_full_parity(name, None)
+
+
+def tiny_full_parity(name, geometry):
     cfg = tiny_cfg(name)
     o = Oracle(cfg)
     P = o.P
-    R = run_pipeline(cfg, 7, 3)
+    R = run_pipeline(cfg, 7, 3, geometry=geometry)
     sess = R["sess"]
     s = o.keygen(21)
     # key
@@ -151,13 +155,17 @@ def _library_root(q, log_n):
         x += 2
 
 
-@pytest.mark.parametrize("name", ["cfg1", "cfg2", "cfg4"])
-def test_ntt_is_evaluation_at_odd_powers(name):
-    """The batched forward transform (32-bit arithmetic for cfg1's 30-bit
-    prime, 64-bit otherwise) puts a(psi^(2 brv(pos) + 1)) at position pos."""
+@pytest.mark.parametrize("name,ntt_loge,ntt_limbs", [
+    ("cfg1", 4, 1), ("cfg1", 3, 1), ("cfg1", 4, 2), ("cfg1", 3, 2),
+    ("cfg2", 4, 2), ("cfg2", 3, 2), ("cfg4", 4, 2), ("cfg4", 3, 2)])
+def test_ntt_is_evaluation_at_odd_powers(name, ntt_loge, ntt_limbs):
+    """Every batched-transform variant (radix 8 or 16; 32-bit arithmetic for
+    cfg1's 30-bit prime, 64-bit everywhere) puts a(psi^(2 brv(pos) + 1)) at
+    position pos, and its inverse undoes it."""
     from paper_2403_20190_gb300 import binding as B
     cfg = get_config(name)
-    sess = session(cfg)
+    sess = session(cfg, dict(ntt_loge=ntt_loge, ntt_limbs=ntt_limbs))
+    assert (sess.geometry["ntt_loge"], sess.geometry["ntt_limbs"]) == (ntt_loge, ntt_limbs)
     sz = sess.sz
     n, r, log_n = sz["n"], sz["r"], cfg.log_n
     rng = np.random.default_rng(1)
@@ -192,10 +200,14 @@ def test_ntt_is_evaluation_at_odd_powers(name):
 def test_workload_parameters_sampled_parity(name, n_train, n_test, rams):
     """Real ring sizes and primes: RGSW rows, trained model rows and
     inference responses on chosen RAMs (the last RAM included) bit-exact."""
+    workload_sampled_parity(name, n_train, n_test, rams, None)
+
+
+def workload_sampled_parity(name, n_train, n_test, rams, geometry):
     cfg = get_config(name)
     o = Oracle(cfg)
     P = o.P
-    R = run_pipeline(cfg, n_train, n_test)
+    R = run_pipeline(cfg, n_train, n_test, geometry=geometry)
     sess = R["sess"]
     s = o.keygen(21)
     obits = wisard.encode(P, R["vals"])
