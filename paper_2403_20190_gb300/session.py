@@ -125,8 +125,8 @@ class ServerStep:
     encrypted batch (IVP + accumulate into the resident model) and answer an
     encrypted test batch (VP + class sums), then decrypt the responses and
     classify them with PD-act.  The encrypted inputs live in rgsw_train /
-    rgsw_test; capture() records the whole step once into a CUDA graph and
-    replay() re-issues it (the model keeps accumulating across replays)."""
+    rgsw_test; capture() records the step once into CUDA graphs and replay()
+    re-issues them (the model keeps accumulating across replays)."""
 
     def __init__(self, sess: Session, key, model, n_train: int, n_test: int):
         self.sess, self.key, self.model = sess, key, model
@@ -143,23 +143,43 @@ class ServerStep:
         self.graph = None
         self.launches_per_step = None
 
-    def run(self, stream=None):
-        s, ctx = self.sess, self.sess.ctx
-        B.hw_train_accumulate(ctx, self.model, self.rgsw_train, self.n_train, self.scratch, stream)
+    def run_train(self, stream=None):
+        B.hw_train_accumulate(self.sess.ctx, self.model, self.rgsw_train, self.n_train, self.scratch, stream)
+
+    def run_infer(self, stream=None):
         resp, sums, scr = self.ibufs
-        B.hw_infer(ctx, self.model, self.rgsw_test, self.n_test, resp, sums, scr, stream)
+        B.hw_infer(self.sess.ctx, self.model, self.rgsw_test, self.n_test, resp, sums, scr, stream)
+
+    def run_post(self, stream=None):
+        s, ctx = self.sess, self.sess.ctx
+        resp = self.ibufs[0]
         l, k0 = s.cfg.n_classes, s.sz["k0"]
         B.hw_decrypt(ctx, self.key, B.HW_DEC_LWE, resp, self.n_test * l * k0, self.counts, stream)
         B.hw_pdact(ctx, self.counts, self.n_test, self.scores, self.labels, stream)
 
-    def capture(self):
-        g = torch.cuda.CUDAGraph()
-        before = B.hw_launch_count(self.sess.ctx)
-        with torch.cuda.graph(g, capture_error_mode="relaxed"):
-            self.run()
-        self.launches_per_step = B.hw_launch_count(self.sess.ctx) - before
-        self.graph = g
-        return g
+    def run(self, stream=None):
+        self.run_train(stream)
+        self.run_infer(stream)
+        self.run_post(stream)
 
-    def replay(self):
-        self.graph.replay()
+    def capture(self):
+        """Capture the step as three CUDA graphs (train, infer, decrypt +
+        PD-act) replayed back to back, so a caller can time the parts."""
+        before = B.hw_launch_count(self.sess.ctx)
+        graphs = []
+        for part in (self.run_train, self.run_infer, self.run_post):
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, capture_error_mode="relaxed"):
+                part()
+            graphs.append(g)
+        self.launches_per_step = B.hw_launch_count(self.sess.ctx) - before
+        self.graphs = graphs
+        self.graph = graphs[0]
+        return graphs
+
+    def replay(self, between=None):
+        """Replay the step; between(i) runs after part i (0: train, 1: infer)."""
+        for i, g in enumerate(self.graphs):
+            g.replay()
+            if between is not None:
+                between(i)
