@@ -110,7 +110,11 @@ typedef struct hw_geometry {
     int32_t ntt_loge;          /* hw_ntt_forward/inverse: 2^ntt_loge residues per thread; 3 or 4 */
     int32_t ntt_limbs;         /* hw_ntt_forward/inverse: 32-bit words per residue in the arithmetic:
                                   1 (only when every q_i < 2^30) or 2 */
-    int32_t reserved[3];
+    int32_t l2_persist;        /* 1: the training / inference kernels mark their per-block
+                                  accumulators persisting in L2 (an access-policy window on each
+                                  launch and a persisting set-aside of this process's context,
+                                  sized to those accumulators); 0: off (default) */
+    int32_t reserved[2];
 } hw_geometry;
 
 /* hw_create with a chosen geometry (NULL = defaults).  HW_EINVAL if the
@@ -137,8 +141,8 @@ typedef struct hw_tune_entry {
 } hw_tune_entry;
 
 /* Autotuner (no counterpart in the paper): times every built external-
- * product geometry (and, where it matters, a halved resident-block count)
- * on one step of n_probe training and n_probe test samples -- encryption,
+ * product geometry (and, where it matters, a halved resident-block count;
+ * then the fastest one again with l2_persist) on one step of n_probe training and n_probe test samples -- encryption,
  * training, inference -- and every batched-NTT variant on a batch of
  * polynomials larger than L2, each `reps` times (best time kept), on
  * synthetic inputs in buffers it allocates and frees itself.  *best gets

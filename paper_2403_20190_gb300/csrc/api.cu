@@ -160,6 +160,7 @@ static int resolve_geometry(const hw_params* p, const hw_geometry* g, hw_geometr
     if (G.ntt_limbs != 1 && G.ntt_limbs != 2) return fail(HW_EINVAL, "ntt_limbs must be 1 or 2");
     if (G.ntt_limbs == 1 && !small_q)
         return fail(HW_EINVAL, "32-bit transform arithmetic needs every prime below 2^30");
+    if (G.l2_persist != 0 && G.l2_persist != 1) return fail(HW_EINVAL, "l2_persist must be 0 or 1");
     *out = G;
     return HW_OK;
 }
@@ -544,6 +545,31 @@ extern "C" int hw_create_tuned(const hw_params* p, const hw_geometry* g, int cud
         if (G.ext_blocks_per_sm > 0 && G.ext_blocks_per_sm < occ) occ = G.ext_blocks_per_sm;
         G.ext_blocks_per_sm = occ;
         li.ext_grid = occ * sms;
+    }
+    li.l2_persist = 0;
+    li.l2_window_max = 0;
+    if (G.l2_persist) {
+        // persisting set-aside of this process's context, sized to the
+        // inference kernel's accumulators (two RLWEs and their evaluation
+        // forms per resident block) and capped by the device; it ends with
+        // the context
+        int max_persist = 0, max_window = 0;
+        cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, cuda_device);
+        cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize, cuda_device);
+        size_t want = (size_t)li.ext_grid * 4 * H.rlwe_words * sizeof(u64);
+        if (want > (size_t)max_persist) want = (size_t)max_persist;
+        size_t cur = 0;
+        cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize);
+        if (want > cur && cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want) != cudaSuccess) {
+            cudaGetLastError();
+            want = cur;
+        }
+        if (want > 0 && max_window > 0) {
+            li.l2_persist = want;
+            li.l2_window_max = (size_t)max_window;
+        } else {
+            G.l2_persist = 0;  // not available here: report it off
+        }
     }
     c->geom = G;
     *out = c;

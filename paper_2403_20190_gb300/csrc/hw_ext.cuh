@@ -8,6 +8,8 @@
 #include "hw_internal.cuh"
 #include "hw_launch.h"
 
+#include <cstring>
+
 // The thresholds live in constant memory, statically initialised in every
 // translation unit that samples (all threads read the same entry).
 static __constant__ u64 c_cdt[HW_CDT_LEN] = {HW_CDT_VALUES};
@@ -339,15 +341,44 @@ struct ExtVariant {
                                                                  seed, first, out);
         return cudaGetLastError();
     }
+    // Launch configuration; with li.l2_persist the launch carries an access-
+    // policy window over the first `window` bytes of the per-block scratch.
+    struct Launch {
+        cudaLaunchConfig_t cfg;
+        cudaLaunchAttribute attr;
+        Launch(const LaunchInfo& li, int grid, cudaStream_t st, void* scratch, size_t window) {
+            memset(&cfg, 0, sizeof(cfg));
+            memset(&attr, 0, sizeof(attr));
+            cfg.gridDim = dim3(grid);
+            cfg.blockDim = dim3(X::T);
+            cfg.dynamicSmemBytes = X::XCHG_BYTES;
+            cfg.stream = st;
+            if (li.l2_persist > 0 && window > 0) {
+                if (window > li.l2_window_max) window = li.l2_window_max;
+                attr.id = cudaLaunchAttributeAccessPolicyWindow;
+                attr.val.accessPolicyWindow.base_ptr = scratch;
+                attr.val.accessPolicyWindow.num_bytes = window;
+                const double ratio = (double)li.l2_persist / (double)window;
+                attr.val.accessPolicyWindow.hitRatio = ratio < 1.0 ? (float)ratio : 1.0f;
+                attr.val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+                attr.val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+                cfg.attrs = &attr;
+                cfg.numAttrs = 1;
+            }
+        }
+    };
     static cudaError_t ivp(const LaunchInfo& li, const uint64_t* rgsw, int items, uint64_t* out,
                            uint64_t* acc, int grid, cudaStream_t st) {
-        k_ivp_train<LOGN, LOGE, NP><<<grid, X::T, X::XCHG_BYTES, st>>>(li.dctx, rgsw, items, out, acc);
-        return cudaGetLastError();
+        // per-block scratch: two accumulators, their evaluation forms, the tree slots
+        Launch L(li, grid, st, acc, (size_t)grid * (4 + li.k1) * li.rlwe_words * sizeof(u64));
+        return cudaLaunchKernelEx(&L.cfg, k_ivp_train<LOGN, LOGE, NP>, li.dctx, (const u64*)rgsw, items,
+                                  (u64*)out, (u64*)acc);
     }
     static cudaError_t vp(const LaunchInfo& li, const uint64_t* model, const uint64_t* rgsw, int items,
                           uint64_t* resp, uint64_t* acc, int grid, cudaStream_t st) {
-        k_vp_infer<LOGN, LOGE, NP><<<grid, X::T, X::XCHG_BYTES, st>>>(li.dctx, model, rgsw, items, resp, acc);
-        return cudaGetLastError();
+        Launch L(li, grid, st, acc, (size_t)grid * 4 * li.rlwe_words * sizeof(u64));
+        return cudaLaunchKernelEx(&L.cfg, k_vp_infer<LOGN, LOGE, NP>, li.dctx, (const u64*)model,
+                                  (const u64*)rgsw, items, (u64*)resp, (u64*)acc);
     }
     static ExtOps ops() {
         return ExtOps{LOGE, NP, X::T, X::XCHG_BYTES, ENC_SMEM, &init, &occupancy, &encrypt, &ivp, &vp};

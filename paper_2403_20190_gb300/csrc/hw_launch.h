@@ -34,6 +34,8 @@ struct LaunchInfo {
     int ext_grid;       // persistent grid of the IVP / VP kernels
     int ntt_loge;       // hw_ntt_*: 2^ntt_loge residues per thread
     int ntt_limbs;      // hw_ntt_*: 1 = 32-bit arithmetic, 2 = 64-bit
+    size_t l2_persist;     // > 0: persisting L2 bytes for the IVP / VP accumulators
+    size_t l2_window_max;  // largest access-policy window the device takes
     unsigned long long* launches;  // launch counter
 };
 

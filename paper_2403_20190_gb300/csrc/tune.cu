@@ -200,6 +200,27 @@ extern "C" int hw_autotune(const hw_params* p, int dev, size_t n_probe, int32_t 
             best_ms = t;
         }
     }
+    // the best step geometry again with its accumulators persisting in L2;
+    // the set-aside it takes is given back afterwards
+    if (best_step >= 0) {
+        size_t prev = 0;
+        cudaDeviceGetLimit(&prev, cudaLimitPersistingL2CacheSize);
+        hw_geometry g = all[best_step].geometry;
+        g.l2_persist = 1;
+        hw_tune_entry e;
+        probe_step(p, g, dev, n_probe, reps, st, &e);
+        cudaCtxResetPersistingL2Cache();
+        cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, prev);
+        cudaGetLastError();
+        if (e.status == HW_OK && e.geometry.l2_persist == 1) {
+            all.push_back(e);
+            const double t = e.ms_encrypt + e.ms_train + e.ms_infer;
+            if (t < best_ms) {
+                best_step = (int)all.size() - 1;
+                best_ms = t;
+            }
+        }
+    }
     // batched-transform variants (radix 8 / 16, 64-bit and, for primes
     // below 2^30, 32-bit arithmetic) with the default step geometry
     const size_t first_ntt = all.size();

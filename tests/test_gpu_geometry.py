@@ -32,6 +32,15 @@ def test_tiny_ring_one_block_per_sm():
     tiny_full_parity("zgtL", dict(ext_blocks_per_sm=1))
 
 
+@pytest.mark.parametrize("name", ["zgtL", "r2_beta1024"])
+def test_tiny_ring_accumulators_persisting_in_l2(name):
+    tiny_full_parity(name, dict(l2_persist=1))
+
+
+def test_workload_ring_accumulators_persisting_in_l2():
+    workload_sampled_parity("cfg2", 2, 1, [0, 130], dict(l2_persist=1))
+
+
 @pytest.mark.parametrize("name,n_train,n_test,rams", [
     ("cfg1", 3, 2, [0, 29]),
     ("cfg2", 2, 1, [0, 130]),
