@@ -226,7 +226,7 @@ int hw_pdact(hw_ctx* ctx, const int64_t* counts_dev, size_t n, int64_t* scores_d
  * - All calls share the array: calls whose work overlaps on the GPU (other
  *   streams, other threads, other contexts on the same device) race.  Order
  *   them, e.g. on one stream.
- * - Rings whose four per-block buffers exceed the array (4 * rlwe_words * 8
+ * - Rings whose three per-block buffers exceed the array (3 * rlwe_words * 8
  *   bytes > HW_STATIC_SCRATCH_BYTES) are rejected with HW_EINVAL; the number
  *   of resident blocks is capped so that all of them fit.
  * - Nothing is allocated or freed: no cudaMalloc, cudaFree or allocating

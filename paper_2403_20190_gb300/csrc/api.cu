@@ -556,7 +556,7 @@ extern "C" int hw_create_tuned(const hw_params* p, const hw_geometry* g, int cud
         int max_persist = 0, max_window = 0;
         cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, cuda_device);
         cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize, cuda_device);
-        size_t want = (size_t)li.ext_grid * 4 * H.rlwe_words * sizeof(u64);
+        size_t want = (size_t)li.ext_grid * 3 * H.rlwe_words * sizeof(u64);
         if (want > (size_t)max_persist) want = (size_t)max_persist;
         size_t cur = 0;
         cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize);
@@ -635,17 +635,18 @@ int hw_ctx_fail(int code, const char* msg) { return fail(code, "%s", msg); }
 
 extern "C" const char* hw_last_error(void) { return g_last_error.c_str(); }
 
-// Persistent-grid scratch per block: two accumulators and their evaluation
-// forms (inference), plus the evaluation forms of the k1 tree slots (training).
+// Persistent-grid scratch per block: two accumulators and one evaluation-form
+// buffer (inference), plus the evaluation forms of the k1 tree slots
+// (training).
 extern "C" size_t hw_train_scratch_words(const hw_ctx* c, size_t n) {
     if (!c) return 0;
-    return n * c->sz.model_words + (size_t)c->li.ext_grid * (4 + c->sz.k1) * c->sz.rlwe_words;
+    return n * c->sz.model_words + (size_t)c->li.ext_grid * (3 + c->sz.k1) * c->sz.rlwe_words;
 }
 
 extern "C" size_t hw_infer_scratch_words(const hw_ctx* c, size_t n) {
     if (!c) return 0;
     (void)n;
-    return (size_t)c->li.ext_grid * 4 * c->sz.rlwe_words;
+    return (size_t)c->li.ext_grid * 3 * c->sz.rlwe_words;
 }
 
 #define CHECK_CTX(c)                                                   \

@@ -131,10 +131,12 @@ __global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP>::T, ExtCfg<LOGN, LOGE, 
     const DevCtx& C = *Cp;
     const int tid = threadIdx.x, T = blockDim.x;
     const size_t rl = C.rlwe_words;
-    u64* blk = scratch + (size_t)blockIdx.x * (4 + C.k1) * rl;
+    u64* blk = scratch + (size_t)blockIdx.x * (3 + C.k1) * rl;
     u64* acc[2] = {blk, blk + rl};
-    u64* accn[2] = {blk + 2 * rl, blk + 3 * rl};
-    u64* tn = blk + 4 * rl;  // evaluation forms of the tree slots
+    // one evaluation-form buffer, updated in place: the external product
+    // reads each thread's own words of a prime before it writes them
+    u64* accn = blk + 2 * rl;
+    u64* tn = blk + 3 * rl;  // evaluation forms of the tree slots
     const int kbits = C.L + C.a;
     for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
         const int i = item / C.k0, j = item % C.k0;
@@ -146,7 +148,7 @@ __global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP>::T, ExtCfg<LOGN, LOGE, 
             if (bit_slot(C, j, t) >= 0) last = t;
         // acc = trivial RLWE (0, Delta * 1); its evaluation form is Delta everywhere in b
         u64* first_dst = last >= 0 ? acc[0] : Lout;
-        u64* first_ntt = last >= 0 ? accn[0] : tn;
+        u64* first_ntt = last >= 0 ? accn : tn;
         for (size_t w = tid; w < rl; w += T) {
             size_t comp = w / ((size_t)C.r * C.n), rem = w % ((size_t)C.r * C.n);
             int p = (int)(rem / C.n), x = (int)(rem % C.n);
@@ -160,13 +162,13 @@ __global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP>::T, ExtCfg<LOGN, LOGE, 
             if (slot < 0) continue;  // constant-0 control: the CMUX keeps acc
             const int w = 1 << (t - C.z);
             u64* dst = (t == last) ? Lout : acc[cur ^ 1];
-            u64* dstn = (t == last) ? tn : accn[cur ^ 1];
+            u64* dstn = (t == last) ? tn : accn;
             int nslot = -1;  // the next encrypted control (rotation bit or first tree gate)
             for (int t2 = t + 1; t2 < kbits && nslot < 0; t2++) nslot = bit_slot(C, j, t2);
             if (nslot < 0 && C.n_gates > 0) nslot = bit_slot(C, j, C.gate_lvl[0]);
             ext_product<LOGN, LOGE, NP>(
                 C, sample + (size_t)slot * C.rgsw_words, acc[cur], w, acc[cur], 0, EXT_ADD, dst, xc,
-                ExtNtt{accn[cur], dstn, t - C.z, 0,
+                ExtNtt{accn, dstn, t - C.z, 0,
                        nslot >= 0 ? sample + (size_t)nslot * C.rgsw_words : nullptr, 1});
             cur ^= 1;
         }
@@ -221,9 +223,10 @@ __global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP>::T, ExtCfg<LOGN, LOGE, 
     const int tid = threadIdx.x, T = blockDim.x;
     const size_t rl = C.rlwe_words;
     const int two_n = 2 * C.n;
-    u64* blk = scratch + (size_t)blockIdx.x * 4 * rl;
+    u64* blk = scratch + (size_t)blockIdx.x * 3 * rl;
     u64* acc[2] = {blk, blk + rl};
-    u64* accn[2] = {blk + 2 * rl, blk + 3 * rl};
+    // one evaluation-form buffer, updated in place (see k_ivp_train)
+    u64* accn = blk + 2 * rl;
     const int kbits = C.L + C.a;
     const int l = C.n_classes;
     for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
@@ -290,7 +293,7 @@ __global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP>::T, ExtCfg<LOGN, LOGE, 
             int nslot = -1;
             if (c == 0)
                 for (int t2 = t + 1; t2 < kbits && nslot < 0; t2++) nslot = bit_slot(C, j, t2);
-            const ExtNtt nt{srcn, t == last ? nullptr : accn[cur ^ 1], t - C.z, 1,
+            const ExtNtt nt{srcn, t == last ? nullptr : accn, t - C.z, 1,
                             nslot >= 0 ? sample + (size_t)nslot * C.rgsw_words : nullptr, 0};
             if (t == last) {
                 ext_product<LOGN, LOGE, NP>(C, sample + (size_t)slot * C.rgsw_words, src, eA, src,
@@ -299,7 +302,7 @@ __global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP>::T, ExtCfg<LOGN, LOGE, 
                 ext_product<LOGN, LOGE, NP>(C, sample + (size_t)slot * C.rgsw_words, src, eA, src,
                                                   e0, EXT_ADD, acc[cur ^ 1], xc, nt);
                 src = acc[cur ^ 1];
-                srcn = accn[cur ^ 1];
+                srcn = accn;
                 cur ^= 1;
             }
             e0 = 0;
@@ -370,13 +373,13 @@ struct ExtVariant {
     static cudaError_t ivp(const LaunchInfo& li, const uint64_t* rgsw, int items, uint64_t* out,
                            uint64_t* acc, int grid, cudaStream_t st) {
         // per-block scratch: two accumulators, their evaluation forms, the tree slots
-        Launch L(li, grid, st, acc, (size_t)grid * (4 + li.k1) * li.rlwe_words * sizeof(u64));
+        Launch L(li, grid, st, acc, (size_t)grid * (3 + li.k1) * li.rlwe_words * sizeof(u64));
         return cudaLaunchKernelEx(&L.cfg, k_ivp_train<LOGN, LOGE, NP>, li.dctx, (const u64*)rgsw, items,
                                   (u64*)out, (u64*)acc);
     }
     static cudaError_t vp(const LaunchInfo& li, const uint64_t* model, const uint64_t* rgsw, int items,
                           uint64_t* resp, uint64_t* acc, int grid, cudaStream_t st) {
-        Launch L(li, grid, st, acc, (size_t)grid * 4 * li.rlwe_words * sizeof(u64));
+        Launch L(li, grid, st, acc, (size_t)grid * 3 * li.rlwe_words * sizeof(u64));
         return cudaLaunchKernelEx(&L.cfg, k_vp_infer<LOGN, LOGE, NP>, li.dctx, (const u64*)model,
                                   (const u64*)rgsw, items, (u64*)resp, (u64*)acc);
     }

@@ -89,6 +89,20 @@ __device__ __forceinline__ u64 rot_read(const u64* p, int x, int e, int n, u64 q
 }
 
 
+// RGSW rows are streamed once per (sample, RAM) step: loading them with an
+// L2 evict-first policy keeps them from displacing the per-block
+// accumulators, which are reread at the next step.  A hint only.
+__device__ __forceinline__ u64 rgsw_policy() {
+    u64 pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ u64 ld_rgsw(const u64* p, u64 pol) {
+    u64 v;
+    asm("ld.global.nc.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(v) : "l"(p), "l"(pol));
+    return v;
+}
+
 // A digit |d| < q_j lifted to [0, q_j).
 __device__ __forceinline__ u64 lift_small(int64_t d, u64 q) { return d >= 0 ? (u64)d : (u64)(d + (int64_t)q); }
 
@@ -583,6 +597,7 @@ __device__ __noinline__ void ext_product(const DevCtx& C, const u64* __restrict_
     // digits that need a forward transform at target prime j
     const int ndig = diag_in ? 2 * (r - 1) : 2 * C.dnum;
     // stream this product's RGSW and the next one's into L2 ahead of the MACs
+    const u64 rpol = rgsw_policy();
     if (nt.prefetch_cur) prefetch_l2(rgsw, C.rgsw_words);
     if (nt.next_rgsw) prefetch_l2(nt.next_rgsw, C.rgsw_words);
     __syncthreads();  // exchange buffers are free
@@ -605,7 +620,7 @@ __device__ __noinline__ void ext_product(const DevCtx& C, const u64* __restrict_
                 const u64* Rb = rgsw + ((size_t)(row * 2 + 1) * r + j) * N + tid;
 #pragma unroll
                 for (int e = 0; e < E; e++) {
-                    const u64 ra = __ldg(Ra + e * T), rb = __ldg(Rb + e * T);
+                    const u64 ra = ld_rgsw(Ra + e * T, rpol), rb = ld_rgsw(Rb + e * T, rpol);
                     u64 x = sn[e * T];
                     if (cmux_rot) {
                         const ulonglong2 t0 = __ldg(rtab + e * T);
@@ -654,7 +669,7 @@ __device__ __noinline__ void ext_product(const DevCtx& C, const u64* __restrict_
                 const u64* Rb = rgsw + ((size_t)(row * 2 + 1) * r + j) * N + tid;
 #pragma unroll
                 for (int e = 0; e < E; e++) {
-                    const u64 ra = __ldg(Ra + e * T), rb = __ldg(Rb + e * T);
+                    const u64 ra = ld_rgsw(Ra + e * T, rpol), rb = ld_rgsw(Rb + e * T, rpol);
                     const u64 x = v[pp][e];
                     acc[0][e] += redc_lazy(__umul64hi(x, ra), x * ra, qj, Pj.qneg);
                     acc[1][e] += redc_lazy(__umul64hi(x, rb), x * rb, qj, Pj.qneg);
