@@ -35,11 +35,12 @@ class HwSizes(ctypes.Structure):
             "resp_words", "sums_words")]
 
 
-GEOMETRY_FIELDS = ("ext_loge", "ext_np", "ext_blocks_per_sm", "ntt_loge", "ntt_limbs", "l2_persist")
+GEOMETRY_FIELDS = ("ext_loge", "ext_np", "ext_blocks_per_sm", "ntt_loge", "ntt_limbs", "ext_eval_smem",
+                   "l2_persist")
 
 
 class HwGeometry(ctypes.Structure):
-    _fields_ = [(name, ctypes.c_int32) for name in GEOMETRY_FIELDS] + [("reserved", ctypes.c_int32 * 2)]
+    _fields_ = [(name, ctypes.c_int32) for name in GEOMETRY_FIELDS] + [("reserved", ctypes.c_int32)]
 
 
 class HwTuneEntry(ctypes.Structure):

@@ -151,9 +151,18 @@ static int resolve_geometry(const hw_params* p, const hw_geometry* g, hw_geometr
     if (G.ext_np == 0) G.ext_np = default_ext_np(log_n);
     if (G.ntt_loge == 0) G.ntt_loge = 4;
     if (G.ntt_limbs == 0) G.ntt_limbs = small_q ? 1 : 2;
-    if (!hw_ext_find(log_n, G.ext_loge, G.ext_np))
-        return fail(HW_EINVAL, "external-product geometry (loge %d, np %d) is not built for log_n %d",
-                    G.ext_loge, G.ext_np, log_n);
+    if (G.ext_eval_smem != 0 && G.ext_eval_smem != 1) return fail(HW_EINVAL, "ext_eval_smem must be 0 or 1");
+    const ExtOps* ops = hw_ext_find(log_n, G.ext_loge, G.ext_np, G.ext_eval_smem);
+    if (!ops)
+        return fail(HW_EINVAL,
+                    "external-product geometry (loge %d, np %d, eval_smem %d) is not built for log_n %d",
+                    G.ext_loge, G.ext_np, G.ext_eval_smem, log_n);
+    if (ops->ev) {
+        const size_t rl_bytes = (size_t)2 * p->n_primes * ((size_t)1 << log_n) * sizeof(u64);
+        if (ops->smem + rl_bytes > (size_t)227 * 1024)
+            return fail(HW_EINVAL, "the evaluation form (%zu bytes) does not fit in shared memory beside "
+                        "the exchange buffer (%zu bytes)", rl_bytes, ops->smem);
+    }
     if (G.ext_blocks_per_sm < 0 || G.ext_blocks_per_sm > 32)
         return fail(HW_EINVAL, "ext_blocks_per_sm must be 0..32");
     if (G.ntt_loge != 3 && G.ntt_loge != 4) return fail(HW_EINVAL, "ntt_loge must be 3 or 4");
@@ -485,7 +494,8 @@ extern "C" int hw_create_tuned(const hw_params* p, const hw_geometry* g, int cud
     c->dctx = (DevCtx*)put(&H, sizeof(DevCtx));
     LaunchInfo& li = c->li;
     li.log_n = log_n;
-    li.ext = hw_ext_find(log_n, G.ext_loge, G.ext_np);
+    li.ext = hw_ext_find(log_n, G.ext_loge, G.ext_np, G.ext_eval_smem);
+    li.ext_smem = li.ext->smem + (li.ext->ev ? (size_t)H.rlwe_words * sizeof(u64) : 0);
     li.ntt_loge = G.ntt_loge;
     li.ntt_limbs = G.ntt_limbs;
     e = hw_kernels_init(li);
@@ -541,7 +551,7 @@ extern "C" int hw_create_tuned(const hw_params* p, const hw_geometry* g, int cud
     li.small_q = p->prime_bits <= 30 ? 1 : 0;
     li.launches = &c->launches;
     {
-        int occ = li.ext->occupancy();
+        int occ = li.ext->occupancy(li.ext_smem);
         if (G.ext_blocks_per_sm > 0 && G.ext_blocks_per_sm < occ) occ = G.ext_blocks_per_sm;
         G.ext_blocks_per_sm = occ;
         li.ext_grid = occ * sms;
@@ -556,7 +566,7 @@ extern "C" int hw_create_tuned(const hw_params* p, const hw_geometry* g, int cud
         int max_persist = 0, max_window = 0;
         cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, cuda_device);
         cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize, cuda_device);
-        size_t want = (size_t)li.ext_grid * 3 * H.rlwe_words * sizeof(u64);
+        size_t want = (size_t)li.ext_grid * li.ext->scratch_rlwe * H.rlwe_words * sizeof(u64);
         if (want > (size_t)max_persist) want = (size_t)max_persist;
         size_t cur = 0;
         cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize);
@@ -589,17 +599,18 @@ extern "C" int hw_list_geometries(const hw_params* p, hw_geometry* out, size_t m
     const ExtOps* t = hw_ext_table(p->log_n, &nt);
     const int d_loge = default_ext_loge(p->log_n), d_np = default_ext_np(p->log_n);
     size_t k = 0;
-    auto emit = [&](int loge, int np) {
+    auto emit = [&](int loge, int np, int ev) {
         if (out && k < max) {
             memset(&out[k], 0, sizeof(hw_geometry));
             out[k].ext_loge = loge;
             out[k].ext_np = np;
+            out[k].ext_eval_smem = ev;
         }
         k++;
     };
-    emit(d_loge, d_np);
+    emit(d_loge, d_np, 0);
     for (int i = 0; i < nt; i++)
-        if (!(t[i].loge == d_loge && t[i].np == d_np)) emit(t[i].loge, t[i].np);
+        if (!(t[i].loge == d_loge && t[i].np == d_np && t[i].ev == 0)) emit(t[i].loge, t[i].np, t[i].ev);
     *count = k;
     return HW_OK;
 }
@@ -635,18 +646,19 @@ int hw_ctx_fail(int code, const char* msg) { return fail(code, "%s", msg); }
 
 extern "C" const char* hw_last_error(void) { return g_last_error.c_str(); }
 
-// Persistent-grid scratch per block: two accumulators and one evaluation-form
-// buffer (inference), plus the evaluation forms of the k1 tree slots
-// (training).
+// Persistent-grid scratch per block: two accumulators and, unless it lives in
+// shared memory, one evaluation-form buffer (inference), plus the evaluation
+// forms of the k1 tree slots (training).
 extern "C" size_t hw_train_scratch_words(const hw_ctx* c, size_t n) {
     if (!c) return 0;
-    return n * c->sz.model_words + (size_t)c->li.ext_grid * (3 + c->sz.k1) * c->sz.rlwe_words;
+    return n * c->sz.model_words +
+           (size_t)c->li.ext_grid * (c->li.ext->scratch_rlwe + c->sz.k1) * c->sz.rlwe_words;
 }
 
 extern "C" size_t hw_infer_scratch_words(const hw_ctx* c, size_t n) {
     if (!c) return 0;
     (void)n;
-    return (size_t)c->li.ext_grid * 3 * c->sz.rlwe_words;
+    return (size_t)c->li.ext_grid * c->li.ext->scratch_rlwe * c->sz.rlwe_words;
 }
 
 #define CHECK_CTX(c)                                                   \

@@ -121,22 +121,24 @@ __global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP>::T, ExtCfg<LOGN, LOGE, 
 // Per-block scratch: two accumulators, their evaluation forms, and the
 // evaluation forms of the k1 tree slots.
 // ---------------------------------------------------------------------------
-template <int LOGN, int LOGE, int NP>
-__global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP>::T, ExtCfg<LOGN, LOGE, NP>::MINB)
+template <int LOGN, int LOGE, int NP, int EV>
+__global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP, EV>::T, ExtCfg<LOGN, LOGE, NP, EV>::MINB)
     k_ivp_train(const DevCtx* __restrict__ Cp, const u64* __restrict__ rgsw, int n_items,
                 u64* __restrict__ out, u64* __restrict__ scratch) {
-    using X = ExtCfg<LOGN, LOGE, NP>;
+    using X = ExtCfg<LOGN, LOGE, NP, EV>;
     extern __shared__ u64 smem[];
-    Xchg xc{smem, smem + NP * X::PADDED, X::PADDED, 0};
+    Xchg xc{smem, EV ? smem : smem + NP * X::PADDED, X::PADDED, 0};
     const DevCtx& C = *Cp;
     const int tid = threadIdx.x, T = blockDim.x;
     const size_t rl = C.rlwe_words;
-    u64* blk = scratch + (size_t)blockIdx.x * (3 + C.k1) * rl;
+    constexpr int NB = EV ? 2 : 3;  // per-block RLWE buffers besides the tree
+    u64* blk = scratch + (size_t)blockIdx.x * (NB + C.k1) * rl;
     u64* acc[2] = {blk, blk + rl};
-    // one evaluation-form buffer, updated in place: the external product
-    // reads each thread's own words of a prime before it writes them
-    u64* accn = blk + 2 * rl;
-    u64* tn = blk + 3 * rl;  // evaluation forms of the tree slots
+    // one evaluation-form buffer (in shared memory with EV), updated in
+    // place: the external product reads each thread's own words of a prime
+    // before it writes them
+    u64* accn = EV ? smem + NP * X::PADDED : blk + 2 * rl;
+    u64* tn = blk + NB * rl;  // evaluation forms of the tree slots
     const int kbits = C.L + C.a;
     for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
         const int i = item / C.k0, j = item % C.k0;
@@ -211,22 +213,23 @@ __global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP>::T, ExtCfg<LOGN, LOGE, 
 // weights +2^k (X^-2^k) and the last CMUX writes ExtractLWE(., 0) directly.
 // Per-block scratch: two accumulators and their evaluation forms.
 // ---------------------------------------------------------------------------
-template <int LOGN, int LOGE, int NP>
-__global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP>::T, ExtCfg<LOGN, LOGE, NP>::MINB)
+template <int LOGN, int LOGE, int NP, int EV>
+__global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP, EV>::T, ExtCfg<LOGN, LOGE, NP, EV>::MINB)
     k_vp_infer(const DevCtx* __restrict__ Cp, const u64* __restrict__ model,
                const u64* __restrict__ rgsw, int n_items, u64* __restrict__ resp,
                u64* __restrict__ scratch) {
-    using X = ExtCfg<LOGN, LOGE, NP>;
+    using X = ExtCfg<LOGN, LOGE, NP, EV>;
     extern __shared__ u64 smem[];
-    Xchg xc{smem, smem + NP * X::PADDED, X::PADDED, 0};
+    Xchg xc{smem, EV ? smem : smem + NP * X::PADDED, X::PADDED, 0};
     const DevCtx& C = *Cp;
     const int tid = threadIdx.x, T = blockDim.x;
     const size_t rl = C.rlwe_words;
     const int two_n = 2 * C.n;
-    u64* blk = scratch + (size_t)blockIdx.x * 3 * rl;
+    u64* blk = scratch + (size_t)blockIdx.x * (EV ? 2 : 3) * rl;
     u64* acc[2] = {blk, blk + rl};
-    // one evaluation-form buffer, updated in place (see k_ivp_train)
-    u64* accn = blk + 2 * rl;
+    // one evaluation-form buffer (in shared memory with EV), updated in
+    // place (see k_ivp_train)
+    u64* accn = EV ? smem + NP * X::PADDED : blk + 2 * rl;
     const int kbits = C.L + C.a;
     const int l = C.n_classes;
     for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
@@ -313,27 +316,31 @@ __global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP>::T, ExtCfg<LOGN, LOGE, 
 // ---------------------------------------------------------------------------
 // Launch table of one geometry
 // ---------------------------------------------------------------------------
-template <int LOGN, int LOGE, int NP>
+template <int LOGN, int LOGE, int NP, int EV>
 struct ExtVariant {
-    using X = ExtCfg<LOGN, LOGE, NP>;
-    static constexpr size_t ENC_SMEM = X::XCHG_BYTES + (size_t)Ring<LOGN>::N * 9;
+    using X = ExtCfg<LOGN, LOGE, NP, EV>;
+    using XE = ExtCfg<LOGN, LOGE, NP, 0>;  // encryption never holds an evaluation form
+    static constexpr size_t ENC_SMEM = XE::XCHG_BYTES + (size_t)Ring<LOGN>::N * 9;
+    static constexpr int MAX_SMEM = 227 * 1024;
 
     static cudaError_t init() {
         cudaError_t e = cudaFuncSetAttribute(k_encrypt<LOGN, LOGE, NP>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ENC_SMEM);
+        const int smem = EV ? MAX_SMEM : (int)X::XCHG_BYTES;
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_ivp_train<LOGN, LOGE, NP>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)X::XCHG_BYTES);
+            e = cudaFuncSetAttribute(k_ivp_train<LOGN, LOGE, NP, EV>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_vp_infer<LOGN, LOGE, NP>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)X::XCHG_BYTES);
+            e = cudaFuncSetAttribute(k_vp_infer<LOGN, LOGE, NP, EV>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         return e;
     }
-    // resident blocks per SM of the persistent kernels (the smaller of the two)
-    static int occupancy() {
+    // resident blocks per SM of the persistent kernels (the smaller of the
+    // two) at `smem` bytes of dynamic shared memory per block
+    static int occupancy(size_t smem) {
         int a = 0, b = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_ivp_train<LOGN, LOGE, NP>, X::T, X::XCHG_BYTES);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_vp_infer<LOGN, LOGE, NP>, X::T, X::XCHG_BYTES);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_ivp_train<LOGN, LOGE, NP, EV>, X::T, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_vp_infer<LOGN, LOGE, NP, EV>, X::T, smem);
         int o = a < b ? a : b;
         return o < 1 ? 1 : o;
     }
@@ -354,7 +361,7 @@ struct ExtVariant {
             memset(&attr, 0, sizeof(attr));
             cfg.gridDim = dim3(grid);
             cfg.blockDim = dim3(X::T);
-            cfg.dynamicSmemBytes = X::XCHG_BYTES;
+            cfg.dynamicSmemBytes = li.ext_smem;
             cfg.stream = st;
             if (li.l2_persist > 0 && window > 0) {
                 if (window > li.l2_window_max) window = li.l2_window_max;
@@ -370,25 +377,27 @@ struct ExtVariant {
             }
         }
     };
+    static constexpr int SCRATCH_RLWE = EV ? 2 : 3;  // per-block RLWE buffers (inference)
     static cudaError_t ivp(const LaunchInfo& li, const uint64_t* rgsw, int items, uint64_t* out,
                            uint64_t* acc, int grid, cudaStream_t st) {
-        // per-block scratch: two accumulators, their evaluation forms, the tree slots
-        Launch L(li, grid, st, acc, (size_t)grid * (3 + li.k1) * li.rlwe_words * sizeof(u64));
-        return cudaLaunchKernelEx(&L.cfg, k_ivp_train<LOGN, LOGE, NP>, li.dctx, (const u64*)rgsw, items,
+        // per-block scratch: two accumulators, (their evaluation form,) the tree slots
+        Launch L(li, grid, st, acc, (size_t)grid * (SCRATCH_RLWE + li.k1) * li.rlwe_words * sizeof(u64));
+        return cudaLaunchKernelEx(&L.cfg, k_ivp_train<LOGN, LOGE, NP, EV>, li.dctx, (const u64*)rgsw, items,
                                   (u64*)out, (u64*)acc);
     }
     static cudaError_t vp(const LaunchInfo& li, const uint64_t* model, const uint64_t* rgsw, int items,
                           uint64_t* resp, uint64_t* acc, int grid, cudaStream_t st) {
-        Launch L(li, grid, st, acc, (size_t)grid * 3 * li.rlwe_words * sizeof(u64));
-        return cudaLaunchKernelEx(&L.cfg, k_vp_infer<LOGN, LOGE, NP>, li.dctx, (const u64*)model,
+        Launch L(li, grid, st, acc, (size_t)grid * SCRATCH_RLWE * li.rlwe_words * sizeof(u64));
+        return cudaLaunchKernelEx(&L.cfg, k_vp_infer<LOGN, LOGE, NP, EV>, li.dctx, (const u64*)model,
                                   (const u64*)rgsw, items, (u64*)resp, (u64*)acc);
     }
     static ExtOps ops() {
-        return ExtOps{LOGE, NP, X::T, X::XCHG_BYTES, ENC_SMEM, &init, &occupancy, &encrypt, &ivp, &vp};
+        return ExtOps{LOGE, NP, EV, SCRATCH_RLWE, X::T, X::XCHG_BYTES, ENC_SMEM, &init, &occupancy,
+                      &encrypt, &ivp, &vp};
     }
 };
 
-#define HW_EXT_VARIANT(L, E, P) ExtVariant<L, E, P>::ops(),
+#define HW_EXT_VARIANT(L, E, P, V) ExtVariant<L, E, P, V>::ops(),
 // Defines hw_ext_table_<L>: the geometries instantiated for N = 2^L.
 #define HW_EXT_TABLE(L, LIST)                                 \
     const ExtOps* hw_ext_table_##L(int* count) {              \

@@ -264,7 +264,8 @@ __device__ __forceinline__ void inv_round(u64 (&v)[NP][1 << LOGE], const ulonglo
 // Exchange buffers: two sets, alternated between exchanges (par) so that
 // one barrier per exchange suffices -- a set is rewritten only two exchanges
 // after it was read, with a barrier in between.  Each set holds NP padded
-// polynomials (stride `stride` words).
+// polynomials (stride `stride` words).  With b0 == b1 (one set, half the
+// shared memory) each exchange takes a second barrier before its writes.
 struct Xchg {
     u64* b0;
     u64* b1;
@@ -285,6 +286,7 @@ __device__ __forceinline__ void fwd_from(u64 (&v)[NP][1 << LOGE], Xchg& xc,
     if constexpr (ST0 + R < LOGN) {
         constexpr int R2 = FwdR<LOGN, LOGE, ST0 + R>::R, G2 = (1 << LOGE) >> R2;
         u64* sm = xc.next();
+        if (xc.b0 == xc.b1) __syncthreads();  // one buffer: the last exchange's reads are done
 #pragma unroll
         for (int pp = 0; pp < NP; pp++)
 #pragma unroll
@@ -312,6 +314,7 @@ __device__ __forceinline__ void inv_from(u64 (&v)[NP][1 << LOGE], Xchg& xc,
     if constexpr (P0 + R < LOGN) {
         constexpr int R2 = InvR<LOGN, LOGE, P0 + R>::R, G2 = (1 << LOGE) >> R2;
         u64* sm = xc.next();
+        if (xc.b0 == xc.b1) __syncthreads();  // one buffer: the last exchange's reads are done
 #pragma unroll
         for (int pp = 0; pp < NP; pp++)
 #pragma unroll
@@ -435,6 +438,7 @@ __device__ __forceinline__ void fwd_from32(u32 (&v)[NP][1 << LOGE], Xchg& xc,
     if constexpr (ST0 + R < LOGN) {
         constexpr int R2 = FwdR<LOGN, LOGE, ST0 + R>::R, G2 = (1 << LOGE) >> R2;
         u32* sm = (u32*)xc.next();
+        if (xc.b0 == xc.b1) __syncthreads();  // one buffer: the last exchange's reads are done
 #pragma unroll
         for (int pp = 0; pp < NP; pp++)
 #pragma unroll
@@ -462,6 +466,7 @@ __device__ __forceinline__ void inv_from32(u32 (&v)[NP][1 << LOGE], Xchg& xc,
     if constexpr (P0 + R < LOGN) {
         constexpr int R2 = InvR<LOGN, LOGE, P0 + R>::R, G2 = (1 << LOGE) >> R2;
         u32* sm = (u32*)xc.next();
+        if (xc.b0 == xc.b1) __syncthreads();  // one buffer: the last exchange's reads are done
 #pragma unroll
         for (int pp = 0; pp < NP; pp++)
 #pragma unroll
@@ -749,18 +754,20 @@ __device__ __noinline__ void ext_product(const DevCtx& C, const u64* __restrict_
 
 // Launch geometry of the external-product kernels: 2^LOGE residues per
 // thread, NP polynomials transformed together, T = N / 2^LOGE threads.
-template <int LOGN, int LOGE, int NP_>
+template <int LOGN, int LOGE, int NP_, int EV = 0>
 struct ExtCfg {
     static constexpr int LOGE_ = LOGE;
     static constexpr int NP = NP_;
     static constexpr int T = Ring<LOGN, LOGE>::T;
     static constexpr int PADDED = Ring<LOGN, LOGE>::PADDED;
-    static constexpr size_t XCHG_BYTES = 2 * (size_t)NP * PADDED * sizeof(u64);
+    // EV = 1: one exchange set, the rest of shared memory holds the
+    // accumulator's evaluation form (its size depends on r: added at launch)
+    static constexpr size_t XCHG_BYTES = (EV ? 1 : 2) * (size_t)NP * PADDED * sizeof(u64);
     // blocks that can be resident per SM by shared memory (227 KiB, 1 KiB
     // reserved per block) and by a 512-thread target; the register cap the
     // compiler gets follows from the smaller, so a block that only fits once
     // per SM is not squeezed into registers it cannot use
-    static constexpr int SMEM_BLOCKS = (int)((227 * 1024) / (XCHG_BYTES + 1024));
+    static constexpr int SMEM_BLOCKS = EV ? 1 : (int)((227 * 1024) / (XCHG_BYTES + 1024));
     static constexpr int THR_BLOCKS = (512 / T) < 1 ? 1 : (512 / T);
     static constexpr int MINB0 = SMEM_BLOCKS < THR_BLOCKS ? SMEM_BLOCKS : THR_BLOCKS;
     static constexpr int MINB = MINB0 < 1 ? 1 : (MINB0 > 16 ? 16 : MINB0);

@@ -11,10 +11,13 @@ struct LaunchInfo;
 // Launchers of one external-product geometry (hw_ext.cuh): 2^loge residues
 // per thread, np polynomials per transform, `threads` threads per block.
 struct ExtOps {
-    int loge, np, threads;
-    size_t smem, encrypt_smem;
-    cudaError_t (*init)();   // shared-memory attributes of its kernels
-    int (*occupancy)();      // resident blocks per SM of the IVP / VP kernels
+    int loge, np;
+    int ev;            // 1: the accumulator's evaluation form lives in shared memory
+    int scratch_rlwe;  // per-block RLWE buffers of inference (training adds k1)
+    int threads;
+    size_t smem, encrypt_smem;  // smem: exchange buffers (+ r-dependent evaluation form with ev)
+    cudaError_t (*init)();      // shared-memory attributes of its kernels
+    int (*occupancy)(size_t smem);  // resident blocks per SM of the IVP / VP kernels
     cudaError_t (*encrypt)(const LaunchInfo&, const uint64_t* key, const uint8_t* bits,
                            const uint32_t* labels, int slot0, int n_enc, unsigned blocks,
                            uint64_t seed, uint64_t first, uint64_t* out, cudaStream_t);
@@ -32,6 +35,7 @@ struct LaunchInfo {
     int small_q;  // every q_i < 2^30: the 32-bit transform tables exist
     const ExtOps* ext;  // the context's external-product geometry
     int ext_grid;       // persistent grid of the IVP / VP kernels
+    size_t ext_smem;    // their dynamic shared memory per block
     int ntt_loge;       // hw_ntt_*: 2^ntt_loge residues per thread
     int ntt_limbs;      // hw_ntt_*: 1 = 32-bit arithmetic, 2 = 64-bit
     size_t l2_persist;     // > 0: persisting L2 bytes for the IVP / VP accumulators
@@ -45,7 +49,7 @@ HW_EXT_TABLE_DECL(6) HW_EXT_TABLE_DECL(7) HW_EXT_TABLE_DECL(8) HW_EXT_TABLE_DECL
 HW_EXT_TABLE_DECL(10) HW_EXT_TABLE_DECL(11) HW_EXT_TABLE_DECL(12) HW_EXT_TABLE_DECL(13)
 #undef HW_EXT_TABLE_DECL
 const ExtOps* hw_ext_table(int log_n, int* count);
-const ExtOps* hw_ext_find(int log_n, int loge, int np);
+const ExtOps* hw_ext_find(int log_n, int loge, int np, int ev);
 
 cudaError_t launch_keygen(const LaunchInfo& li, uint64_t seed, uint64_t* key, cudaStream_t st);
 cudaError_t launch_encode(const LaunchInfo& li, const uint8_t* values, size_t n, uint8_t* bits,
