@@ -110,9 +110,11 @@ typedef struct hw_geometry {
     int32_t ntt_loge;          /* hw_ntt_forward/inverse: 2^ntt_loge residues per thread; 3 or 4 */
     int32_t ntt_limbs;         /* hw_ntt_forward/inverse: 32-bit words per residue in the arithmetic:
                                   1 (only when every q_i < 2^30) or 2 */
-    int32_t ext_eval_smem;     /* 1: the training / inference kernels keep the accumulator's
-                                  evaluation form in shared memory (one exchange buffer instead
-                                  of two); only where it fits: HW_EINVAL otherwise */
+    int32_t ext_smem;          /* what else the training / inference kernels keep in shared
+                                  memory beside one exchange buffer (instead of two): 0 nothing;
+                                  1 the accumulator's evaluation form (2*r*N words; HW_EINVAL
+                                  where it does not fit); 2 the accumulator polynomials of the
+                                  prime being processed (2*N words, off the registers) */
     int32_t l2_persist;        /* 1: the training / inference kernels mark their per-block
                                   accumulators persisting in L2 (an access-policy window on each
                                   launch and a persisting set-aside of this process's context,
@@ -128,8 +130,8 @@ int hw_create_tuned(const hw_params* params, const hw_geometry* geometry, int cu
 /* The context's geometry with every default resolved. */
 int hw_get_geometry(const hw_ctx* ctx, hw_geometry* out);
 /* The external-product geometries built for params->log_n (ext_loge,
- * ext_np, ext_eval_smem set; other fields 0), default first; a listed
- * geometry with ext_eval_smem may still not fit a parameter set.  Host only: needs no GPU.
+ * ext_np, ext_smem set; other fields 0), default first; a listed
+ * geometry with ext_smem = 1 may still not fit a parameter set.  Host only: needs no GPU.
  * Writes min(*count, max) entries; *count = the number available. */
 int hw_list_geometries(const hw_params* params, hw_geometry* out_host, size_t max, size_t* count);
 

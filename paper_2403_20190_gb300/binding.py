@@ -35,7 +35,7 @@ class HwSizes(ctypes.Structure):
             "resp_words", "sums_words")]
 
 
-GEOMETRY_FIELDS = ("ext_loge", "ext_np", "ext_blocks_per_sm", "ntt_loge", "ntt_limbs", "ext_eval_smem",
+GEOMETRY_FIELDS = ("ext_loge", "ext_np", "ext_blocks_per_sm", "ntt_loge", "ntt_limbs", "ext_smem",
                    "l2_persist")
 
 

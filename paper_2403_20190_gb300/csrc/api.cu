@@ -151,13 +151,13 @@ static int resolve_geometry(const hw_params* p, const hw_geometry* g, hw_geometr
     if (G.ext_np == 0) G.ext_np = default_ext_np(log_n);
     if (G.ntt_loge == 0) G.ntt_loge = 4;
     if (G.ntt_limbs == 0) G.ntt_limbs = small_q ? 1 : 2;
-    if (G.ext_eval_smem != 0 && G.ext_eval_smem != 1) return fail(HW_EINVAL, "ext_eval_smem must be 0 or 1");
-    const ExtOps* ops = hw_ext_find(log_n, G.ext_loge, G.ext_np, G.ext_eval_smem);
+    if (G.ext_smem < 0 || G.ext_smem > 2) return fail(HW_EINVAL, "ext_smem must be 0, 1 or 2");
+    const ExtOps* ops = hw_ext_find(log_n, G.ext_loge, G.ext_np, G.ext_smem);
     if (!ops)
         return fail(HW_EINVAL,
-                    "external-product geometry (loge %d, np %d, eval_smem %d) is not built for log_n %d",
-                    G.ext_loge, G.ext_np, G.ext_eval_smem, log_n);
-    if (ops->ev) {
+                    "external-product geometry (loge %d, np %d, smem mode %d) is not built for log_n %d",
+                    G.ext_loge, G.ext_np, G.ext_smem, log_n);
+    if (ops->sm == 1) {
         const size_t rl_bytes = (size_t)2 * p->n_primes * ((size_t)1 << log_n) * sizeof(u64);
         if (ops->smem + rl_bytes > (size_t)227 * 1024)
             return fail(HW_EINVAL, "the evaluation form (%zu bytes) does not fit in shared memory beside "
@@ -494,8 +494,8 @@ extern "C" int hw_create_tuned(const hw_params* p, const hw_geometry* g, int cud
     c->dctx = (DevCtx*)put(&H, sizeof(DevCtx));
     LaunchInfo& li = c->li;
     li.log_n = log_n;
-    li.ext = hw_ext_find(log_n, G.ext_loge, G.ext_np, G.ext_eval_smem);
-    li.ext_smem = li.ext->smem + (li.ext->ev ? (size_t)H.rlwe_words * sizeof(u64) : 0);
+    li.ext = hw_ext_find(log_n, G.ext_loge, G.ext_np, G.ext_smem);
+    li.ext_smem = li.ext->smem + (li.ext->sm == 1 ? (size_t)H.rlwe_words * sizeof(u64) : 0);
     li.ntt_loge = G.ntt_loge;
     li.ntt_limbs = G.ntt_limbs;
     e = hw_kernels_init(li);
@@ -599,18 +599,18 @@ extern "C" int hw_list_geometries(const hw_params* p, hw_geometry* out, size_t m
     const ExtOps* t = hw_ext_table(p->log_n, &nt);
     const int d_loge = default_ext_loge(p->log_n), d_np = default_ext_np(p->log_n);
     size_t k = 0;
-    auto emit = [&](int loge, int np, int ev) {
+    auto emit = [&](int loge, int np, int sm) {
         if (out && k < max) {
             memset(&out[k], 0, sizeof(hw_geometry));
             out[k].ext_loge = loge;
             out[k].ext_np = np;
-            out[k].ext_eval_smem = ev;
+            out[k].ext_smem = sm;
         }
         k++;
     };
     emit(d_loge, d_np, 0);
     for (int i = 0; i < nt; i++)
-        if (!(t[i].loge == d_loge && t[i].np == d_np && t[i].ev == 0)) emit(t[i].loge, t[i].np, t[i].ev);
+        if (!(t[i].loge == d_loge && t[i].np == d_np && t[i].sm == 0)) emit(t[i].loge, t[i].np, t[i].sm);
     *count = k;
     return HW_OK;
 }

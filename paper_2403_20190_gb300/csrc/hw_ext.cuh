@@ -121,23 +121,24 @@ __global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP>::T, ExtCfg<LOGN, LOGE, 
 // Per-block scratch: two accumulators, their evaluation forms, and the
 // evaluation forms of the k1 tree slots.
 // ---------------------------------------------------------------------------
-template <int LOGN, int LOGE, int NP, int EV>
-__global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP, EV>::T, ExtCfg<LOGN, LOGE, NP, EV>::MINB)
+template <int LOGN, int LOGE, int NP, int SM>
+__global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP, SM>::T, ExtCfg<LOGN, LOGE, NP, SM>::MINB)
     k_ivp_train(const DevCtx* __restrict__ Cp, const u64* __restrict__ rgsw, int n_items,
                 u64* __restrict__ out, u64* __restrict__ scratch) {
-    using X = ExtCfg<LOGN, LOGE, NP, EV>;
+    using X = ExtCfg<LOGN, LOGE, NP, SM>;
     extern __shared__ u64 smem[];
-    Xchg xc{smem, EV ? smem : smem + NP * X::PADDED, X::PADDED, 0};
+    Xchg xc{smem, SM ? smem : smem + NP * X::PADDED, X::PADDED, 0};
+    if (SM == 2) xc.accs = smem + NP * X::PADDED;
     const DevCtx& C = *Cp;
     const int tid = threadIdx.x, T = blockDim.x;
     const size_t rl = C.rlwe_words;
-    constexpr int NB = EV ? 2 : 3;  // per-block RLWE buffers besides the tree
+    constexpr int NB = SM == 1 ? 2 : 3;  // per-block RLWE buffers besides the tree
     u64* blk = scratch + (size_t)blockIdx.x * (NB + C.k1) * rl;
     u64* acc[2] = {blk, blk + rl};
-    // one evaluation-form buffer (in shared memory with EV), updated in
+    // one evaluation-form buffer (in shared memory in mode 1), updated in
     // place: the external product reads each thread's own words of a prime
     // before it writes them
-    u64* accn = EV ? smem + NP * X::PADDED : blk + 2 * rl;
+    u64* accn = SM == 1 ? smem + NP * X::PADDED : blk + 2 * rl;
     u64* tn = blk + NB * rl;  // evaluation forms of the tree slots
     const int kbits = C.L + C.a;
     for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
@@ -168,7 +169,7 @@ __global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP, EV>::T, ExtCfg<LOGN, LO
             int nslot = -1;  // the next encrypted control (rotation bit or first tree gate)
             for (int t2 = t + 1; t2 < kbits && nslot < 0; t2++) nslot = bit_slot(C, j, t2);
             if (nslot < 0 && C.n_gates > 0) nslot = bit_slot(C, j, C.gate_lvl[0]);
-            ext_product<LOGN, LOGE, NP>(
+            ext_product<LOGN, LOGE, NP, SM == 2>(
                 C, sample + (size_t)slot * C.rgsw_words, acc[cur], w, acc[cur], 0, EXT_ADD, dst, xc,
                 ExtNtt{accn, dstn, t - C.z, 0,
                        nslot >= 0 ? sample + (size_t)nslot * C.rgsw_words : nullptr, 1});
@@ -190,7 +191,7 @@ __global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP, EV>::T, ExtCfg<LOGN, LO
                 continue;
             }
             const int nslot = g + 1 < C.n_gates ? bit_slot(C, j, C.gate_lvl[g + 1]) : -1;
-            ext_product<LOGN, LOGE, NP>(
+            ext_product<LOGN, LOGE, NP, SM == 2>(
                 C, sample + (size_t)slot * C.rgsw_words, lo, 0, nullptr, 0, EXT_PLAIN, hi, xc,
                 ExtNtt{lon, hin, -1, 0, nslot >= 0 ? sample + (size_t)nslot * C.rgsw_words : nullptr,
                        1});
@@ -213,23 +214,24 @@ __global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP, EV>::T, ExtCfg<LOGN, LO
 // weights +2^k (X^-2^k) and the last CMUX writes ExtractLWE(., 0) directly.
 // Per-block scratch: two accumulators and their evaluation forms.
 // ---------------------------------------------------------------------------
-template <int LOGN, int LOGE, int NP, int EV>
-__global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP, EV>::T, ExtCfg<LOGN, LOGE, NP, EV>::MINB)
+template <int LOGN, int LOGE, int NP, int SM>
+__global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP, SM>::T, ExtCfg<LOGN, LOGE, NP, SM>::MINB)
     k_vp_infer(const DevCtx* __restrict__ Cp, const u64* __restrict__ model,
                const u64* __restrict__ rgsw, int n_items, u64* __restrict__ resp,
                u64* __restrict__ scratch) {
-    using X = ExtCfg<LOGN, LOGE, NP, EV>;
+    using X = ExtCfg<LOGN, LOGE, NP, SM>;
     extern __shared__ u64 smem[];
-    Xchg xc{smem, EV ? smem : smem + NP * X::PADDED, X::PADDED, 0};
+    Xchg xc{smem, SM ? smem : smem + NP * X::PADDED, X::PADDED, 0};
+    if (SM == 2) xc.accs = smem + NP * X::PADDED;
     const DevCtx& C = *Cp;
     const int tid = threadIdx.x, T = blockDim.x;
     const size_t rl = C.rlwe_words;
     const int two_n = 2 * C.n;
-    u64* blk = scratch + (size_t)blockIdx.x * (EV ? 2 : 3) * rl;
+    u64* blk = scratch + (size_t)blockIdx.x * (SM == 1 ? 2 : 3) * rl;
     u64* acc[2] = {blk, blk + rl};
-    // one evaluation-form buffer (in shared memory with EV), updated in
+    // one evaluation-form buffer (in shared memory in mode 1), updated in
     // place (see k_ivp_train)
-    u64* accn = EV ? smem + NP * X::PADDED : blk + 2 * rl;
+    u64* accn = SM == 1 ? smem + NP * X::PADDED : blk + 2 * rl;
     const int kbits = C.L + C.a;
     const int l = C.n_classes;
     for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
@@ -257,7 +259,7 @@ __global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP, EV>::T, ExtCfg<LOGN, LO
             if (slot < 0) {
                 src = lo;
             } else {
-                ext_product<LOGN, LOGE, NP>(C, sample + (size_t)slot * C.rgsw_words, hi, 0, lo,
+                ext_product<LOGN, LOGE, NP, SM == 2>(C, sample + (size_t)slot * C.rgsw_words, hi, 0, lo,
                                                   0, EXT_ADD, acc[0], xc,
                                                   ExtNtt{nullptr, nullptr, -1, 0, nullptr, 0});
                 src = acc[0];
@@ -299,10 +301,10 @@ __global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP, EV>::T, ExtCfg<LOGN, LO
             const ExtNtt nt{srcn, t == last ? nullptr : accn, t - C.z, 1,
                             nslot >= 0 ? sample + (size_t)nslot * C.rgsw_words : nullptr, 0};
             if (t == last) {
-                ext_product<LOGN, LOGE, NP>(C, sample + (size_t)slot * C.rgsw_words, src, eA, src,
+                ext_product<LOGN, LOGE, NP, SM == 2>(C, sample + (size_t)slot * C.rgsw_words, src, eA, src,
                                                   e0, EXT_LWE, lwe, xc, nt);
             } else {
-                ext_product<LOGN, LOGE, NP>(C, sample + (size_t)slot * C.rgsw_words, src, eA, src,
+                ext_product<LOGN, LOGE, NP, SM == 2>(C, sample + (size_t)slot * C.rgsw_words, src, eA, src,
                                                   e0, EXT_ADD, acc[cur ^ 1], xc, nt);
                 src = acc[cur ^ 1];
                 srcn = accn;
@@ -316,22 +318,22 @@ __global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP, EV>::T, ExtCfg<LOGN, LO
 // ---------------------------------------------------------------------------
 // Launch table of one geometry
 // ---------------------------------------------------------------------------
-template <int LOGN, int LOGE, int NP, int EV>
+template <int LOGN, int LOGE, int NP, int SM>
 struct ExtVariant {
-    using X = ExtCfg<LOGN, LOGE, NP, EV>;
-    using XE = ExtCfg<LOGN, LOGE, NP, 0>;  // encryption never holds an evaluation form
+    using X = ExtCfg<LOGN, LOGE, NP, SM>;
+    using XE = ExtCfg<LOGN, LOGE, NP, 0>;  // encryption keeps nothing else in shared memory
     static constexpr size_t ENC_SMEM = XE::XCHG_BYTES + (size_t)Ring<LOGN>::N * 9;
     static constexpr int MAX_SMEM = 227 * 1024;
 
     static cudaError_t init() {
         cudaError_t e = cudaFuncSetAttribute(k_encrypt<LOGN, LOGE, NP>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ENC_SMEM);
-        const int smem = EV ? MAX_SMEM : (int)X::XCHG_BYTES;
+        const int smem = SM == 1 ? MAX_SMEM : (int)X::FIXED_BYTES;
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_ivp_train<LOGN, LOGE, NP, EV>,
+            e = cudaFuncSetAttribute(k_ivp_train<LOGN, LOGE, NP, SM>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_vp_infer<LOGN, LOGE, NP, EV>,
+            e = cudaFuncSetAttribute(k_vp_infer<LOGN, LOGE, NP, SM>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         return e;
     }
@@ -339,8 +341,8 @@ struct ExtVariant {
     // two) at `smem` bytes of dynamic shared memory per block
     static int occupancy(size_t smem) {
         int a = 0, b = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_ivp_train<LOGN, LOGE, NP, EV>, X::T, smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_vp_infer<LOGN, LOGE, NP, EV>, X::T, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_ivp_train<LOGN, LOGE, NP, SM>, X::T, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_vp_infer<LOGN, LOGE, NP, SM>, X::T, smem);
         int o = a < b ? a : b;
         return o < 1 ? 1 : o;
     }
@@ -377,27 +379,27 @@ struct ExtVariant {
             }
         }
     };
-    static constexpr int SCRATCH_RLWE = EV ? 2 : 3;  // per-block RLWE buffers (inference)
+    static constexpr int SCRATCH_RLWE = SM == 1 ? 2 : 3;  // per-block RLWE buffers (inference)
     static cudaError_t ivp(const LaunchInfo& li, const uint64_t* rgsw, int items, uint64_t* out,
                            uint64_t* acc, int grid, cudaStream_t st) {
         // per-block scratch: two accumulators, (their evaluation form,) the tree slots
         Launch L(li, grid, st, acc, (size_t)grid * (SCRATCH_RLWE + li.k1) * li.rlwe_words * sizeof(u64));
-        return cudaLaunchKernelEx(&L.cfg, k_ivp_train<LOGN, LOGE, NP, EV>, li.dctx, (const u64*)rgsw, items,
+        return cudaLaunchKernelEx(&L.cfg, k_ivp_train<LOGN, LOGE, NP, SM>, li.dctx, (const u64*)rgsw, items,
                                   (u64*)out, (u64*)acc);
     }
     static cudaError_t vp(const LaunchInfo& li, const uint64_t* model, const uint64_t* rgsw, int items,
                           uint64_t* resp, uint64_t* acc, int grid, cudaStream_t st) {
         Launch L(li, grid, st, acc, (size_t)grid * SCRATCH_RLWE * li.rlwe_words * sizeof(u64));
-        return cudaLaunchKernelEx(&L.cfg, k_vp_infer<LOGN, LOGE, NP, EV>, li.dctx, (const u64*)model,
+        return cudaLaunchKernelEx(&L.cfg, k_vp_infer<LOGN, LOGE, NP, SM>, li.dctx, (const u64*)model,
                                   (const u64*)rgsw, items, (u64*)resp, (u64*)acc);
     }
     static ExtOps ops() {
-        return ExtOps{LOGE, NP, EV, SCRATCH_RLWE, X::T, X::XCHG_BYTES, ENC_SMEM, &init, &occupancy,
+        return ExtOps{LOGE, NP, SM, SCRATCH_RLWE, X::T, X::FIXED_BYTES, ENC_SMEM, &init, &occupancy,
                       &encrypt, &ivp, &vp};
     }
 };
 
-#define HW_EXT_VARIANT(L, E, P, V) ExtVariant<L, E, P, V>::ops(),
+#define HW_EXT_VARIANT(L, E, P, M) ExtVariant<L, E, P, M>::ops(),
 // Defines hw_ext_table_<L>: the geometries instantiated for N = 2^L.
 #define HW_EXT_TABLE(L, LIST)                                 \
     const ExtOps* hw_ext_table_##L(int* count) {              \

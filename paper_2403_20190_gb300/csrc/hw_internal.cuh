@@ -135,10 +135,11 @@ __device__ __forceinline__ u64 redc_lazy(u64 hi, u64 lo, u64 q, u64 qneg) {
 // last inverse round writes positions tid + k*T (v[k]); the last forward
 // round leaves, and the first inverse round takes, positions 16*tid + e.
 // ---------------------------------------------------------------------------
-// Default external-product geometry: 2^3 residues per thread and two
-// polynomials per transform below N = 8192, 2^4 and one at N = 8192.  A
-// context may choose another instantiated geometry (hw_create_tuned).
-__host__ __device__ constexpr int default_ext_loge(int log_n) { return log_n >= 13 ? 4 : 3; }
+// Default external-product geometry: 2^3 residues per thread, two
+// polynomials per transform below N = 8192 and one at N = 8192 (1024-thread
+// blocks).  A context may choose another instantiated geometry
+// (hw_create_tuned).
+__host__ __device__ constexpr int default_ext_loge(int) { return 3; }
 __host__ __device__ constexpr int default_ext_np(int log_n) { return log_n >= 13 ? 1 : 2; }
 
 // Evaluation-form arrays (RGSW rows, the key's evaluation form, rotation
@@ -271,6 +272,7 @@ struct Xchg {
     u64* b1;
     int stride;
     int par;
+    u64* accs = nullptr;  // external-product accumulators in shared memory (mode 2), 2*N words
     __device__ __forceinline__ u64* next() {
         u64* p = par ? b1 : b0;
         par ^= 1;
@@ -584,7 +586,29 @@ struct ExtNtt {
 // are skipped when nt.src_ntt is given.  When it is not, a rotation CMUX
 // recovers the evaluation form of its base from the diagonal digit's
 // transform (times (Psi^(+-2^t) - 1)^-1) so that dst_ntt can still be written.
-template <int LOGN, int LOGE, int NP>
+// The external product's two accumulator polynomials at one prime: E words
+// per thread each, in registers, or (AS) in thread-private shared-memory
+// slots (oc*E + e)*T + tid, which frees 2E 64-bit registers.
+template <int E, int T, bool AS>
+struct Acc {
+    u64 r[AS ? 1 : 2][AS ? 1 : E];
+    u64* s;
+    __device__ __forceinline__ explicit Acc(u64* base) : s(AS ? base + threadIdx.x : nullptr) {}
+    __device__ __forceinline__ u64 get(int oc, int e) const {
+        if constexpr (AS) return s[(oc * E + e) * T];
+        else return r[oc][e];
+    }
+    __device__ __forceinline__ void set(int oc, int e, u64 v) {
+        if constexpr (AS) s[(oc * E + e) * T] = v;
+        else r[oc][e] = v;
+    }
+    __device__ __forceinline__ void add(int oc, int e, u64 v) {
+        if constexpr (AS) s[(oc * E + e) * T] += v;
+        else r[oc][e] += v;
+    }
+};
+
+template <int LOGN, int LOGE, int NP, int AS = 0>
 __device__ __noinline__ void ext_product(const DevCtx& C, const u64* __restrict__ rgsw,
                                          const u64* srcA, int eA, const u64* srcB, int eB, int mode,
                                          u64* dst, Xchg& xc, ExtNtt nt) {
@@ -612,9 +636,12 @@ __device__ __noinline__ void ext_product(const DevCtx& C, const u64* __restrict_
         const ulonglong2* rtab =
             cmux_rot ? C.rot_tab + (((size_t)j * 2 + nt.rot_sign) * C.log_n + nt.rot_t) * N + tid
                      : nullptr;
-        u64 acc[2][E];
+        Acc<E, T, AS != 0> acc(xc.accs);
 #pragma unroll
-        for (int e = 0; e < E; e++) acc[0][e] = acc[1][e] = 0;
+        for (int e = 0; e < E; e++) {
+            acc.set(0, e, 0);
+            acc.set(1, e, 0);
+        }
         if (diag_in) {
             // the two diagonal digits, straight from the evaluation form
 #pragma unroll
@@ -631,8 +658,8 @@ __device__ __noinline__ void ext_product(const DevCtx& C, const u64* __restrict_
                         const ulonglong2 t0 = __ldg(rtab + e * T);
                         x = shoup_mul_lazy(x, t0.x, t0.y, qj);
                     }
-                    acc[0][e] += redc_lazy(__umul64hi(x, ra), x * ra, qj, Pj.qneg);
-                    acc[1][e] += redc_lazy(__umul64hi(x, rb), x * rb, qj, Pj.qneg);
+                    acc.add(0, e, redc_lazy(__umul64hi(x, ra), x * ra, qj, Pj.qneg));
+                    acc.add(1, e, redc_lazy(__umul64hi(x, rb), x * rb, qj, Pj.qneg));
                 }
             }
         }
@@ -676,8 +703,8 @@ __device__ __noinline__ void ext_product(const DevCtx& C, const u64* __restrict_
                 for (int e = 0; e < E; e++) {
                     const u64 ra = ld_rgsw(Ra + e * T, rpol), rb = ld_rgsw(Rb + e * T, rpol);
                     const u64 x = v[pp][e];
-                    acc[0][e] += redc_lazy(__umul64hi(x, ra), x * ra, qj, Pj.qneg);
-                    acc[1][e] += redc_lazy(__umul64hi(x, rb), x * rb, qj, Pj.qneg);
+                    acc.add(0, e, redc_lazy(__umul64hi(x, ra), x * ra, qj, Pj.qneg));
+                    acc.add(1, e, redc_lazy(__umul64hi(x, rb), x * rb, qj, Pj.qneg));
                 }
                 if (derive_base && rho == j) {
                     // the base's evaluation form: D_j / (Psi^(+-2^t) - 1)
@@ -701,7 +728,7 @@ __device__ __noinline__ void ext_product(const DevCtx& C, const u64* __restrict_
                                 : (base_given ? nt.src_ntt + ((size_t)oc * r + j) * N + tid : nullptr);
 #pragma unroll
                 for (int e = 0; e < E; e++) {
-                    u64 val = acc[oc][e] + (bn ? bn[e * T] : 0);
+                    u64 val = acc.get(oc, e) + (bn ? bn[e * T] : 0);
                     dn[e * T] = reduce64(val, Pj);
                 }
             }
@@ -713,7 +740,7 @@ __device__ __noinline__ void ext_product(const DevCtx& C, const u64* __restrict_
 #pragma unroll
             for (int pp = 0; pp < NPI; pp++)
 #pragma unroll
-                for (int e = 0; e < E; e++) v[pp][e] = shoup_mul_lazy(acc[oc0 + pp][e], ninv, ninv_s, qj);
+                for (int e = 0; e < E; e++) v[pp][e] = shoup_mul_lazy(acc.get(oc0 + pp, e), ninv, ninv_s, qj);
             ntt_inv<LOGN, LOGE, NPI>(v, xc, C, j);
 #pragma unroll
             for (int pp = 0; pp < NPI; pp++) {
@@ -754,20 +781,23 @@ __device__ __noinline__ void ext_product(const DevCtx& C, const u64* __restrict_
 
 // Launch geometry of the external-product kernels: 2^LOGE residues per
 // thread, NP polynomials transformed together, T = N / 2^LOGE threads.
-template <int LOGN, int LOGE, int NP_, int EV = 0>
+template <int LOGN, int LOGE, int NP_, int SM = 0>
 struct ExtCfg {
     static constexpr int LOGE_ = LOGE;
     static constexpr int NP = NP_;
     static constexpr int T = Ring<LOGN, LOGE>::T;
     static constexpr int PADDED = Ring<LOGN, LOGE>::PADDED;
-    // EV = 1: one exchange set, the rest of shared memory holds the
-    // accumulator's evaluation form (its size depends on r: added at launch)
-    static constexpr size_t XCHG_BYTES = (EV ? 1 : 2) * (size_t)NP * PADDED * sizeof(u64);
+    // shared-memory mode SM: 0 = two exchange sets; 1 = one set, the rest
+    // holds the accumulator's evaluation form (2*r*N words, added at launch);
+    // 2 = one set plus the two accumulator polynomials of one prime (2*N words)
+    static constexpr size_t XCHG_BYTES = (SM ? 1 : 2) * (size_t)NP * PADDED * sizeof(u64);
+    static constexpr size_t ACC_BYTES = SM == 2 ? 2 * (size_t)Ring<LOGN>::N * sizeof(u64) : 0;
+    static constexpr size_t FIXED_BYTES = XCHG_BYTES + ACC_BYTES;
     // blocks that can be resident per SM by shared memory (227 KiB, 1 KiB
     // reserved per block) and by a 512-thread target; the register cap the
     // compiler gets follows from the smaller, so a block that only fits once
     // per SM is not squeezed into registers it cannot use
-    static constexpr int SMEM_BLOCKS = EV ? 1 : (int)((227 * 1024) / (XCHG_BYTES + 1024));
+    static constexpr int SMEM_BLOCKS = SM == 1 ? 1 : (int)((227 * 1024) / (FIXED_BYTES + 1024));
     static constexpr int THR_BLOCKS = (512 / T) < 1 ? 1 : (512 / T);
     static constexpr int MINB0 = SMEM_BLOCKS < THR_BLOCKS ? SMEM_BLOCKS : THR_BLOCKS;
     static constexpr int MINB = MINB0 < 1 ? 1 : (MINB0 > 16 ? 16 : MINB0);

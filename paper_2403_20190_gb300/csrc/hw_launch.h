@@ -12,10 +12,11 @@ struct LaunchInfo;
 // per thread, np polynomials per transform, `threads` threads per block.
 struct ExtOps {
     int loge, np;
-    int ev;            // 1: the accumulator's evaluation form lives in shared memory
+    int sm;            // shared-memory mode: 0 none, 1 the accumulator's evaluation form,
+                       // 2 the accumulator polynomials of one prime
     int scratch_rlwe;  // per-block RLWE buffers of inference (training adds k1)
     int threads;
-    size_t smem, encrypt_smem;  // smem: exchange buffers (+ r-dependent evaluation form with ev)
+    size_t smem, encrypt_smem;  // smem: fixed part (+ r-dependent evaluation form in mode 1)
     cudaError_t (*init)();      // shared-memory attributes of its kernels
     int (*occupancy)(size_t smem);  // resident blocks per SM of the IVP / VP kernels
     cudaError_t (*encrypt)(const LaunchInfo&, const uint64_t* key, const uint8_t* bits,
@@ -49,7 +50,7 @@ HW_EXT_TABLE_DECL(6) HW_EXT_TABLE_DECL(7) HW_EXT_TABLE_DECL(8) HW_EXT_TABLE_DECL
 HW_EXT_TABLE_DECL(10) HW_EXT_TABLE_DECL(11) HW_EXT_TABLE_DECL(12) HW_EXT_TABLE_DECL(13)
 #undef HW_EXT_TABLE_DECL
 const ExtOps* hw_ext_table(int log_n, int* count);
-const ExtOps* hw_ext_find(int log_n, int loge, int np, int ev);
+const ExtOps* hw_ext_find(int log_n, int loge, int np, int sm);
 
 cudaError_t launch_keygen(const LaunchInfo& li, uint64_t seed, uint64_t* key, cudaStream_t st);
 cudaError_t launch_encode(const LaunchInfo& li, const uint8_t* values, size_t n, uint8_t* bits,

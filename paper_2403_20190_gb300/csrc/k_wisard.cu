@@ -53,11 +53,11 @@ const ExtOps* hw_ext_table(int log_n, int* count) {
     return nullptr;
 }
 
-const ExtOps* hw_ext_find(int log_n, int loge, int np, int ev) {
+const ExtOps* hw_ext_find(int log_n, int loge, int np, int sm) {
     int count = 0;
     const ExtOps* t = hw_ext_table(log_n, &count);
     for (int k = 0; k < count; k++)
-        if (t[k].loge == loge && t[k].np == np && t[k].ev == ev) return &t[k];
+        if (t[k].loge == loge && t[k].np == np && t[k].sm == sm) return &t[k];
     return nullptr;
 }
 

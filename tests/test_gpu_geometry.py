@@ -21,10 +21,10 @@ def geometries(cfg):
 
 
 @pytest.mark.parametrize("name", list(TINY))
-@pytest.mark.parametrize("k", range(6))
+@pytest.mark.parametrize("k", range(10))
 def test_tiny_rings_every_geometry(name, k):
     geos = geometries(tiny_cfg(name))
-    assert len(geos) == 6
+    assert len(geos) == 10
     tiny_full_parity(name, geos[k])
 
 
@@ -56,15 +56,15 @@ def test_autotune_picks_a_built_geometry_and_keeps_parity():
     from paper_2403_20190_gb300 import binding
     cfg = tiny_cfg("zltL_h3")
     best, entries = binding.hw_autotune(cfg, 0, n_probe=2, reps=1)
-    built = {(g["ext_loge"], g["ext_np"], g["ext_eval_smem"]) for g in geometries(cfg)}
-    assert (best["ext_loge"], best["ext_np"], best["ext_eval_smem"]) in built
+    built = {(g["ext_loge"], g["ext_np"], g["ext_smem"]) for g in geometries(cfg)}
+    assert (best["ext_loge"], best["ext_np"], best["ext_smem"]) in built
     step = [e for e in entries if e["ms_train"] >= 0]
     ntt = [e for e in entries if e["ms_ntt"] >= 0]
     assert len(step) >= len(built) and all(e["status"] == 0 for e in entries)
-    assert any(e["geometry"]["ext_eval_smem"] == 1 for e in step)
+    assert any(e["geometry"]["ext_smem"] == 1 for e in step)
     # 55-bit primes: radix 8 and 16, 64-bit words only
     assert sorted((e["geometry"]["ntt_loge"], e["geometry"]["ntt_limbs"]) for e in ntt) == [(3, 2), (4, 2)]
     fastest = min(step, key=lambda e: e["ms_encrypt"] + e["ms_train"] + e["ms_infer"])
-    keys = ("ext_loge", "ext_np", "ext_blocks_per_sm", "ext_eval_smem", "l2_persist")
+    keys = ("ext_loge", "ext_np", "ext_blocks_per_sm", "ext_smem", "l2_persist")
     assert tuple(best[k] for k in keys) == tuple(fastest["geometry"][k] for k in keys)
     tiny_full_parity("zltL_h3", best)
