@@ -58,10 +58,10 @@ def parse():
 # in profiles/k_vp_infer_cfg2.md (2 test samples, scaled by samples: the
 # traffic is per item); valid only for the kernel sources it was taken on.
 PROFILED_VP_TRAFFIC = {
-    "config": "cfg2", "ext_loge": 3, "ext_np": 2, "bytes_per_test_sample": 8.173e9,
+    "config": "cfg2", "ext_loge": 3, "ext_np": 2, "ext_smem": 1, "bytes_per_test_sample": 2.1465e9,
     "sources": ("paper_2403_20190_gb300/csrc/hw_ext.cuh", "paper_2403_20190_gb300/csrc/hw_internal.cuh",
                 "paper_2403_20190_gb300/csrc/modarith.cuh"),
-    "sha256": "58237154f6d70f4bb379554f5f879546aa96388fdeb236da2c4406aee3bc093a",
+    "sha256": "35031caf9835481718cf615fbb75c3adf6fc38fd79943a67254eaeda733effe8",
 }
 # Register-only 64-bit lazy Cooley-Tukey butterflies per second on one GB300
 # at 2070 MHz (profiles/butterfly_ceiling.md): what the integer pipes issue
@@ -73,7 +73,7 @@ BUTTERFLY_CEILING = {"ct64_t_per_s": 0.8414, "gs64_t_per_s": 0.8755,
 def profiled_traffic(config, geometry, n_test):
     import hashlib
     t = PROFILED_VP_TRAFFIC
-    if config != t["config"] or geometry.get("ext_loge") != t["ext_loge"] or geometry.get("ext_np") != t["ext_np"]:
+    if config != t["config"] or any(geometry.get(k) != t[k] for k in ("ext_loge", "ext_np", "ext_smem")):
         return None
     h = hashlib.sha256()
     for f in t["sources"]:
@@ -561,7 +561,8 @@ def serve_leg(args, local):
     from paper_2403_20190_gb300.serve import ResidentModel, Server, latency_stats, poisson_stream
     from synthdata import get_config
     cfgs = {nm: get_config(nm) for nm in ("cfg1", "cfg2", "cfg3", "cfg4")}
-    models = {nm: ResidentModel(c, local, key_seed=c.key_seed) for nm, c in cfgs.items()}
+    geo = "auto" if args.geometry == "auto" else None
+    models = {nm: ResidentModel(c, local, key_seed=c.key_seed, geometry=geo) for nm, c in cfgs.items()}
     reqs = poisson_stream(cfgs, n_requests=args.serve_requests, rate=200.0, seed=2024,
                           max_samples=SERVE_MAX)
     from paper_2403_20190_gb300.arena import DeviceArena

@@ -65,9 +65,10 @@ class Request:
 
 
 class ResidentModel:
-    def __init__(self, cfg, device, key_seed):
+    def __init__(self, cfg, device, key_seed, geometry=None):
+        """geometry: as for Session (None, "auto" or a dict)."""
         self.cfg = cfg
-        self.sess = Session(cfg, device)
+        self.sess = Session(cfg, device, geometry=geometry)
         self.key = self.sess.keygen(key_seed)
         self.model = self.sess.new_model()   # frozen during a window
         self.delta = self.sess.new_model()   # this window's training
