@@ -334,6 +334,9 @@ extern "C" int hw_create_tuned(const hw_params* p, const hw_geometry* g, int cud
         H.yM[i] = (u64)(((u128)y << 64) % q[i]);
         H.n_inv[i] = hinv((u64)n % q[i], q[i]);
         H.n_inv_s[i] = shoup(H.n_inv[i], q[i]);
+        H.mr[i] = t;
+        H.mr_s[i] = shoup(t, q[i]);
+        H.mr2_s[i] = shoup(P.r2, q[i]);
         S.q[i] = q[i];
     }
     for (int rho = 0; rho < dnum; rho++) {

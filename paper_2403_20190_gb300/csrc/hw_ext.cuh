@@ -71,10 +71,15 @@ __global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP>::T, ExtCfg<LOGN, LOGE, 
         const PrimeConst P = C.P[j];
         const u64 q = P.q;
         __syncthreads();  // A is free; ebuf is complete
+        // the whole row is computed in Montgomery form (x R mod q, the form
+        // it is stored in): a uniform draw hi*2^64 + lo gives
+        // a R = hi (R^2 mod q) + lo (R mod q), two products by constants; the
+        // transform is linear, so it keeps the form
+        const u64 mr = C.mr[j], mr_s = C.mr_s[j], mr2_s = C.mr2_s[j];
         for (int c0 = tid; c0 < N / 2; c0 += T) {
             Philox4 w = hw_draw(seed, HW_TAG_RGSW_A, (u64)c0, (u64)(row * r + j), stream);
-            A[2 * c0] = reduce128(w.v[0], w.v[1], P);
-            A[2 * c0 + 1] = reduce128(w.v[2], w.v[3], P);
+            A[2 * c0] = add_mod(shoup_mul(w.v[0], P.r2, mr2_s, q), shoup_mul(w.v[1], mr, mr_s, q), q);
+            A[2 * c0 + 1] = add_mod(shoup_mul(w.v[2], P.r2, mr2_s, q), shoup_mul(w.v[3], mr, mr_s, q), q);
         }
         __syncthreads();
         // a and e transformed together (NP == 2) or one after the other
@@ -83,7 +88,7 @@ __global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP>::T, ExtCfg<LOGN, LOGE, 
         for (int kk = 0; kk < E; kk++) {
             const int x = tid + kk * T;
             v[0][kk] = A[x];
-            v[1][kk] = from_signed((int64_t)ebuf[x], q);
+            v[1][kk] = shoup_mul(from_signed((int64_t)ebuf[x], q), mr, mr_s, q);  // e R
         }
         if constexpr (NP == 2) {
             ntt_fwd<LOGN, LOGE, 2>(v, xc, C, j);
@@ -91,22 +96,23 @@ __global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP>::T, ExtCfg<LOGN, LOGE, 
             ntt_fwd<LOGN, LOGE, 1>(reinterpret_cast<u64(&)[1][E]>(v[0]), xc, C, j);
             ntt_fwd<LOGN, LOGE, 1>(reinterpret_cast<u64(&)[1][E]>(v[1]), xc, C, j);
         }
-        const u64 g = (bit && j == gi) ? C.gconst[rho] : 0;
+        const u64 gM = (bit && j == gi) ? to_mont(C.gconst[rho], P) : 0;
         const u64* sM = key + (size_t)(r + j) * N;
         u64* da = dst_row + (size_t)(0 * r + j) * N;
         u64* db = dst_row + (size_t)(1 * r + j) * N;
 #pragma unroll
         for (int e = 0; e < E; e++) {
             const int pos = e * T + tid;  // evaluation position E*tid + e, thread-major
-            u64 a = reduce_full(v[0][e], P);
-            u64 b = add_mod(mont_mul(a, sM[pos], P), reduce_full(v[1][e], P), q);
+            u64 aM = reduce_full(v[0][e], P);
+            // REDC(aR * sR) = a s R
+            u64 bM = add_mod(mont_mul(aM, sM[pos], P), reduce_full(v[1][e], P), q);
             // the evaluation form of the constant polynomial g is g everywhere
             if (row < C.dnum)
-                b = add_mod(b, g, q);
+                bM = add_mod(bM, gM, q);
             else
-                a = add_mod(a, g, q);
-            da[pos] = to_mont(a, P);
-            db[pos] = to_mont(b, P);
+                aM = add_mod(aM, gM, q);
+            da[pos] = aM;
+            db[pos] = bM;
         }
     }
 }
