@@ -245,6 +245,16 @@ int hw_infer_static_scratch(hw_ctx* ctx, const uint64_t* model_dev, const uint64
 int hw_export_rgsw(hw_ctx* ctx, const uint64_t* rgsw_dev, size_t count, uint64_t* out_dev,
                    void* stream);
 
+/* The inverse of hw_export_rgsw: count RGSW ciphertexts in canonical
+ * coefficient form ([row 0..2*dnum-1][RLWE], words reduced mod q_i on
+ * entry) into this context's internal evaluation form, as hw_train_accumulate
+ * and hw_infer read it.  No counterpart in the paper: it lets ciphertexts
+ * made elsewhere (another implementation, or a context of another geometry,
+ * via hw_export_rgsw) be used here.  canonical_dev and rgsw_dev may be the
+ * same buffer. */
+int hw_import_rgsw(hw_ctx* ctx, const uint64_t* canonical_dev, size_t count, uint64_t* rgsw_dev,
+                   void* stream);
+
 /* Batched forward / inverse negacyclic transform of count polynomials in
  * place, polynomial t using prime (t mod r).  The forward output is in the
  * library's evaluation order; inverse(forward(x)) = x. */

@@ -78,6 +78,7 @@ _SIGS = {
     "hw_decrypt": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, _SZ, _VP, _VP]),
     "hw_pdact": (ctypes.c_int, [_VP, _VP, _SZ, _VP, _VP, _VP]),
     "hw_export_rgsw": (ctypes.c_int, [_VP, _VP, _SZ, _VP, _VP]),
+    "hw_import_rgsw": (ctypes.c_int, [_VP, _VP, _SZ, _VP, _VP]),
     "hw_ntt_forward": (ctypes.c_int, [_VP, _VP, _SZ, _VP]),
     "hw_ntt_inverse": (ctypes.c_int, [_VP, _VP, _SZ, _VP]),
     "hw_launch_count": (_U64, [_VP]),
@@ -286,6 +287,11 @@ def hw_pdact(ctx, counts, n, scores, labels, stream=None):
 def hw_export_rgsw(ctx, rgsw, count, out, stream=None):
     _check(load().hw_export_rgsw(ctx.handle, _ptr(rgsw), count, _ptr(out), _stream(stream)),
            "hw_export_rgsw")
+
+
+def hw_import_rgsw(ctx, canonical, count, rgsw, stream=None):
+    _check(load().hw_import_rgsw(ctx.handle, _ptr(canonical), count, _ptr(rgsw), _stream(stream)),
+           "hw_import_rgsw")
 
 
 def hw_ntt_forward(ctx, poly, count, stream=None):

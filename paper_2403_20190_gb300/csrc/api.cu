@@ -759,6 +759,14 @@ extern "C" int hw_export_rgsw(hw_ctx* c, const uint64_t* rgsw, size_t count, uin
     return HW_OK;
 }
 
+extern "C" int hw_import_rgsw(hw_ctx* c, const uint64_t* canonical, size_t count, uint64_t* rgsw,
+                              void* stream) {
+    CHECK_CTX(c);
+    if (count && (!canonical || !rgsw)) return fail(HW_EINVAL, "hw_import_rgsw: null buffer");
+    CUDA_TRY(launch_import_rgsw(c->li, canonical, count, rgsw, (cudaStream_t)stream));
+    return HW_OK;
+}
+
 extern "C" int hw_ntt_forward(hw_ctx* c, uint64_t* poly, size_t count, void* stream) {
     CHECK_CTX(c);
     if (count && !poly) return fail(HW_EINVAL, "hw_ntt_forward: null buffer");

@@ -75,6 +75,8 @@ cudaError_t launch_pdact(const LaunchInfo& li, const int64_t* counts, size_t n, 
                          int32_t* labels, cudaStream_t st);
 cudaError_t launch_export_rgsw(const LaunchInfo& li, const uint64_t* rgsw, size_t count,
                                uint64_t* out, cudaStream_t st);
+cudaError_t launch_import_rgsw(const LaunchInfo& li, const uint64_t* in, size_t count, uint64_t* rgsw,
+                               cudaStream_t st);
 cudaError_t launch_ntt_batch(const LaunchInfo& li, uint64_t* poly, size_t count, int inverse,
                              cudaStream_t st);
 // Shared-memory attributes of the context's kernels (its ring size, its

@@ -297,6 +297,30 @@ __global__ void __launch_bounds__(Geo<LOGN>::T)
     for (int kk = 0; kk < 16; kk++) out[poly * N + tid + kk * T] = v[kk] >= P.q ? v[kk] - P.q : v[kk];
 }
 
+// The inverse of k_export_rgsw: canonical coefficient words (any 64-bit
+// values, reduced mod q_i first) -> evaluation form, Montgomery
+// representation, the context's thread-major layout.  Every read precedes
+// the first barrier and every write follows the last, so it runs in place.
+template <int LOGN>
+__global__ void __launch_bounds__(Geo<LOGN>::T)
+    k_import_rgsw(const DevCtx* __restrict__ Cp, const u64* in, u64* out) {
+    extern __shared__ u64 smem[];
+    constexpr int N = Ring<LOGN>::N, T = Ring<LOGN>::T;
+    Xchg xc{smem, smem + Ring<LOGN>::PADDED, Ring<LOGN>::PADDED, 0};
+    const DevCtx& C = *Cp;
+    const int tid = threadIdx.x;
+    const size_t poly = blockIdx.x;  // [rgsw][row][comp][prime]
+    const int j = (int)(poly % C.r);
+    const PrimeConst P = C.P[j];
+    u64 v[16];
+#pragma unroll
+    for (int kk = 0; kk < 16; kk++) v[kk] = reduce_full(in[poly * N + tid + kk * T], P);
+    ntt_fwd1<LOGN>(v, xc, C, j);
+#pragma unroll
+    for (int e = 0; e < 16; e++)
+        out[poly * N + eval_addr(16 * tid + e, LOGN, C.ext_loge)] = to_mont(reduce_full(v[e], P), P);
+}
+
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
@@ -397,6 +421,19 @@ cudaError_t launch_export_rgsw(const LaunchInfo& li, const uint64_t* rgsw, size_
     return HW_LAUNCHED();
 }
 
+cudaError_t launch_import_rgsw(const LaunchInfo& li, const uint64_t* in, size_t count, uint64_t* rgsw,
+                               cudaStream_t st) {
+    if (count == 0) return cudaSuccess;
+    size_t polys = count * 2 * li.dnum * 2 * li.r;
+#define B(L)                                                                                      \
+    case L:                                                                                       \
+        k_import_rgsw<L><<<(unsigned)polys, Geo<L>::T, Geo<L>::XCHG_BYTES, st>>>(li.dctx, in, rgsw); \
+        break;
+    HW_DISPATCH(li.log_n, B)
+#undef B
+    return HW_LAUNCHED();
+}
+
 extern cudaError_t hw_ntt_kernels_init(const LaunchInfo& li);
 
 cudaError_t hw_kernels_init(const LaunchInfo& li) {
@@ -408,6 +445,7 @@ cudaError_t hw_kernels_init(const LaunchInfo& li) {
         A(k_keygen, L, Geo<L>::XCHG_BYTES)     \
         A(k_rlwe_phase, L, Geo<L>::XCHG_BYTES) \
         A(k_export_rgsw, L, Geo<L>::XCHG_BYTES) \
+        A(k_import_rgsw, L, Geo<L>::XCHG_BYTES) \
         break;
     switch (li.log_n) {
         HW_FOR_EACH_LOGN(X)

@@ -119,6 +119,11 @@ class Session:
         B.hw_export_rgsw(self.ctx, rgsw, count, out, stream)
         return out
 
+    def import_rgsw(self, canonical, count, stream=None):
+        out = self.words(int(count) * self.sz["rgsw_words"], zero=False)
+        B.hw_import_rgsw(self.ctx, canonical, count, out, stream)
+        return out
+
 
 class ServerStep:
     """The server side of one step on fixed batch sizes: train on an
