@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-ntt", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-balance", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=40)
     ap.add_argument("--geometry", default="auto", choices=["auto", "default"],
                     help="kernel geometry: autotuned (cached per GPU and parameters) or the library default")
@@ -403,6 +404,30 @@ def gpu_arm(args, ws, rank, local, pg):
     keys = ["encrypt_train", "train", "encrypt_test", "infer", "decrypt_pdact"]
     ph = {kn: evs[a].elapsed_time(evs[b]) for a, b, kn in zip(names[:-1], names[1:], keys)}
 
+    # dataset balancing (Section 3.6.1) on the same step: the label-bit IVP
+    # over the training batch into the class-count ciphertext, its
+    # decryption and the balanced PD-act of the test batch
+    balancing = None
+    if not args.no_balance:
+        bal_counts = sess.new_counts()
+        bal_scr = sess.words(B.hw_count_scratch_words(sess.ctx, bsz), zero=False)
+        for _ in range(2):
+            sess.count_classes(bal_counts, st.rgsw_train, bsz, scratch=bal_scr, stream=stream)
+        torch.cuda.synchronize()
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        sess.count_classes(bal_counts, st.rgsw_train, bsz, scratch=bal_scr, stream=stream)
+        e1.record(stream)
+        cc = sess.class_counts(key, bal_counts, stream=stream)
+        sess.pdact_balanced(st.counts, cc, bsz, stream=stream)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        t_count, t_post = e0.elapsed_time(e1), e1.elapsed_time(e2)
+        balancing = {"count_ms_per_step": t_count, "decrypt_pdact_ms": t_post,
+                     "share_of_step": (t_count + t_post) / (elapsed_ms / args.steps),
+                     "ext_products_per_sample": sz["L"]}
+        del bal_scr
+
     # e2e through the C ABI with pinned host buffers, copies inside the timed region
     e2e = None
     if not args.no_e2e:
@@ -530,6 +555,7 @@ def gpu_arm(args, ws, rank, local, pg):
             "inferences_per_s": bsz / (ph["infer"] / 1000.0),
             "train_modmul_per_s": train_modmul / (ph["train"] / 1000.0),
             "phases_ms": ph,
+            "balancing": balancing,
             "roofline": roofline,
             "ntt": ntt,
             "geometry": sess.geometry,

@@ -241,6 +241,27 @@ int hw_pdact(hw_ctx* ctx, const int64_t* counts_dev, size_t n, int64_t* scores_d
 int hw_infer_static_scratch(hw_ctx* ctx, const uint64_t* model_dev, const uint64_t* rgsw_dev,
                             size_t n, uint64_t* resp_dev, uint64_t* sums_dev, void* stream);
 
+/* Dataset balancing (Section 3.6.1): for each of n encrypted training
+ * samples (the same rgsw_dev as hw_train_accumulate), a small IVP over its
+ * label bits -- BlindRotate from (0, Delta) with weights X^(+2^t) over the
+ * L label slots -- gives an RLWE with Delta at coefficient = label; the
+ * batch is added (mod q_i) into counts_dev (rlwe_words, caller-zeroed
+ * before the first batch), whose coefficient c then decrypts
+ * (hw_decrypt, HW_DEC_RLWE) to the number of class-c samples.
+ * scratch_dev: hw_count_scratch_words(ctx, n) device words. */
+size_t hw_count_scratch_words(const hw_ctx* ctx, size_t n);
+int hw_count_classes(hw_ctx* ctx, uint64_t* counts_dev, const uint64_t* rgsw_dev, size_t n,
+                     uint64_t* scratch_dev, size_t scratch_words, void* stream);
+
+/* PD-act with the balancing rescale (Section 3.6.1 leaves the rule open;
+ * this library's reading): class_counts_dev [l] (the decrypted counts),
+ * counters of class c scaled by n_ref / n_c with floor division before the
+ * activation (n_ref = the largest count; classes with n_c = 0 unchanged) --
+ * the same as training on a set where every class is repeated up to n_ref
+ * samples.  Layouts as hw_pdact. */
+int hw_pdact_balanced(hw_ctx* ctx, const int64_t* counts_dev, const int64_t* class_counts_dev, size_t n,
+                      int64_t* scores_dev, int32_t* labels_dev, void* stream);
+
 /* Canonical coefficient form of count RGSW ciphertexts (for checks). */
 int hw_export_rgsw(hw_ctx* ctx, const uint64_t* rgsw_dev, size_t count, uint64_t* out_dev,
                    void* stream);

@@ -134,6 +134,30 @@ class Oracle:
                     lib().or_rlwe_add(self.ctx, _p64(H[j, P.slot[v]]), _p64(np.ascontiguousarray(L[v])))
         return H
 
+    # ---------------------------------------------- dataset balancing (3.6.1)
+    def count_item(self, rgsw_by_slot) -> np.ndarray:
+        """Section 3.6.1: a small IVP over the label bits of one sample --
+        BlindRotate from the trivial (0, Delta) with weights -2^t (X^{+2^t})
+        over the L label slots -- leaves Delta at coefficient = label."""
+        P = self.P
+        acc = self.trivial_one()
+        ptrs = (u64p * P.L)()
+        clear = (ctypes.c_int * P.L)()
+        for t in range(P.L):
+            ptrs[t] = _p64(rgsw_by_slot[t])
+        lib().or_blind_rotate(self.ctx, _p64(acc), ptrs, clear, P.L, -1)
+        return acc
+
+    def count_classes(self, counts, s, seed, labels, sample_offset=0):
+        """Adds every sample's class-count RLWE into `counts` (rlwe_words),
+        from the same encrypted label bits training uses; coefficient c of the
+        sum decrypts to the number of samples of class c."""
+        P = self.P
+        for i, lab in enumerate(labels):
+            rg = self.encrypt_slots(s, seed, sample_offset + i, None, lab, range(P.L))
+            lib().or_rlwe_add(self.ctx, _p64(counts), _p64(self.count_item(rg)))
+        return counts
+
     # ----------------------------------------------------------- inference
     def vp_item(self, H, rgsw_by_slot, j, c) -> np.ndarray:
         """VP(b, H[j]) with clear label bits of class c (Algorithm 7)."""

@@ -180,6 +180,24 @@ def pdact(cfg, u):
     return scores, labels
 
 
+def balanced_pdact(cfg, u, class_counts):
+    """PD-act with the dataset-balancing rescale of Section 3.6.1.  The
+    paper leaves the rule open; reading: a per-class learning rate
+    n_ref / n_c (n_ref = the largest class count), applied to the decrypted
+    counters before the activation with floor division,
+    u'[i][c][j] = floor(u[i][c][j] * n_ref / n_c) (u' = u where n_c = 0,
+    whose counters are all 0).  It equals training on a set where every
+    class is repeated up to n_ref samples."""
+    u = np.asarray(u, dtype=np.int64)
+    n = np.asarray(class_counts, dtype=np.int64)
+    n_ref = int(n.max()) if n.size else 0
+    scaled = u.copy()
+    for c in range(u.shape[1]):
+        if n[c] > 0:
+            scaled[:, c, :] = (u[:, c, :] * n_ref) // n[c]
+    return pdact(cfg, scaled)
+
+
 def evaluate(P, W, data_bits):
     """Algorithm 2 with the activation applied to the looked-up counters."""
     return pdact(P.cfg, lookups(P, W, data_bits))

@@ -79,6 +79,9 @@ _SIGS = {
     "hw_pdact": (ctypes.c_int, [_VP, _VP, _SZ, _VP, _VP, _VP]),
     "hw_export_rgsw": (ctypes.c_int, [_VP, _VP, _SZ, _VP, _VP]),
     "hw_import_rgsw": (ctypes.c_int, [_VP, _VP, _SZ, _VP, _VP]),
+    "hw_count_scratch_words": (_SZ, [_VP, _SZ]),
+    "hw_count_classes": (ctypes.c_int, [_VP, _VP, _VP, _SZ, _VP, _SZ, _VP]),
+    "hw_pdact_balanced": (ctypes.c_int, [_VP, _VP, _VP, _SZ, _VP, _VP, _VP]),
     "hw_ntt_forward": (ctypes.c_int, [_VP, _VP, _SZ, _VP]),
     "hw_ntt_inverse": (ctypes.c_int, [_VP, _VP, _SZ, _VP]),
     "hw_launch_count": (_U64, [_VP]),
@@ -292,6 +295,20 @@ def hw_export_rgsw(ctx, rgsw, count, out, stream=None):
 def hw_import_rgsw(ctx, canonical, count, rgsw, stream=None):
     _check(load().hw_import_rgsw(ctx.handle, _ptr(canonical), count, _ptr(rgsw), _stream(stream)),
            "hw_import_rgsw")
+
+
+def hw_count_scratch_words(ctx, n) -> int:
+    return int(load().hw_count_scratch_words(ctx.handle, n))
+
+
+def hw_count_classes(ctx, counts, rgsw, n, scratch, stream=None):
+    _check(load().hw_count_classes(ctx.handle, _ptr(counts), _ptr(rgsw), n, _ptr(scratch), scratch.numel(),
+                                   _stream(stream)), "hw_count_classes")
+
+
+def hw_pdact_balanced(ctx, counts, class_counts, n, scores, labels, stream=None):
+    _check(load().hw_pdact_balanced(ctx.handle, _ptr(counts), _ptr(class_counts), n, _ptr(scores), _ptr(labels),
+                                    _stream(stream)), "hw_pdact_balanced")
 
 
 def hw_ntt_forward(ctx, poly, count, stream=None):

@@ -750,6 +750,35 @@ extern "C" int hw_pdact(hw_ctx* c, const int64_t* counts, size_t n, int64_t* sco
     return HW_OK;
 }
 
+extern "C" size_t hw_count_scratch_words(const hw_ctx* c, size_t n) {
+    if (!c) return 0;
+    return n * c->sz.rlwe_words + (size_t)c->li.ext_grid * c->li.ext->scratch_rlwe * c->sz.rlwe_words;
+}
+
+extern "C" int hw_count_classes(hw_ctx* c, uint64_t* counts, const uint64_t* rgsw, size_t n, uint64_t* scratch,
+                                size_t scratch_words, void* stream) {
+    CHECK_CTX(c);
+    if (n == 0) return HW_OK;
+    if (!counts || !rgsw || !scratch) return fail(HW_EINVAL, "hw_count_classes: null buffer");
+    const size_t need = hw_count_scratch_words(c, n);
+    if (scratch_words < need)
+        return fail(HW_ENOMEM, "hw_count_classes: scratch needs %zu words, got %zu", need, scratch_words);
+    if (n > 0x7fffffff) return fail(HW_EINVAL, "hw_count_classes: batch too large");
+    u64* out = scratch;
+    u64* acc = scratch + n * c->sz.rlwe_words;
+    CUDA_TRY(launch_count_classes(c->li, counts, rgsw, n, out, acc, c->li.ext_grid, (cudaStream_t)stream));
+    return HW_OK;
+}
+
+extern "C" int hw_pdact_balanced(hw_ctx* c, const int64_t* counts, const int64_t* class_counts, size_t n,
+                                 int64_t* scores, int32_t* labels, void* stream) {
+    CHECK_CTX(c);
+    if (n && (!counts || !class_counts || !scores || !labels))
+        return fail(HW_EINVAL, "hw_pdact_balanced: null buffer");
+    CUDA_TRY(launch_pdact_balanced(c->li, counts, class_counts, n, scores, labels, (cudaStream_t)stream));
+    return HW_OK;
+}
+
 extern "C" int hw_export_rgsw(hw_ctx* c, const uint64_t* rgsw, size_t count, uint64_t* out,
                               void* stream) {
     CHECK_CTX(c);

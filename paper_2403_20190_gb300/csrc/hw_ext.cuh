@@ -322,6 +322,50 @@ __global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP, SM>::T, ExtCfg<LOGN, LO
 }
 
 // ---------------------------------------------------------------------------
+// Dataset balancing (Section 3.6.1): a small IVP over the label bits of each
+// sample.  One block per sample, persistent: acc = (0, Delta); for each label
+// bit t: acc <- acc + C_t [x] (acc X^(2^t) - acc) (IVP direction); the result,
+// Delta at coefficient = label, goes to out[sample] and a reduction adds the
+// batch into the class-count ciphertext.  Per-block scratch as for VP.
+// ---------------------------------------------------------------------------
+template <int LOGN, int LOGE, int NP, int SM>
+__global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP, SM>::T, ExtCfg<LOGN, LOGE, NP, SM>::MINB)
+    k_count_classes(const DevCtx* __restrict__ Cp, const u64* __restrict__ rgsw, int n_items,
+                    u64* __restrict__ out, u64* __restrict__ scratch) {
+    using X = ExtCfg<LOGN, LOGE, NP, SM>;
+    extern __shared__ u64 smem[];
+    Xchg xc{smem, SM ? smem : smem + NP * X::PADDED, X::PADDED, 0};
+    if (SM == 2) xc.accs = smem + NP * X::PADDED;
+    const DevCtx& C = *Cp;
+    const int tid = threadIdx.x, T = blockDim.x;
+    const size_t rl = C.rlwe_words;
+    u64* blk = scratch + (size_t)blockIdx.x * (SM == 1 ? 2 : 3) * rl;
+    u64* acc[2] = {blk, blk + rl};
+    u64* accn = SM == 1 ? smem + NP * X::PADDED : blk + 2 * rl;
+    for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+        const u64* sample = rgsw + (size_t)item * C.sample_words;
+        u64* res = out + (size_t)item * rl;
+        for (size_t w = tid; w < rl; w += T) {
+            const size_t comp = w / ((size_t)C.r * C.n), rem = w % ((size_t)C.r * C.n);
+            const int p = (int)(rem / C.n), x = (int)(rem % C.n);
+            acc[0][w] = (comp == 1 && x == 0) ? C.delta[p] : 0;
+            accn[w] = comp == 1 ? C.delta[p] : 0;
+        }
+        __syncthreads();
+        int cur = 0;
+        for (int t = 0; t < C.L; t++) {
+            const bool last = t == C.L - 1;
+            ext_product<LOGN, LOGE, NP, SM == 2>(
+                C, sample + (size_t)t * C.rgsw_words, acc[cur], 1 << t, acc[cur], 0, EXT_ADD,
+                last ? res : acc[cur ^ 1], xc,
+                ExtNtt{accn, last ? nullptr : accn, t, 0,
+                       last ? nullptr : sample + (size_t)(t + 1) * C.rgsw_words, 1});
+            cur ^= 1;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Launch table of one geometry
 // ---------------------------------------------------------------------------
 template <int LOGN, int LOGE, int NP, int SM>
@@ -340,6 +384,9 @@ struct ExtVariant {
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k_vp_infer<LOGN, LOGE, NP, SM>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_count_classes<LOGN, LOGE, NP, SM>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         return e;
     }
@@ -399,9 +446,15 @@ struct ExtVariant {
         return cudaLaunchKernelEx(&L.cfg, k_vp_infer<LOGN, LOGE, NP, SM>, li.dctx, (const u64*)model,
                                   (const u64*)rgsw, items, (u64*)resp, (u64*)acc);
     }
+    static cudaError_t count(const LaunchInfo& li, const uint64_t* rgsw, int items, uint64_t* out,
+                             uint64_t* acc, int grid, cudaStream_t st) {
+        Launch L(li, grid, st, acc, 0);
+        return cudaLaunchKernelEx(&L.cfg, k_count_classes<LOGN, LOGE, NP, SM>, li.dctx, (const u64*)rgsw,
+                                  items, (u64*)out, (u64*)acc);
+    }
     static ExtOps ops() {
         return ExtOps{LOGE, NP, SM, SCRATCH_RLWE, X::T, X::FIXED_BYTES, ENC_SMEM, &init, &occupancy,
-                      &encrypt, &ivp, &vp};
+                      &encrypt, &ivp, &vp, &count};
     }
 };
 

@@ -26,6 +26,8 @@ struct ExtOps {
                        uint64_t* acc, int grid, cudaStream_t);
     cudaError_t (*vp)(const LaunchInfo&, const uint64_t* model, const uint64_t* rgsw, int items,
                       uint64_t* resp, uint64_t* acc, int grid, cudaStream_t);
+    cudaError_t (*count)(const LaunchInfo&, const uint64_t* rgsw, int items, uint64_t* out,
+                         uint64_t* acc, int grid, cudaStream_t);
 };
 
 struct LaunchInfo {
@@ -64,6 +66,10 @@ cudaError_t launch_accumulate(const LaunchInfo& li, uint64_t* model, const uint6
                               cudaStream_t st);
 cudaError_t launch_vp_infer(const LaunchInfo& li, const uint64_t* model, const uint64_t* rgsw,
                             size_t n, uint64_t* resp, uint64_t* acc, int grid, cudaStream_t st);
+cudaError_t launch_count_classes(const LaunchInfo& li, uint64_t* counts, const uint64_t* rgsw, size_t n,
+                                 uint64_t* out, uint64_t* acc, int grid, cudaStream_t st);
+cudaError_t launch_pdact_balanced(const LaunchInfo& li, const int64_t* counts, const int64_t* class_counts,
+                                  size_t n, int64_t* scores, int32_t* labels, cudaStream_t st);
 cudaError_t launch_class_sums(const LaunchInfo& li, const uint64_t* resp, size_t n, uint64_t* sums,
                               cudaStream_t st);
 cudaError_t launch_decrypt_rlwe(const LaunchInfo& li, const uint64_t* key, const uint64_t* ct,

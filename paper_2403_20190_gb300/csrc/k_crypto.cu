@@ -273,6 +273,35 @@ __global__ void k_pdact(const DevCtx* __restrict__ Cp, const int64_t* __restrict
     labels[i] = best;
 }
 
+// PD-act with the balancing rescale (Section 3.6.1; the rule is a reading):
+// every counter of class c is scaled by n_ref / n_c with floor division
+// before the activation, n_ref = the largest class count; classes with
+// n_c = 0 are left as they are (their counters are 0).
+__global__ void k_pdact_balanced(const DevCtx* __restrict__ Cp, const int64_t* __restrict__ counts,
+                                 const int64_t* __restrict__ class_counts, int n,
+                                 int64_t* __restrict__ scores, int32_t* __restrict__ labels) {
+    const DevCtx& C = *Cp;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int l = C.n_classes;
+    int64_t n_ref = 0;
+    for (int c = 0; c < l; c++) n_ref = class_counts[c] > n_ref ? class_counts[c] : n_ref;
+    int best = 0;
+    int64_t best_s = -1;
+    for (int c = 0; c < l; c++) {
+        const int64_t* u = counts + ((size_t)i * l + c) * C.k0;
+        const int64_t nc = class_counts[c];
+        int64_t s = 0;
+        for (int j = 0; j < C.k0; j++) s += activate(C, nc > 0 ? (u[j] * n_ref) / nc : u[j]);
+        scores[(size_t)i * l + c] = s;
+        if (s > best_s) {
+            best_s = s;
+            best = c;
+        }
+    }
+    labels[i] = best;
+}
+
 // ---------------------------------------------------------------------------
 // Transform utilities.
 // ---------------------------------------------------------------------------
@@ -405,6 +434,14 @@ cudaError_t launch_pdact(const LaunchInfo& li, const int64_t* counts, size_t n, 
                          int32_t* labels, cudaStream_t st) {
     if (n == 0) return cudaSuccess;
     k_pdact<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(li.dctx, counts, (int)n, scores, labels);
+    return HW_LAUNCHED();
+}
+
+cudaError_t launch_pdact_balanced(const LaunchInfo& li, const int64_t* counts, const int64_t* class_counts,
+                                  size_t n, int64_t* scores, int32_t* labels, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    k_pdact_balanced<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(li.dctx, counts, class_counts, (int)n,
+                                                                    scores, labels);
     return HW_LAUNCHED();
 }
 

@@ -20,6 +20,21 @@ __global__ void k_accumulate(const DevCtx* __restrict__ Cp, u64* __restrict__ mo
     }
 }
 
+// counts[w] += sum over the batch of out[i][w] (mod q): the class-count
+// ciphertext of dataset balancing, one word per thread.
+__global__ void k_add_rlwes(const DevCtx* __restrict__ Cp, u64* __restrict__ counts,
+                            const u64* __restrict__ out, int n) {
+    const DevCtx& C = *Cp;
+    const size_t total = C.rlwe_words;
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const u64 q = C.P[(idx / C.n) % C.r].q;
+        u64 s = counts[idx];
+        for (int i = 0; i < n; i++) s = add_mod(s, out[(size_t)i * total + idx], q);
+        counts[idx] = s;
+    }
+}
+
 // sums[i][c] = sum_j resp[i][c][j] (mod q), one word per thread.
 __global__ void k_class_sums(const DevCtx* __restrict__ Cp, const u64* __restrict__ resp,
                              int n_pairs, u64* __restrict__ sums) {
@@ -89,6 +104,20 @@ cudaError_t launch_vp_infer(const LaunchInfo& li, const uint64_t* model, const u
     cudaError_t e = li.ext->vp(li, model, rgsw, items, resp, acc, grid, st);
     (*li.launches)++;
     return e;
+}
+
+cudaError_t launch_count_classes(const LaunchInfo& li, uint64_t* counts, const uint64_t* rgsw, size_t n,
+                                 uint64_t* out, uint64_t* acc, int grid, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    if (grid > (int)n) grid = (int)n;
+    cudaError_t e = li.ext->count(li, rgsw, (int)n, out, acc, grid, st);
+    (*li.launches)++;
+    if (e != cudaSuccess) return e;
+    const int threads = 256;
+    const size_t blocks = (li.rlwe_words + threads - 1) / threads;
+    k_add_rlwes<<<(unsigned)blocks, threads, 0, st>>>(li.dctx, counts, out, (int)n);
+    (*li.launches)++;
+    return cudaGetLastError();
 }
 
 cudaError_t launch_class_sums(const LaunchInfo& li, const uint64_t* resp, size_t n, uint64_t* sums,

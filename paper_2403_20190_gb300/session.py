@@ -83,6 +83,28 @@ class Session:
         B.hw_decrypt(self.ctx, key, B.HW_DEC_LWE, obj, count, out, stream)
         return out
 
+    # ------------------------------------------------ dataset balancing
+    def new_counts(self):
+        """Class-count ciphertext (one RLWE), zero."""
+        return self.words(self.sz["rlwe_words"])
+
+    def count_classes(self, counts, rgsw, n, scratch=None, stream=None):
+        if scratch is None:
+            scratch = self.words(B.hw_count_scratch_words(self.ctx, n), zero=False)
+        B.hw_count_classes(self.ctx, counts, rgsw, n, scratch, stream)
+        return counts
+
+    def class_counts(self, key, counts, stream=None):
+        """Decrypted class counts (l,) as an int64 device tensor."""
+        return self.decrypt_rlwe(key, counts, 1, stream)[: self.cfg.n_classes].contiguous()
+
+    def pdact_balanced(self, counts, class_counts, n, stream=None):
+        l = self.cfg.n_classes
+        scores = torch.empty(n * l, dtype=torch.int64, device=self.device)
+        labels = torch.empty(n, dtype=torch.int32, device=self.device)
+        B.hw_pdact_balanced(self.ctx, counts, class_counts, n, scores, labels, stream)
+        return scores.view(n, l), labels
+
     def pdact(self, counts, n, stream=None):
         l = self.cfg.n_classes
         scores = torch.empty(n * l, dtype=torch.int64, device=self.device)
