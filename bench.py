@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-ntt", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-balance", action="store_true")
+    ap.add_argument("--no-packing", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=40)
     ap.add_argument("--geometry", default="auto", choices=["auto", "default"],
                     help="kernel geometry: autotuned (cached per GPU and parameters) or the library default")
@@ -505,6 +506,42 @@ def gpu_arm(args, ws, rank, local, pg):
             ntt["cfg1"] = ntt_rate(s1, 262144)
             del s1
 
+    # horizontal packing (Section 6): plain vs packed inference on the
+    # Wisconsin-shaped ring (label bits low, z = 0: one VP answers both
+    # classes); the digit workloads keep a stored ciphertext per class
+    packing = None
+    if not args.no_packing:
+        pc = cfg if args.config == "cfg1" else get_config("cfg1")
+        ps = sess if args.config == "cfg1" else Session(pc, local, geometry="auto" if args.geometry == "auto" else None)
+        n_p = 100
+        pv, _ = make_dataset(pc, "test", n=n_p)
+        pkey = ps.keygen(pc.key_seed)
+        pbits = ps.encode(torch.from_numpy(pv).to(ps.device))
+        prg = ps.encrypt(pkey, pbits, None, seed=4242)
+        pmodel = ps.new_model()
+        pbufs = ps.infer_buffers(n_p)
+        rates = {}
+        for mode in (False, True):
+            ts = []
+            for k in range(4):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                ps.infer(pmodel, prg, n_p, bufs=pbufs, packed=mode)
+                b.record()
+                torch.cuda.synchronize()
+                if k:
+                    ts.append(a.elapsed_time(b))
+            rates["packed" if mode else "plain"] = n_p / (min(ts) / 1000.0)
+        psz = ps.sz
+        groups = min(pc.n_classes, 1 << psz["z"]) if psz["z"] <= psz["L"] else pc.n_classes
+        packing = {"workload": "cfg1", "inferences_per_s_plain": rates["plain"],
+                   "inferences_per_s_packed": rates["packed"],
+                   "vp_per_sample": {"plain": pc.n_classes * psz["k0"], "packed": groups * psz["k0"]},
+                   "applies_to_bench_workload": sz["z"] <= sz["L"] and min(cfg.n_classes, 1 << sz["z"]) < cfg.n_classes}
+        del pbufs, prg
+        if ps is not sess:
+            del ps
+
     # the same workload one request at a time: each request one train and one
     # test sample, encoded, encrypted, trained, inferred, decrypted, waited for
     single = None
@@ -556,6 +593,7 @@ def gpu_arm(args, ws, rank, local, pg):
             "train_modmul_per_s": train_modmul / (ph["train"] / 1000.0),
             "phases_ms": ph,
             "balancing": balancing,
+            "horizontal_packing": packing,
             "roofline": roofline,
             "ntt": ntt,
             "geometry": sess.geometry,

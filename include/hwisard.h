@@ -206,6 +206,18 @@ int hw_infer(hw_ctx* ctx, const uint64_t* model_dev, const uint64_t* rgsw_dev, s
              uint64_t* resp_dev, uint64_t* sums_dev, uint64_t* scratch_dev, size_t scratch_words,
              void* stream);
 
+/* hw_infer with horizontal packing (Section 6): the classes that share a
+ * stored ciphertext (c = g mod 2^z) and differ only in clear label bits
+ * above z are answered by one VP -- the accumulator is not rotated by those
+ * bits, and class c's response is ExtractLWE(acc, c >> z).  It needs
+ * min(l, 2^z) VPs per (sample, RAM) instead of l (cfg1: 1 instead of 2).
+ * Same buffers and layouts as hw_infer; the responses are different
+ * ciphertexts that decrypt to the same counters.  When a tree level is an
+ * encrypted address bit (z > L) nothing can be packed and it runs hw_infer. */
+int hw_infer_packed(hw_ctx* ctx, const uint64_t* model_dev, const uint64_t* rgsw_dev, size_t n,
+                    uint64_t* resp_dev, uint64_t* sums_dev, uint64_t* scratch_dev, size_t scratch_words,
+                    void* stream);
+
 /* DecRLWE / DecLWE (Section 2.4): phase b - a*s combined over the primes by
  * the CRT and rounded, m = floor((p*phi + floor(Q/2)) / Q) mod p.  what =
  * HW_DEC_RLWE: obj_dev holds count RLWEs, out_dev gets count*N values;

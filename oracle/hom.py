@@ -189,6 +189,92 @@ class Oracle:
         lib().or_vp(self.ctx, Lin, ptrs, clear, k, P.z, _p64(lwe))
         return lwe
 
+    # ------------------------------------------------ horizontal packing
+    def packing_groups(self):
+        """Classes that share a stored ciphertext and differ only in clear
+        rotation bits (label bits z..L-1), keyed by c mod 2^z; empty when a
+        tree level is an encrypted address bit (z > L): no packing then."""
+        P = self.P
+        if P.z > P.L:
+            return {}
+        g = {}
+        for c in range(self.cfg.n_classes):
+            g.setdefault(c % (1 << P.z), []).append(c)
+        return g
+
+    def extract_lwe(self, ct, k) -> np.ndarray:
+        """ExtractLWE(ct, k): the LWE of coefficient k of the phase,
+        a'_x = a_{k-x} for x <= k, -a_{N+k-x} otherwise, b' = b_k."""
+        P = self.P
+        n, r = P.n, P.r
+        a = ct[: r * n].reshape(r, n)
+        b = ct[r * n:].reshape(r, n)
+        out = np.zeros((r, n + 1), dtype=np.uint64)
+        for j in range(r):
+            q = int(P.q[j])
+            for x in range(n):
+                out[j, x] = a[j, k - x] if x <= k else (q - int(a[j, n + k - x])) % q
+            out[j, n] = b[j, k]
+        return out.reshape(-1)
+
+    def vp_item_packed(self, H, rgsw_by_slot, j, rho) -> dict:
+        """Horizontal packing (Section 6): one VP of H[j] for every class
+        c = rho (mod 2^z) at once -- the clear label bits above z are not
+        rotated, so the lookup of class c sits at coefficient c >> z of the
+        accumulator; returns {c: LWE}."""
+        P = self.P
+        k = P.L + P.a
+        ptrs = (u64p * k)()
+        clear = (ctypes.c_int * k)()
+        for t in range(P.L):
+            ptrs[t] = ctypes.cast(None, u64p)
+            clear[t] = ((rho >> t) & 1) if t < P.z else 0
+        for i in range(P.a):
+            d = int(self.ram_bits[j][i])
+            if d >= 0:
+                ptrs[P.L + i] = _p64(rgsw_by_slot[P.L + d])
+            else:
+                ptrs[P.L + i] = ctypes.cast(None, u64p)
+                clear[P.L + i] = 0
+        nl = 1 << P.z
+        Lin = (u64p * nl)()
+        rows = []
+        for v in range(nl):
+            if v in P.slot:
+                row = np.ascontiguousarray(H[j, P.slot[v]])
+                rows.append(row)
+                Lin[v] = _p64(row)
+            else:
+                Lin[v] = ctypes.cast(None, u64p)
+        acc = np.zeros(self.rlwe_words, dtype=np.uint64)
+        lib().or_vp_rlwe(self.ctx, Lin, ptrs, clear, k, P.z, _p64(acc))
+        return {c: self.extract_lwe(acc, c >> P.z) for c in self.packing_groups()[rho]}
+
+    def infer_packed(self, H, s, seed, data_bits, rams=None, sample_offset=0):
+        """Inference with horizontal packing: responses u[i][c][j] (LWE) and
+        per-class sums, as infer() lays them out."""
+        P = self.P
+        l = self.cfg.n_classes
+        groups = self.packing_groups()
+        if not groups:
+            return self.infer(H, s, seed, data_bits, rams, sample_offset)
+        rams = list(range(P.k0)) if rams is None else list(rams)
+        slots = self.slots_for_rams(rams, with_labels=False)
+        n = data_bits.shape[0]
+        lw = P.r * (P.n + 1)
+        resp = np.zeros((n, l, len(rams), lw), dtype=np.uint64)
+        sums = np.zeros((n, l, lw), dtype=np.uint64)
+        for i in range(n):
+            rg = self.encrypt_slots(s, seed, sample_offset + i, data_bits[i], 0, slots)
+            for jj, j in enumerate(rams):
+                for rho in groups:
+                    for c, lwe in self.vp_item_packed(H, rg, j, rho).items():
+                        resp[i, c, jj] = lwe
+            for c in range(l):
+                for jj in range(len(rams)):
+                    lib().or_lwe_add(self.ctx, _p64(sums[i, c]), _p64(np.ascontiguousarray(resp[i, c, jj])))
+        return resp, sums
+
     def infer(self, H, s, seed, data_bits, rams=None, sample_offset=0, trivial=False):
         """Algorithm 7 (PD-act): responses u[i][c][j] as LWE ciphertexts and
         the per-class sums over the listed RAMs."""

@@ -610,6 +610,29 @@ void or_ivp(const or_ctx *c, const u64 *lhat, const u64 *const *rgsw, const int 
  * j in [0, n); then blind rotation of L_0 by b_z..b_{k-1} with weights
  * +2^0, +2^1, ...; then ExtractLWE(., 0).  Lin holds 2^z RLWE pointers,
  * NULL meaning an all-zero ciphertext. */
+/* The accumulator of VP before ExtractLWE: the tree, then BlindRotate over
+ * bits z..k-1 (clear bits rotate exactly or are skipped); used by horizontal
+ * packing, which extracts several coefficients of one accumulator. */
+void or_vp_rlwe(const or_ctx *c, const u64 *const *Lin, const u64 *const *rgsw, const int *clear,
+                int k, int z, u64 *out) {
+    size_t rlwe = or_rlwe_words(c);
+    int nl = 1 << z;
+    u64 *L = (u64 *)calloc(rlwe * nl, sizeof(u64));
+    for (int v = 0; v < nl; v++)
+        if (Lin[v]) memcpy(L + (size_t)v * rlwe, Lin[v], sizeof(u64) * rlwe);
+    for (int lvl = z - 1; lvl >= 0; lvl--) {
+        int n = 1 << lvl;
+        for (int j = 0; j < n; j++) {
+            u64 *lo = L + (size_t)j * rlwe, *hi = L + (size_t)(j + n) * rlwe;
+            if (rgsw[lvl] != NULL) or_cmux(c, rgsw[lvl], hi, lo, lo);
+            else if (clear[lvl]) memcpy(lo, hi, sizeof(u64) * rlwe);
+        }
+    }
+    or_blind_rotate(c, L, rgsw + z, clear + z, k - z, +1);
+    memcpy(out, L, sizeof(u64) * rlwe);
+    free(L);
+}
+
 void or_vp(const or_ctx *c, const u64 *const *Lin, const u64 *const *rgsw, const int *clear,
            int k, int z, u64 *lwe) {
     size_t rlwe = or_rlwe_words(c);

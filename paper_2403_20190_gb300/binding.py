@@ -75,6 +75,7 @@ _SIGS = {
     "hw_train_accumulate": (ctypes.c_int, [_VP, _VP, _VP, _SZ, _VP, _SZ, _VP]),
     "hw_infer": (ctypes.c_int, [_VP, _VP, _VP, _SZ, _VP, _VP, _VP, _SZ, _VP]),
     "hw_infer_static_scratch": (ctypes.c_int, [_VP, _VP, _VP, _SZ, _VP, _VP, _VP]),
+    "hw_infer_packed": (ctypes.c_int, [_VP, _VP, _VP, _SZ, _VP, _VP, _VP, _SZ, _VP]),
     "hw_decrypt": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, _SZ, _VP, _VP]),
     "hw_pdact": (ctypes.c_int, [_VP, _VP, _SZ, _VP, _VP, _VP]),
     "hw_export_rgsw": (ctypes.c_int, [_VP, _VP, _SZ, _VP, _VP]),
@@ -268,6 +269,11 @@ def hw_train_accumulate(ctx, model, rgsw, n, scratch, stream=None):
 def hw_infer(ctx, model, rgsw, n, resp, sums, scratch, stream=None):
     _check(load().hw_infer(ctx.handle, _ptr(model), _ptr(rgsw), n, _ptr(resp), _ptr(sums),
                            _ptr(scratch), scratch.numel(), _stream(stream)), "hw_infer")
+
+
+def hw_infer_packed(ctx, model, rgsw, n, resp, sums, scratch, stream=None):
+    _check(load().hw_infer_packed(ctx.handle, _ptr(model), _ptr(rgsw), n, _ptr(resp), _ptr(sums),
+                                  _ptr(scratch), scratch.numel(), _stream(stream)), "hw_infer_packed")
 
 
 def hw_infer_static_scratch(ctx, model, rgsw, n, resp, sums, stream=None):

@@ -545,6 +545,7 @@ extern "C" int hw_create_tuned(const hw_params* p, const hw_geometry* g, int cud
     li.n_slots = H.n_slots;
     li.L = L;
     li.dnum = dnum;
+    li.z = z;
     li.rlwe_words = H.rlwe_words;
     li.lwe_words = H.lwe_words;
     li.rgsw_words = H.rgsw_words;
@@ -722,6 +723,22 @@ extern "C" int hw_infer(hw_ctx* c, const uint64_t* model, const uint64_t* rgsw, 
     int grid = c->li.ext_grid;
     cudaStream_t st = (cudaStream_t)stream;
     CUDA_TRY(launch_vp_infer(c->li, model, rgsw, n, resp, scratch, grid, st));
+    CUDA_TRY(launch_class_sums(c->li, resp, n, sums, st));
+    return HW_OK;
+}
+
+extern "C" int hw_infer_packed(hw_ctx* c, const uint64_t* model, const uint64_t* rgsw, size_t n,
+                               uint64_t* resp, uint64_t* sums, uint64_t* scratch, size_t scratch_words,
+                               void* stream) {
+    CHECK_CTX(c);
+    if (n == 0) return HW_OK;
+    if (!model || !rgsw || !resp || !sums || !scratch)
+        return fail(HW_EINVAL, "hw_infer_packed: null buffer");
+    size_t need = hw_infer_scratch_words(c, n);
+    if (scratch_words < need)
+        return fail(HW_ENOMEM, "hw_infer_packed: scratch has %zu words, needs %zu", scratch_words, need);
+    cudaStream_t st = (cudaStream_t)stream;
+    CUDA_TRY(launch_vp_infer(c->li, model, rgsw, n, resp, scratch, c->li.ext_grid, st, 1));
     CUDA_TRY(launch_class_sums(c->li, resp, n, sums, st));
     return HW_OK;
 }

@@ -211,6 +211,23 @@ __global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP, SM>::T, ExtCfg<LOGN, LO
     }
 }
 
+// ExtractLWE(ct, k) written by the block: the LWE of coefficient k of the
+// phase, a'_y = a_{k-y} for y <= k, -a_{N+k-y} otherwise, b' = b_k (per
+// prime, [prime][N a'-coefficients, b']).
+__device__ __forceinline__ void extract_lwe_at(const DevCtx& C, const u64* ct, int k, u64* lw) {
+    const int tid = threadIdx.x, T = blockDim.x;
+    for (int jp = 0; jp < C.r; jp++) {
+        const u64 q = C.P[jp].q;
+        const u64* pa = ct + (size_t)jp * C.n;
+        u64* o = lw + (size_t)jp * (C.n + 1);
+        for (int y = tid; y < C.n; y += T) {
+            const int x = k - y;
+            o[y] = x >= 0 ? pa[x] : neg_mod(pa[x + C.n], q);
+        }
+        if (tid == 0) o[C.n] = ct[(size_t)(C.r + jp) * C.n + k];
+    }
+}
+
 // ---------------------------------------------------------------------------
 // VP inference.  One thread block per item (sample i, RAM j, class c).
 // Label bits are in clear: tree levels driven by label bits select a stored
@@ -220,7 +237,7 @@ __global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP, SM>::T, ExtCfg<LOGN, LO
 // weights +2^k (X^-2^k) and the last CMUX writes ExtractLWE(., 0) directly.
 // Per-block scratch: two accumulators and their evaluation forms.
 // ---------------------------------------------------------------------------
-template <int LOGN, int LOGE, int NP, int SM>
+template <int LOGN, int LOGE, int NP, int SM, int PK>
 __global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP, SM>::T, ExtCfg<LOGN, LOGE, NP, SM>::MINB)
     k_vp_infer(const DevCtx* __restrict__ Cp, const u64* __restrict__ model,
                const u64* __restrict__ rgsw, int n_items, u64* __restrict__ resp,
@@ -240,21 +257,27 @@ __global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP, SM>::T, ExtCfg<LOGN, LO
     u64* accn = SM == 1 ? smem + NP * X::PADDED : blk + 2 * rl;
     const int kbits = C.L + C.a;
     const int l = C.n_classes;
+    // PK (horizontal packing, z <= L only): one item per group of classes
+    // sharing a stored ciphertext (c = g mod 2^z); their clear label bits
+    // above z are not rotated, so class c's lookup is coefficient c >> z of
+    // the accumulator
+    const int G = PK ? (l < (1 << C.z) ? l : (1 << C.z)) : l;
     for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
-        const int c = item % l;
-        const int ij = item / l;
+        const int c = item % G;  // the class, or the group residue with PK
+        const int ij = item / G;
         const int i = ij / C.k0, j = ij % C.k0;
         const u64* sample = rgsw + (size_t)i * C.sample_words;
         const u64* Hj = model + (size_t)j * C.k1 * rl;
         // items run class-fastest (the l classes of a (sample, RAM) share its
         // RGSW bits); responses are stored [sample][class][RAM]
         u64* lwe = resp + (((size_t)i * l + c) * C.k0 + j) * C.lwe_words;
+        [[maybe_unused]] const size_t class_stride = (size_t)C.k0 * C.lwe_words;  // next class's response
         const u64* src;
         const u64* srcn = nullptr;  // evaluation form of src, once known
         int e0;
         if (C.z <= C.L) {
             src = Hj + (size_t)C.slot_of[c & ((1 << C.z) - 1)] * rl;
-            const int R = c >> C.z;  // clear label bits among the rotation bits
+            const int R = PK ? 0 : c >> C.z;  // clear label bits among the rotation bits
             e0 = (two_n - R) % two_n;
         } else {
             // one encrypted tree level (bit z-1, an address bit): CMUX(C, L_{v+n}, L_v)
@@ -275,6 +298,14 @@ __global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP, SM>::T, ExtCfg<LOGN, LO
         int last = -1;
         for (int t = (C.z > C.L ? C.z : C.L); t < kbits; t++)
             if (bit_slot(C, j, t) >= 0) last = t;
+        if constexpr (PK) {
+            if (last < 0) {  // nothing encrypted left: extract every class of the group
+                for (int cc = c, k = 0; cc < l; cc += 1 << C.z, k++)
+                    extract_lwe_at(C, src, k, lwe + (size_t)(cc - c) * class_stride);
+                __syncthreads();
+                continue;
+            }
+        }
         if (last < 0) {  // nothing encrypted left: extract src * X^e0
             for (int jp = 0; jp < C.r; jp++) {
                 const u64 q = C.P[jp].q;
@@ -306,7 +337,13 @@ __global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP, SM>::T, ExtCfg<LOGN, LO
                 for (int t2 = t + 1; t2 < kbits && nslot < 0; t2++) nslot = bit_slot(C, j, t2);
             const ExtNtt nt{srcn, t == last ? nullptr : accn, t - C.z, 1,
                             nslot >= 0 ? sample + (size_t)nslot * C.rgsw_words : nullptr, 0};
-            if (t == last) {
+            if (PK && t == last) {
+                ext_product<LOGN, LOGE, NP, SM == 2>(C, sample + (size_t)slot * C.rgsw_words, src, eA, src,
+                                                  e0, EXT_ADD, acc[cur ^ 1], xc, nt);
+                for (int cc = c, k = 0; cc < l; cc += 1 << C.z, k++)
+                    extract_lwe_at(C, acc[cur ^ 1], k, lwe + (size_t)(cc - c) * class_stride);
+                __syncthreads();
+            } else if (t == last) {
                 ext_product<LOGN, LOGE, NP, SM == 2>(C, sample + (size_t)slot * C.rgsw_words, src, eA, src,
                                                   e0, EXT_LWE, lwe, xc, nt);
             } else {
@@ -383,7 +420,10 @@ struct ExtVariant {
             e = cudaFuncSetAttribute(k_ivp_train<LOGN, LOGE, NP, SM>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_vp_infer<LOGN, LOGE, NP, SM>,
+            e = cudaFuncSetAttribute(k_vp_infer<LOGN, LOGE, NP, SM, 0>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_vp_infer<LOGN, LOGE, NP, SM, 1>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k_count_classes<LOGN, LOGE, NP, SM>,
@@ -395,7 +435,7 @@ struct ExtVariant {
     static int occupancy(size_t smem) {
         int a = 0, b = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_ivp_train<LOGN, LOGE, NP, SM>, X::T, smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_vp_infer<LOGN, LOGE, NP, SM>, X::T, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_vp_infer<LOGN, LOGE, NP, SM, 0>, X::T, smem);
         int o = a < b ? a : b;
         return o < 1 ? 1 : o;
     }
@@ -441,9 +481,12 @@ struct ExtVariant {
                                   (u64*)out, (u64*)acc);
     }
     static cudaError_t vp(const LaunchInfo& li, const uint64_t* model, const uint64_t* rgsw, int items,
-                          uint64_t* resp, uint64_t* acc, int grid, cudaStream_t st) {
+                          uint64_t* resp, uint64_t* acc, int grid, int packed, cudaStream_t st) {
         Launch L(li, grid, st, acc, (size_t)grid * SCRATCH_RLWE * li.rlwe_words * sizeof(u64));
-        return cudaLaunchKernelEx(&L.cfg, k_vp_infer<LOGN, LOGE, NP, SM>, li.dctx, (const u64*)model,
+        if (packed)
+            return cudaLaunchKernelEx(&L.cfg, k_vp_infer<LOGN, LOGE, NP, SM, 1>, li.dctx, (const u64*)model,
+                                      (const u64*)rgsw, items, (u64*)resp, (u64*)acc);
+        return cudaLaunchKernelEx(&L.cfg, k_vp_infer<LOGN, LOGE, NP, SM, 0>, li.dctx, (const u64*)model,
                                   (const u64*)rgsw, items, (u64*)resp, (u64*)acc);
     }
     static cudaError_t count(const LaunchInfo& li, const uint64_t* rgsw, int items, uint64_t* out,

@@ -25,7 +25,7 @@ struct ExtOps {
     cudaError_t (*ivp)(const LaunchInfo&, const uint64_t* rgsw, int items, uint64_t* out,
                        uint64_t* acc, int grid, cudaStream_t);
     cudaError_t (*vp)(const LaunchInfo&, const uint64_t* model, const uint64_t* rgsw, int items,
-                      uint64_t* resp, uint64_t* acc, int grid, cudaStream_t);
+                      uint64_t* resp, uint64_t* acc, int grid, int packed, cudaStream_t);
     cudaError_t (*count)(const LaunchInfo&, const uint64_t* rgsw, int items, uint64_t* out,
                          uint64_t* acc, int grid, cudaStream_t);
 };
@@ -41,6 +41,7 @@ struct LaunchInfo {
     size_t ext_smem;    // their dynamic shared memory per block
     int ntt_loge;       // hw_ntt_*: 2^ntt_loge residues per thread
     int ntt_limbs;      // hw_ntt_*: 1 = 32-bit arithmetic, 2 = 64-bit
+    int z;              // CMUX-tree levels (horizontal packing needs z <= L)
     size_t l2_persist;     // > 0: persisting L2 bytes for the IVP / VP accumulators
     size_t l2_window_max;  // largest access-policy window the device takes
     unsigned long long* launches;  // launch counter
@@ -65,7 +66,8 @@ cudaError_t launch_ivp_train(const LaunchInfo& li, const uint64_t* rgsw, size_t 
 cudaError_t launch_accumulate(const LaunchInfo& li, uint64_t* model, const uint64_t* out, size_t n,
                               cudaStream_t st);
 cudaError_t launch_vp_infer(const LaunchInfo& li, const uint64_t* model, const uint64_t* rgsw,
-                            size_t n, uint64_t* resp, uint64_t* acc, int grid, cudaStream_t st);
+                            size_t n, uint64_t* resp, uint64_t* acc, int grid, cudaStream_t st,
+                            int packed = 0);
 cudaError_t launch_count_classes(const LaunchInfo& li, uint64_t* counts, const uint64_t* rgsw, size_t n,
                                  uint64_t* out, uint64_t* acc, int grid, cudaStream_t st);
 cudaError_t launch_pdact_balanced(const LaunchInfo& li, const int64_t* counts, const int64_t* class_counts,

@@ -97,11 +97,14 @@ cudaError_t launch_accumulate(const LaunchInfo& li, uint64_t* model, const uint6
 }
 
 cudaError_t launch_vp_infer(const LaunchInfo& li, const uint64_t* model, const uint64_t* rgsw,
-                            size_t n, uint64_t* resp, uint64_t* acc, int grid, cudaStream_t st) {
-    int items = (int)(n * li.k0 * li.n_classes);
+                            size_t n, uint64_t* resp, uint64_t* acc, int grid, cudaStream_t st,
+                            int packed) {
+    if (li.z > li.L) packed = 0;  // a tree level is an encrypted address bit: no packing
+    const int groups = packed ? (li.n_classes < (1 << li.z) ? li.n_classes : (1 << li.z)) : li.n_classes;
+    int items = (int)(n * li.k0 * groups);
     if (items == 0) return cudaSuccess;
     if (grid > items) grid = items;
-    cudaError_t e = li.ext->vp(li, model, rgsw, items, resp, acc, grid, st);
+    cudaError_t e = li.ext->vp(li, model, rgsw, items, resp, acc, grid, packed, st);
     (*li.launches)++;
     return e;
 }

@@ -67,9 +67,10 @@ class Session:
         scratch = self.words(B.hw_infer_scratch_words(self.ctx, n), zero=False)
         return resp, sums, scratch
 
-    def infer(self, model, rgsw, n, bufs=None, stream=None):
+    def infer(self, model, rgsw, n, bufs=None, stream=None, packed=False):
         resp, sums, scratch = bufs if bufs is not None else self.infer_buffers(n)
-        B.hw_infer(self.ctx, model, rgsw, n, resp, sums, scratch, stream)
+        fn = B.hw_infer_packed if packed else B.hw_infer
+        fn(self.ctx, model, rgsw, n, resp, sums, scratch, stream)
         return resp, sums
 
     # ---------------------------------------------------------------- client
