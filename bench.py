@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-balance", action="store_true")
     ap.add_argument("--no-packing", action="store_true")
+    ap.add_argument("--no-keyswitch", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=40)
     ap.add_argument("--geometry", default="auto", choices=["auto", "default"],
                     help="kernel geometry: autotuned (cached per GPU and parameters) or the library default")
@@ -429,6 +430,32 @@ def gpu_arm(args, ws, rank, local, pg):
                      "ext_products_per_sample": sz["L"]}
         del bal_scr
 
+    # PackingKeySwitching (Section 2.4): the test batch's responses packed
+    # into one RLWE per sample (what Algorithm 7 returns for PD-act)
+    keyswitch = None
+    if not args.no_keyswitch:
+        resp = st.ibufs[0]
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        ksk = sess.ksk_gen(key, cfg.key_seed + 1, stream=stream)
+        e1.record(stream)
+        pscr = sess.words(B.hw_pack_scratch_words(sess.ctx), zero=False)
+        sess.pack_responses(ksk, resp, bsz, scratch=pscr, stream=stream)  # warm-up
+        torch.cuda.synchronize()
+        t_pack = []
+        for _ in range(2):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            sess.pack_responses(ksk, resp, bsz, scratch=pscr, stream=stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            t_pack.append(a.elapsed_time(b))
+        keyswitch = {"pack_ms_per_step": min(t_pack), "ksk_gen_ms_once": e0.elapsed_time(e1),
+                     "ksk_bytes": B.hw_ksk_words(sess.ctx) * 8,
+                     "response_bytes_per_sample": {"lwe": sz["resp_words"] * 8, "packed": sz["rlwe_words"] * 8},
+                     "share_of_infer": min(t_pack) / ph["infer"]}
+        del ksk, pscr
+
     # e2e through the C ABI with pinned host buffers, copies inside the timed region
     e2e = None
     if not args.no_e2e:
@@ -594,6 +621,7 @@ def gpu_arm(args, ws, rank, local, pg):
             "phases_ms": ph,
             "balancing": balancing,
             "horizontal_packing": packing,
+            "packing_keyswitch": keyswitch,
             "roofline": roofline,
             "ntt": ntt,
             "geometry": sess.geometry,

@@ -253,6 +253,25 @@ int hw_pdact(hw_ctx* ctx, const int64_t* counts_dev, size_t n, int64_t* scores_d
 int hw_infer_static_scratch(hw_ctx* ctx, const uint64_t* model_dev, const uint64_t* rgsw_dev,
                             size_t n, uint64_t* resp_dev, uint64_t* sums_dev, void* stream);
 
+/* PackingKeySwitching (Section 2.4; Algorithm 7 returns its result for
+ * PD-act): packs the l * k0 responses of each test sample into one RLWE
+ * encrypting sum_i u_i X^i, i = c * k0 + j (the response order), so a
+ * client receives one RLWE per sample instead of l * k0 LWEs.
+ * Key: hw_ksk_words(ctx) device words, N * dnum RLWE rows encrypting
+ * s_x * g_rho (x < N, gadget row rho) under the secret key, made by
+ * hw_ksk_gen from key_dev and `seed` (KSK_A / KSK_E streams).
+ * Packing: C = sum_i X^i (0, b_i) - sum_{x,rho} KS_{x,rho} * D_{x,rho}(X),
+ * D_{x,rho}(X) = sum_i Dec_rho(a_{i,x}) X^i (the RGSW gadget).
+ * resp_dev: n * resp_words (as hw_infer writes them); packed_dev: n *
+ * rlwe_words, canonical RLWEs (decrypt with HW_DEC_RLWE: coefficient i is
+ * u_i); scratch_dev: hw_pack_scratch_words(ctx) words, reused per sample.
+ * HW_EINVAL when l * k0 > N. */
+size_t hw_ksk_words(const hw_ctx* ctx);
+int hw_ksk_gen(hw_ctx* ctx, const uint64_t* key_dev, uint64_t seed, uint64_t* ksk_dev, void* stream);
+size_t hw_pack_scratch_words(const hw_ctx* ctx);
+int hw_pack_responses(hw_ctx* ctx, const uint64_t* ksk_dev, const uint64_t* resp_dev, size_t n,
+                      uint64_t* packed_dev, uint64_t* scratch_dev, size_t scratch_words, void* stream);
+
 /* Dataset balancing (Section 3.6.1): for each of n encrypted training
  * samples (the same rgsw_dev as hw_train_accumulate), a small IVP over its
  * label bits -- BlindRotate from (0, Delta) with weights X^(+2^t) over the

@@ -71,6 +71,8 @@ def lib():
             "or_blind_rotate": (None, [vp, u64p, ctypes.POINTER(u64p), ctypes.POINTER(ctypes.c_int),
                                        ctypes.c_int, ctypes.c_int]),
             "or_extract_lwe0": (None, [vp, u64p, u64p]),
+            "or_ksk_gen": (None, [vp, i8p, u64, ctypes.c_int, u64p]),
+            "or_pack_keyswitch": (None, [vp, u64p, u64p, ctypes.c_int, u64p]),
             "or_vp_rlwe": (None, [vp, ctypes.POINTER(u64p), ctypes.POINTER(u64p), ctypes.POINTER(ctypes.c_int),
                                   ctypes.c_int, ctypes.c_int, u64p]),
             "or_lwe_phase": (None, [vp, i8p, u64p, u64p]),

@@ -189,6 +189,25 @@ class Oracle:
         lib().or_vp(self.ctx, Lin, ptrs, clear, k, P.z, _p64(lwe))
         return lwe
 
+    # --------------------------------------------- PackingKeySwitching
+    def ksk_gen(self, s, seed, trivial=False) -> np.ndarray:
+        """PackingKeySwitching key (Section 2.4): N * dnum RLWE rows
+        (x, rho) encrypting s_x * g_rho, coefficient form."""
+        P = self.P
+        out = np.zeros(P.n * P.dnum * self.rlwe_words, dtype=np.uint64)
+        lib().or_ksk_gen(self.ctx, s.ctypes.data_as(i8p), seed, int(trivial), _p64(out))
+        return out
+
+    def pack(self, ksk, lwes) -> np.ndarray:
+        """PackingKeySwitching of k <= N LWEs (k, r*(N+1)) into one RLWE
+        encrypting sum_i m_i X^i."""
+        lwes = np.ascontiguousarray(lwes, dtype=np.uint64).reshape(-1)
+        k = lwes.size // (self.P.r * (self.P.n + 1))
+        assert k <= self.P.n
+        out = np.zeros(self.rlwe_words, dtype=np.uint64)
+        lib().or_pack_keyswitch(self.ctx, _p64(ksk), _p64(lwes), k, _p64(out))
+        return out
+
     # ------------------------------------------------ horizontal packing
     def packing_groups(self):
         """Classes that share a stored ciphertext and differ only in clear

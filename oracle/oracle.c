@@ -132,7 +132,7 @@ void or_philox(const u64 ctr[4], const u64 key[2], u64 out[4]) {
 }
 
 /* Stream tags, carried in the second key word. */
-enum { TAG_KEY = 1, TAG_RGSW_A = 2, TAG_RGSW_E = 3, TAG_PERM = 4, TAG_H3 = 5 };
+enum { TAG_KEY = 1, TAG_RGSW_A = 2, TAG_RGSW_E = 3, TAG_PERM = 4, TAG_H3 = 5, TAG_KSK_A = 7, TAG_KSK_E = 8 };
 
 static void draw(u64 seed, u64 tag, u64 c0, u64 c1, u64 c2, u64 out[4]) {
     u64 ctr[4] = {c0, c1, c2, 0};
@@ -456,6 +456,83 @@ static void decompose(const or_ctx *c, const u64 *comp_res /* [r][N] */, int rho
 /* Exported for the recomposition test: digit rho of one component. */
 void or_decompose(const or_ctx *c, const u64 *comp_res, int rho, u64 *digit) {
     decompose(c, comp_res, rho, digit);
+}
+
+/* ------------------------------------------------------------------ */
+/* PackingKeySwitching (Section 2.4).  Key: for every LWE key coefficient */
+/* x < N and gadget row rho < dnum (row = x*dnum + rho), an RLWE         */
+/* (a, a*s + e + s_x * g_rho) with g_rho the gadget value at prime       */
+/* rho / dpp (0 at the others); a from TAG_KSK_A (two words per          */
+/* coefficient, counter (k>>1, row*r + j, 0)), e from TAG_KSK_E (counter */
+/* (k>>2, row, 0)).  Stored in coefficient form, rows in order.          */
+/* ------------------------------------------------------------------ */
+void or_ksk_gen(const or_ctx *c, const int8_t *s, u64 seed, int trivial, u64 *ksk) {
+    int n = c->n, r = c->r;
+    size_t rlwe = or_rlwe_words(c);
+    u64 *spoly = (u64 *)malloc(sizeof(u64) * n);
+    long long *e = (long long *)malloc(sizeof(long long) * n);
+    for (int x = 0; x < n; x++) {
+        for (int rho = 0; rho < c->dnum; rho++) {
+            const u64 row = (u64)x * c->dnum + rho;
+            int gi = rho / c->dpp, gk = rho % c->dpp;
+            for (int k = 0; k < n; k++) {
+                u64 w[4];
+                draw(seed, TAG_KSK_E, (u64)k >> 2, row, 0, w);
+                e[k] = trivial ? 0 : gaussian(c, w[k & 3]);
+            }
+            u64 *out = ksk + row * rlwe;
+            for (int j = 0; j < r; j++) {
+                u64 q = c->q[j];
+                u64 *a = out + (size_t)(0 * r + j) * n, *b = out + (size_t)(1 * r + j) * n;
+                for (int k = 0; k < n; k++) spoly[k] = from_signed(s[k], q);
+                for (int k = 0; k < n; k++) {
+                    u64 w[4];
+                    draw(seed, TAG_KSK_A, (u64)k >> 1, row * r + j, 0, w);
+                    u64 hi = w[2 * (k & 1)], lo = w[2 * (k & 1) + 1];
+                    a[k] = trivial ? 0 : (u64)((((u128)hi << 64) | lo) % q);
+                }
+                or_poly_mul(a, spoly, b, c->log_n, q, c->psi[j]);
+                for (int k = 0; k < n; k++) b[k] = addmod(b[k], from_signed(e[k], q), q);
+                if (j == gi) {
+                    u64 g = c->log_beta ? powmod((u64)1 << c->log_beta, (u64)gk, q) : 1;
+                    b[0] = addmod(b[0], mulmod(from_signed(s[x], q), g, q), q);
+                }
+            }
+        }
+    }
+    free(spoly); free(e);
+}
+
+/* Packing of k <= N LWE ciphertexts (each [prime][N a', then b']) into one
+ * RLWE encrypting sum_i m_i X^i:
+ *   C = sum_i X^i (0, b_i) - sum_{x, rho} KSK_{x,rho} * D_{x,rho}(X),
+ *   D_{x,rho}(X) = sum_i Dec_rho(a'_{i,x}) X^i, digits lifted to every prime. */
+void or_pack_keyswitch(const or_ctx *c, const u64 *ksk, const u64 *lwes, int k, u64 *out) {
+    int n = c->n, r = c->r;
+    size_t rlwe = or_rlwe_words(c), lw = (size_t)r * (n + 1);
+    u64 *A = (u64 *)malloc(sizeof(u64) * (size_t)r * n);
+    u64 *D = (u64 *)malloc(sizeof(u64) * (size_t)r * n);
+    u64 *t = (u64 *)malloc(sizeof(u64) * n);
+    memset(out, 0, sizeof(u64) * rlwe);
+    for (int i = 0; i < k; i++)
+        for (int j = 0; j < r; j++) out[(size_t)(r + j) * n + i] = lwes[i * lw + (size_t)j * (n + 1) + n];
+    for (int x = 0; x < n; x++) {
+        memset(A, 0, sizeof(u64) * (size_t)r * n);
+        for (int i = 0; i < k; i++)
+            for (int j = 0; j < r; j++) A[(size_t)j * n + i] = lwes[i * lw + (size_t)j * (n + 1) + x];
+        for (int rho = 0; rho < c->dnum; rho++) {
+            decompose(c, A, rho, D);
+            const u64 *row = ksk + ((size_t)x * c->dnum + rho) * rlwe;
+            for (int comp = 0; comp < 2; comp++)
+                for (int j = 0; j < r; j++) {
+                    u64 q = c->q[j];
+                    or_poly_mul(row + (size_t)(comp * r + j) * n, D + (size_t)j * n, t, c->log_n, q, c->psi[j]);
+                    u64 *o = out + (size_t)(comp * r + j) * n;
+                    for (int y = 0; y < n; y++) o[y] = submod(o[y], t[y], q);
+                }
+        }
+    }
+    free(A); free(D); free(t);
 }
 
 /* External product C [x] c (Section 2.4): sum over gadget rows of

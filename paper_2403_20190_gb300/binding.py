@@ -81,6 +81,10 @@ _SIGS = {
     "hw_export_rgsw": (ctypes.c_int, [_VP, _VP, _SZ, _VP, _VP]),
     "hw_import_rgsw": (ctypes.c_int, [_VP, _VP, _SZ, _VP, _VP]),
     "hw_count_scratch_words": (_SZ, [_VP, _SZ]),
+    "hw_ksk_words": (_SZ, [_VP]),
+    "hw_ksk_gen": (ctypes.c_int, [_VP, _VP, _U64, _VP, _VP]),
+    "hw_pack_scratch_words": (_SZ, [_VP]),
+    "hw_pack_responses": (ctypes.c_int, [_VP, _VP, _VP, _SZ, _VP, _VP, _SZ, _VP]),
     "hw_count_classes": (ctypes.c_int, [_VP, _VP, _VP, _SZ, _VP, _SZ, _VP]),
     "hw_pdact_balanced": (ctypes.c_int, [_VP, _VP, _VP, _SZ, _VP, _VP, _VP]),
     "hw_ntt_forward": (ctypes.c_int, [_VP, _VP, _SZ, _VP]),
@@ -301,6 +305,23 @@ def hw_export_rgsw(ctx, rgsw, count, out, stream=None):
 def hw_import_rgsw(ctx, canonical, count, rgsw, stream=None):
     _check(load().hw_import_rgsw(ctx.handle, _ptr(canonical), count, _ptr(rgsw), _stream(stream)),
            "hw_import_rgsw")
+
+
+def hw_ksk_words(ctx) -> int:
+    return int(load().hw_ksk_words(ctx.handle))
+
+
+def hw_ksk_gen(ctx, key, seed, ksk, stream=None):
+    _check(load().hw_ksk_gen(ctx.handle, _ptr(key), seed, _ptr(ksk), _stream(stream)), "hw_ksk_gen")
+
+
+def hw_pack_scratch_words(ctx) -> int:
+    return int(load().hw_pack_scratch_words(ctx.handle))
+
+
+def hw_pack_responses(ctx, ksk, resp, n, packed, scratch, stream=None):
+    _check(load().hw_pack_responses(ctx.handle, _ptr(ksk), _ptr(resp), n, _ptr(packed), _ptr(scratch),
+                                    scratch.numel(), _stream(stream)), "hw_pack_responses")
 
 
 def hw_count_scratch_words(ctx, n) -> int:

@@ -796,6 +796,34 @@ extern "C" int hw_pdact_balanced(hw_ctx* c, const int64_t* counts, const int64_t
     return HW_OK;
 }
 
+extern "C" size_t hw_ksk_words(const hw_ctx* c) {
+    return c ? (size_t)c->sz.n * c->sz.dnum * c->sz.rlwe_words : 0;
+}
+
+extern "C" int hw_ksk_gen(hw_ctx* c, const uint64_t* key, uint64_t seed, uint64_t* ksk, void* stream) {
+    CHECK_CTX(c);
+    if (!key || !ksk) return fail(HW_EINVAL, "hw_ksk_gen: null buffer");
+    CUDA_TRY(launch_ksk_gen(c->li, key, seed, ksk, (cudaStream_t)stream));
+    return HW_OK;
+}
+
+extern "C" size_t hw_pack_scratch_words(const hw_ctx* c) { return c ? hw_pack_scratch_words_li(c->li) : 0; }
+
+extern "C" int hw_pack_responses(hw_ctx* c, const uint64_t* ksk, const uint64_t* resp, size_t n,
+                                 uint64_t* packed, uint64_t* scratch, size_t scratch_words, void* stream) {
+    CHECK_CTX(c);
+    if (n == 0) return HW_OK;
+    if (!ksk || !resp || !packed || !scratch) return fail(HW_EINVAL, "hw_pack_responses: null buffer");
+    if ((size_t)c->sz.k0 * c->prm.n_classes > (size_t)c->sz.n)
+        return fail(HW_EINVAL, "hw_pack_responses: %d responses per sample exceed N = %d",
+                    c->sz.k0 * c->prm.n_classes, c->sz.n);
+    const size_t need = hw_pack_scratch_words_li(c->li);
+    if (scratch_words < need)
+        return fail(HW_ENOMEM, "hw_pack_responses: scratch needs %zu words, got %zu", need, scratch_words);
+    CUDA_TRY(launch_pack(c->li, ksk, resp, n, packed, scratch, (cudaStream_t)stream));
+    return HW_OK;
+}
+
 extern "C" int hw_export_rgsw(hw_ctx* c, const uint64_t* rgsw, size_t count, uint64_t* out,
                               void* stream) {
     CHECK_CTX(c);

@@ -4,25 +4,11 @@
 // size's translation unit instantiates its geometries and exposes them as a
 // table of launchers (ExtOps) that the context picks from.
 #pragma once
-#include "cdt_table.h"
+#include "cdt.cuh"
 #include "hw_internal.cuh"
 #include "hw_launch.h"
 
 #include <cstring>
-
-// The thresholds live in constant memory, statically initialised in every
-// translation unit that samples (all threads read the same entry).
-static __constant__ u64 c_cdt[HW_CDT_LEN] = {HW_CDT_VALUES};
-
-// Discrete Gaussian G(sigma) by inversion of the cumulative table on the top
-// 63 bits of a uniform word: -19 plus the number of thresholds <= u.
-__device__ __forceinline__ int gaussian_from_word(u64 w) {
-    const u64 u = w >> 1;
-    int cnt = 0;
-#pragma unroll
-    for (int t = 0; t < HW_CDT_LEN; t++) cnt += (u >= c_cdt[t]) ? 1 : 0;
-    return cnt - HW_CDT_SUPPORT;
-}
 
 // Encrypted bit slot that drives LUT-index bit t of RAM j: label bits first
 // (slots 0..L-1), then the RAM's tuple bits; -1 for a constant-0 bit.

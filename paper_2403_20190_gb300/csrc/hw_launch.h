@@ -87,6 +87,14 @@ cudaError_t launch_import_rgsw(const LaunchInfo& li, const uint64_t* in, size_t 
                                cudaStream_t st);
 cudaError_t launch_ntt_batch(const LaunchInfo& li, uint64_t* poly, size_t count, int inverse,
                              cudaStream_t st);
+// PackingKeySwitching (k_pack.cu).
+size_t hw_pack_scratch_words_li(const LaunchInfo& li);
+cudaError_t launch_ksk_gen(const LaunchInfo& li, const uint64_t* key, uint64_t seed, uint64_t* ksk,
+                           cudaStream_t st);
+cudaError_t launch_pack(const LaunchInfo& li, const uint64_t* ksk, const uint64_t* resp, size_t n,
+                        uint64_t* packed, uint64_t* scratch, cudaStream_t st);
+cudaError_t hw_pack_kernels_init(const LaunchInfo& li);
+
 // Shared-memory attributes of the context's kernels (its ring size, its
 // external-product geometry and its batched-NTT variant).
 cudaError_t hw_kernels_init(const LaunchInfo& li);

@@ -493,5 +493,6 @@ cudaError_t hw_kernels_init(const LaunchInfo& li) {
 #undef A
     if (e == cudaSuccess) e = li.ext->init();
     if (e == cudaSuccess) e = hw_ntt_kernels_init(li);
+    if (e == cudaSuccess) e = hw_pack_kernels_init(li);
     return e;
 }

@@ -20,6 +20,8 @@ enum HwStreamTag : uint64_t {
     HW_TAG_RGSW_E = 3,  // Gaussian errors e of RGSW rows
     HW_TAG_PERM = 4,    // the bit permutation pi_r
     HW_TAG_H3 = 5,      // H3 hash matrix rows
+    HW_TAG_KSK_A = 7,   // uniform masks of the packing key-switching key
+    HW_TAG_KSK_E = 8,   // Gaussian errors of the packing key-switching key
 };
 
 struct Philox4 {

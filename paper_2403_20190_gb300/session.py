@@ -84,6 +84,26 @@ class Session:
         B.hw_decrypt(self.ctx, key, B.HW_DEC_LWE, obj, count, out, stream)
         return out
 
+    # --------------------------------------------- PackingKeySwitching
+    def ksk_gen(self, key, seed, stream=None):
+        ksk = self.words(B.hw_ksk_words(self.ctx), zero=False)
+        B.hw_ksk_gen(self.ctx, key, seed, ksk, stream)
+        return ksk
+
+    def pack_responses(self, ksk, resp, n, scratch=None, stream=None):
+        """One RLWE per test sample: coefficient c * k0 + j is u[c][j]."""
+        if scratch is None:
+            scratch = self.words(B.hw_pack_scratch_words(self.ctx), zero=False)
+        packed = self.words(int(n) * self.sz["rlwe_words"], zero=False)
+        B.hw_pack_responses(self.ctx, ksk, resp, n, packed, scratch, stream)
+        return packed
+
+    def packed_counts(self, key, packed, n, stream=None):
+        """Decrypted responses (n, l, k0) from packed RLWEs."""
+        l, k0 = self.cfg.n_classes, self.sz["k0"]
+        vals = self.decrypt_rlwe(key, packed, n, stream).view(int(n), self.sz["n"])
+        return vals[:, : l * k0].reshape(int(n), l, k0)
+
     # ------------------------------------------------ dataset balancing
     def new_counts(self):
         """Class-count ciphertext (one RLWE), zero."""
