@@ -663,14 +663,20 @@ def serve_leg(args, local):
     warm = copy.deepcopy(reqs[:4])
     Server(models, arena=arena).run(warm, realtime=False)
     base = copy.deepcopy(reqs)
-    srv = Server(models, n_streams=2, arena=arena)
-    costs = srv.calibrate()  # startup, outside both timed runs
+    srv = Server(models, n_streams=2, arena=arena, packed_infer=True)
+    costs = srv.calibrate()  # startup, outside the timed runs
     batched = srv.run(copy.deepcopy(reqs), realtime=True)
-    alone = Server(models, arena=arena).run_one_at_a_time(base)
+    srv_plain = Server(models, n_streams=2, arena=arena, packed_infer=False)
+    srv_plain.calibrate()
+    batched_plain = srv_plain.run(copy.deepcopy(reqs), realtime=True)
+    alone = Server(models, arena=arena, packed_infer=False).run_one_at_a_time(base)
     out = {"requests": len(reqs), "rate_per_s": 200.0, "hbm_budget_gb": budget / 2**30,
-           "batched": latency_stats(batched), "one_at_a_time": latency_stats(alone),
+           "batched": latency_stats(batched), "batched_without_packing": latency_stats(batched_plain),
+           "one_at_a_time": latency_stats(alone),
            "mix": {nm: sum(1 for r in reqs if r.cfg_name == nm) for nm in cfgs},
-           "policy": "2 streams, shortest expected batch first with aging 1.0, device arena",
+           "policy": "2 streams, shortest expected batch first with aging 1.0, device arena, inference "
+                     "with horizontal packing where the tree layout allows (cfg1, cfg3); the one-at-a-time "
+                     "baseline runs the plain path",
            "calibrated_ms_per_sample": {f"{k[0]}/{k[1]}": round(v * 1e3, 3) for k, v in costs.items()},
            "max_samples_per_request": SERVE_MAX}
     del models, arena

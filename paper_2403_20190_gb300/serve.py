@@ -124,9 +124,12 @@ class _Batch:
 class Server:
     def __init__(self, models: dict, hbm_budget_bytes: int = None, n_streams: int = 2,
                  max_batch_samples: int = 256, keep_responses: bool = False, arena=None,
-                 aging: float = 1.0):
+                 aging: float = 1.0, packed_infer: bool = False):
         """models: name -> ResidentModel.  The arena (or a new one of
-        hbm_budget_bytes on the models' device) holds every batch in flight."""
+        hbm_budget_bytes on the models' device) holds every batch in flight.
+        packed_infer answers inference with horizontal packing
+        (hw_infer_packed: one VP per group of classes sharing a stored
+        ciphertext; other ciphertexts, the same decrypted counters)."""
         self.models = models
         if arena is None:
             dev = next(iter(models.values())).sess.device
@@ -137,6 +140,7 @@ class Server:
         self.max_batch = max_batch_samples
         self.keep_responses = keep_responses
         self.aging = aging
+        self.packed_infer = packed_infer
         self.cost = {}  # (cfg name, kind) -> smoothed GPU seconds per sample
 
     @property
@@ -174,7 +178,8 @@ class Server:
             if kind == "train":
                 B.hw_train_accumulate(s.ctx, rm.delta, buf["rgsw"], n, buf["scratch"], stream)
             else:
-                B.hw_infer(s.ctx, rm.model, buf["rgsw"], n, buf["resp"], buf["sums"], buf["scratch"], stream)
+                infer = B.hw_infer_packed if self.packed_infer else B.hw_infer
+                infer(s.ctx, rm.model, buf["rgsw"], n, buf["resp"], buf["sums"], buf["scratch"], stream)
                 l, k0 = rm.cfg.n_classes, sz["k0"]
                 B.hw_decrypt(s.ctx, rm.key, B.HW_DEC_LWE, buf["resp"], n * l * k0, buf["counts"], stream)
                 B.hw_pdact(s.ctx, buf["counts"], n, buf["scores"], buf["labels_out"], stream)

@@ -53,7 +53,8 @@ def _models(cfgs, pretrain=True):
     return models
 
 
-def test_alone_equals_in_the_mix():
+@pytest.mark.parametrize("packed", [False, True])
+def test_alone_equals_in_the_mix(packed):
     from paper_2403_20190_gb300 import build
     from paper_2403_20190_gb300.merge import add_models
     from paper_2403_20190_gb300.serve import Server, poisson_stream
@@ -64,7 +65,7 @@ def test_alone_equals_in_the_mix():
     reqs = poisson_stream(cfgs, n_requests=18, rate=200.0, seed=9,
                           max_samples={"tiny_rns": 8, "tiny_tree": 8, "cfg1": 16})
     srv = Server(mixed_models, hbm_budget_bytes=8 << 30, n_streams=4, max_batch_samples=64,
-                 keep_responses=True)
+                 keep_responses=True, packed_infer=packed)
     done = srv.run(reqs, realtime=False)
     assert all(r.t_done is not None for r in done)
     batched = sum(1 for r in done if r.kind == "infer")
@@ -79,7 +80,7 @@ def test_alone_equals_in_the_mix():
     for r in done:
         rm = alone_models[r.cfg_name]
         rm.delta.zero_()
-        srv1 = Server(alone_models, n_streams=1, keep_responses=True, arena=arena)
+        srv1 = Server(alone_models, n_streams=1, keep_responses=True, arena=arena, packed_infer=packed)
         import copy
         r1 = copy.copy(r)
         r1.t_done = r1.labels_out = r1.resp = None
