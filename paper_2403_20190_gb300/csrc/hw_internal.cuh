@@ -116,26 +116,27 @@ __device__ __forceinline__ u64 redc_lazy(u64 hi, u64 lo, u64 q, u64 qneg) {
 
 // ---------------------------------------------------------------------------
 // Block-level negacyclic NTT, specialised on the ring size N = 2^LOGN
-// (6 <= LOGN <= 13).  A block of T = N/16 threads holds 16 residues per
-// thread in registers; a round applies up to four consecutive butterfly
-// stages to groups of 2^R residues in registers, and rounds exchange data
-// through one of two padded shared-memory buffers (address p + p/16 keeps
-// every exchange at two wavefronts per warp).
+// (6 <= LOGN <= 13) and the residues per thread E = 2^LOGE (4, 8 or 16).
+// A block of T = N/E threads holds E residues per thread and polynomial in
+// registers; a round applies up to LOGE consecutive butterfly stages to
+// groups of 2^R residues in registers, and rounds exchange data through one
+// of two padded shared-memory buffers (address p + p/E keeps every
+// exchange at two wavefronts per warp).
 //
 // Forward (Cooley-Tukey, psi powers merged, natural order in, bit-reversed
-// out): the partial round of LOGN mod 4 stages comes first, then radix-16
+// out): the partial round of LOGN mod LOGE stages comes first, then full
 // rounds.  Butterflies are lazy (no reduction): X' = X + t, Y' = X + 2q - t
 // with t = Shoup(Y*W) in [0, 2q), so values grow by < 2q per stage and stay
 // below (2*LOGN + 1) q < 2^60.
 // Inverse (Gentleman-Sande, bit-reversed in, natural out, inputs < 2q):
-// radix-16 rounds first, the partial round last; the sum is kept below 2q
-// by one conditional subtraction, the difference goes through a lazy Shoup
+// full rounds first, the partial round last; the sum is kept below 2q by
+// one conditional subtraction, the difference goes through a lazy Shoup
 // product.  Scaling by N^-1 is applied by the caller to the inputs.
 //
-// Register convention: in a round of R stages, v[gg + e*G] (G = 16 / 2^R) is
+// Register convention: in a round of R stages, v[gg + e*G] (G = E / 2^R) is
 // element e of the thread's group gg.  The first forward round reads and the
 // last inverse round writes positions tid + k*T (v[k]); the last forward
-// round leaves, and the first inverse round takes, positions 16*tid + e.
+// round leaves, and the first inverse round takes, positions E*tid + e.
 // ---------------------------------------------------------------------------
 // Default external-product geometry: 2^3 residues per thread, two
 // polynomials per transform below N = 8192 and one at N = 8192 (1024-thread
