@@ -59,6 +59,7 @@ def lib():
             "or_rlwe_rotate": (None, [vp, u64p, ctypes.c_longlong, u64p]),
             "or_rlwe_add": (None, [vp, u64p, u64p]),
             "or_rlwe_sub": (None, [vp, u64p, u64p]),
+            "or_rlwe_mul_plain": (None, [vp, u64p, ctypes.POINTER(ctypes.c_longlong), u64p]),
             "or_keygen": (None, [vp, u64, i8p]),
             "or_gaussian": (ctypes.c_longlong, [vp, u64]),
             "or_encrypt_rgsw": (None, [vp, i8p, u64, u64, ctypes.c_int, ctypes.c_int, u64p]),

@@ -294,6 +294,88 @@ class Oracle:
                     lib().or_lwe_add(self.ctx, _p64(sums[i, c]), _p64(np.ascontiguousarray(resp[i, c, jj])))
         return resp, sums
 
+    # ------------------------------------- unencrypted-model inference
+    def plain_split(self):
+        """Address bits of a clear-model lookup: the low zt = max(0, z - L)
+        bits drive a CMUX tree (the table of one class does not fit one
+        polynomial), the other a - zt <= log2 N bits the blind rotation."""
+        P = self.P
+        return max(0, P.z - P.L)
+
+    def plain_tables(self, W, j, c):
+        """The clear LUT of RAM j, class c as 2^zt plaintext polynomials:
+        coefficient k of table v is the counter of address v + 2^zt k."""
+        P = self.P
+        zt = self.plain_split()
+        row = np.asarray(W[c, j], dtype=np.int64)
+        out = []
+        for v in range(1 << zt):
+            t = np.zeros(P.n, dtype=np.int64)
+            part = row[v::1 << zt]
+            t[: part.size] = part
+            out.append(t)
+        return out
+
+    def vp_plain_item(self, W, rgsw_by_slot, j) -> dict:
+        """VP of RAM j against a model in clear (Section 3.6.2 notes that
+        inference is faster when the model is not encrypted).  The lookup
+        tables are plaintexts, so the blind rotation depends only on the
+        sample: R = BlindRotate((0, Delta), address bits zt..a-1) with weights
+        +2^0, +2^1, ... (X^-2^t) runs once, and class c's response is
+        ExtractLWE of the CMUX tree (address bits 0..zt-1, Algorithm 3's
+        tree) over the products R * T_v -- coefficient 0 of
+        Delta X^-addr T_v(X) is Delta T_v[addr].  Returns {c: LWE}."""
+        P = self.P
+        zt = self.plain_split()
+        nb = P.a - zt
+        ptrs = (u64p * max(nb, 1))()
+        clear = (ctypes.c_int * max(nb, 1))()
+        for i in range(nb):
+            d = int(self.ram_bits[j][zt + i])
+            ptrs[i] = _p64(rgsw_by_slot[P.L + d]) if d >= 0 else ctypes.cast(None, u64p)
+        acc = self.trivial_one()
+        lib().or_blind_rotate(self.ctx, _p64(acc), ptrs, clear, nb, +1)
+        tptrs = (u64p * max(zt, 1))()
+        tclear = (ctypes.c_int * max(zt, 1))()
+        for i in range(zt):
+            d = int(self.ram_bits[j][i])
+            tptrs[i] = _p64(rgsw_by_slot[P.L + d]) if d >= 0 else ctypes.cast(None, u64p)
+        out = {}
+        for c in range(self.cfg.n_classes):
+            prods = []
+            Lin = (u64p * (1 << zt))()
+            for v, t in enumerate(self.plain_tables(W, j, c)):
+                pr = np.zeros(self.rlwe_words, dtype=np.uint64)
+                lib().or_rlwe_mul_plain(self.ctx, _p64(acc),
+                                        t.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)), _p64(pr))
+                prods.append(pr)
+                Lin[v] = _p64(pr)
+            lwe = np.zeros(P.r * (P.n + 1), dtype=np.uint64)
+            lib().or_vp(self.ctx, Lin, tptrs, tclear, zt, zt, _p64(lwe))
+            out[c] = lwe
+        return out
+
+    def infer_plain(self, W, s, seed, data_bits, rams=None, sample_offset=0, trivial=False):
+        """Inference against the clear counters W[c][j][addr] (Algorithm 4's
+        model): responses u[i][c][j] and per-class sums, laid out as infer()."""
+        P = self.P
+        l = self.cfg.n_classes
+        rams = list(range(P.k0)) if rams is None else list(rams)
+        slots = self.slots_for_rams(rams, with_labels=False)
+        n = data_bits.shape[0]
+        lw = P.r * (P.n + 1)
+        resp = np.zeros((n, l, len(rams), lw), dtype=np.uint64)
+        sums = np.zeros((n, l, lw), dtype=np.uint64)
+        for i in range(n):
+            rg = self.encrypt_slots(s, seed, sample_offset + i, data_bits[i], 0, slots, trivial)
+            for jj, j in enumerate(rams):
+                for c, lwe in self.vp_plain_item(W, rg, j).items():
+                    resp[i, c, jj] = lwe
+            for c in range(l):
+                for jj in range(len(rams)):
+                    lib().or_lwe_add(self.ctx, _p64(sums[i, c]), _p64(np.ascontiguousarray(resp[i, c, jj])))
+        return resp, sums
+
     def infer(self, H, s, seed, data_bits, rams=None, sample_offset=0, trivial=False):
         """Algorithm 7 (PD-act): responses u[i][c][j] as LWE ciphertexts and
         the per-class sums over the listed RAMs."""

@@ -286,6 +286,23 @@ void or_rlwe_add(const or_ctx *c, u64 *acc, const u64 *x) {
         }
 }
 
+/* ct * T for a plaintext polynomial T with integer coefficients (reduced
+ * into each prime): both components multiplied by T in R_q, so the phase is
+ * multiplied by T exactly -- (b T) - (a T) s = (b - a s) T.  Used by the
+ * unencrypted-model inference, whose lookup tables are plaintexts. */
+void or_rlwe_mul_plain(const or_ctx *c, const u64 *ct, const long long *t, u64 *out) {
+    int n = c->n;
+    u64 *tq = (u64 *)malloc(sizeof(u64) * n);
+    for (int j = 0; j < c->r; j++) {
+        for (int i = 0; i < n; i++) tq[i] = from_signed(t[i], c->q[j]);
+        for (int comp = 0; comp < 2; comp++) {
+            size_t off = ((size_t)comp * c->r + j) * n;
+            or_poly_mul(ct + off, tq, out + off, c->log_n, c->q[j], c->psi[j]);
+        }
+    }
+    free(tq);
+}
+
 void or_rlwe_sub(const or_ctx *c, u64 *acc, const u64 *x) {
     for (int comp = 0; comp < 2; comp++)
         for (int j = 0; j < c->r; j++) {
