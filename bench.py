@@ -59,12 +59,19 @@ def parse():
 
 # DRAM bytes of k_vp_infer per test sample, from the ncu capture summarised
 # in profiles/k_vp_infer_cfg2.md (2 test samples, scaled by samples: the
-# traffic is per item); valid only for the kernel sources it was taken on.
+# traffic is per item); valid only for the kernel sources it was taken on:
+# the VP kernel with the device helpers it calls (the region of hw_ext.cuh
+# from bit_slot to the VP kernel's end) and the headers of the external
+# product and the modular arithmetic.
 PROFILED_VP_TRAFFIC = {
-    "config": "cfg2", "ext_loge": 3, "ext_np": 2, "ext_smem": 1, "bytes_per_test_sample": 2.1465e9,
-    "sources": ("paper_2403_20190_gb300/csrc/hw_ext.cuh", "paper_2403_20190_gb300/csrc/hw_internal.cuh",
-                "paper_2403_20190_gb300/csrc/modarith.cuh"),
-    "sha256": "35031caf9835481718cf615fbb75c3adf6fc38fd79943a67254eaeda733effe8",
+    "config": "cfg2", "ext_loge": 3, "ext_np": 2, "ext_smem": 1, "bytes_per_test_sample": 2.1424e9,
+    "sources": (("paper_2403_20190_gb300/csrc/hw_ext.cuh", "// Encrypted bit slot that drives",
+                 "// EncRGSW."),
+                ("paper_2403_20190_gb300/csrc/hw_ext.cuh", "// ExtractLWE(ct, k) written by the block",
+                 "// Dataset balancing (Section 3.6.1)"),
+                ("paper_2403_20190_gb300/csrc/hw_internal.cuh", None, None),
+                ("paper_2403_20190_gb300/csrc/modarith.cuh", None, None)),
+    "sha256": "73315347666d96d45f17e4eb1ceaeb3b4353e41f6c41667c14d6edecfd72cba8",
 }
 # Register-only 64-bit lazy Cooley-Tukey butterflies per second on one GB300
 # at 2070 MHz (profiles/butterfly_ceiling.md): what the integer pipes issue
@@ -73,16 +80,25 @@ BUTTERFLY_CEILING = {"ct64_t_per_s": 0.8414, "gs64_t_per_s": 0.8755,
                      "source": "microbench/bfly_ceiling.cu"}
 
 
-def profiled_traffic(config, geometry, n_test):
+def profiled_sources_sha(root=None):
+    """sha256 over the profiled source regions (whole file where no markers)."""
     import hashlib
+    h = hashlib.sha256()
+    for f, start, end in PROFILED_VP_TRAFFIC["sources"]:
+        with open(os.path.join(root or ROOT, f), encoding="utf-8") as fh:
+            text = fh.read()
+        if start is not None:
+            i = text.index(start)
+            text = text[i:text.index(end, i)]
+        h.update(text.encode("utf-8"))
+    return h.hexdigest()
+
+
+def profiled_traffic(config, geometry, n_test):
     t = PROFILED_VP_TRAFFIC
     if config != t["config"] or any(geometry.get(k) != t[k] for k in ("ext_loge", "ext_np", "ext_smem")):
         return None
-    h = hashlib.sha256()
-    for f in t["sources"]:
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(fh.read())
-    if h.hexdigest() != t["sha256"]:
+    if profiled_sources_sha() != t["sha256"]:
         return None  # the kernel changed since the counters were taken
     return t["bytes_per_test_sample"] * n_test
 
