@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--no-balance", action="store_true")
     ap.add_argument("--no-packing", action="store_true")
     ap.add_argument("--no-keyswitch", action="store_true")
+    ap.add_argument("--no-clear-model", action="store_true",
+                    help="skip the leg that answers the test batch against the model in clear")
     ap.add_argument("--serve-requests", type=int, default=40)
     ap.add_argument("--geometry", default="auto", choices=["auto", "default"],
                     help="kernel geometry: autotuned (cached per GPU and parameters) or the library default")
@@ -263,7 +265,7 @@ def algorithmic_counts(sess, cfg):
     bfly = (n // 2) * logn
     per_ext = 2 * dnum * r * bfly + 2 * r * bfly + 2 * 2 * dnum * r * n
     slots = B.hw_get_ram_slots(sess.ctx)
-    ext_train = ext_infer = 0
+    ext_train = ext_infer = ext_clear = 0
     gates = {1: 0}
     for j in range(k0):
         enc = [slots[j * a + i] >= 0 for i in range(a)]
@@ -274,6 +276,11 @@ def algorithmic_counts(sess, cfg):
         rot_i = sum(1 for t in range(max(z, L), L + a) if enc[t - L])
         tree_i = 1 if (z > L and enc[z - 1 - L]) else 0
         ext_infer += l * (rot_i + tree_i)
+        # inference against a model in clear: one rotation over address bits
+        # zt..a-1 shared by the classes, plus the CMUX of address bit 0 per
+        # class when zt = 1
+        zt = max(0, z - L)
+        ext_clear += sum(1 for i in range(zt, a) if enc[i]) + (l if zt and enc[0] else 0)
     _ = gates
     # pruned CDEMUX gates per RAM (same for every RAM when their tree bits are encrypted)
     V = set()
@@ -284,7 +291,7 @@ def algorithmic_counts(sess, cfg):
             if any(v % (1 << (i + 1)) == jj + (1 << i) for v in V))
     ext_train += k0 * g
     return {"per_ext_modmul": per_ext, "ext_train_per_sample": ext_train,
-            "ext_infer_per_sample": ext_infer,
+            "ext_infer_per_sample": ext_infer, "ext_clear_per_sample": ext_clear,
             "rgsw_bytes": sz["rgsw_words"] * 8}
 
 
@@ -472,6 +479,41 @@ def gpu_arm(args, ws, rank, local, pg):
                      "share_of_infer": min(t_pack) / ph["infer"]}
         del ksk, pscr
 
+    # inference against the model in clear (Section 3.6.2): the owner's
+    # decrypted counters as plaintext tables, one blind rotation per (sample,
+    # RAM) shared by the l classes; the same encrypted test batch as the
+    # phase breakdown's, whose decrypted counters it must reproduce
+    clear_model = None
+    if not args.no_clear_model:
+        alg_c = algorithmic_counts(sess, cfg)
+        W = sess.decrypt_model_counts(key, model, stream=stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plain = sess.plain_model(W, stream=stream)
+        e1.record(stream)
+        pbufs = sess.infer_buffers(bsz)
+        sess.infer_plain(plain, st.rgsw_test, bsz, bufs=pbufs, stream=stream)  # warm-up
+        torch.cuda.synchronize()
+        t_load = e0.elapsed_time(e1)
+        t_plain = []
+        for _ in range(3):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            sess.infer_plain(plain, st.rgsw_test, bsz, bufs=pbufs, stream=stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            t_plain.append(a.elapsed_time(b))
+        pc = sess.responses_counts(key, pbufs[0], bsz, stream=stream)
+        same = (pc.reshape(-1) == st.counts[: pc.numel()]).float().mean().item()
+        clear_model = {"inferences_per_s": bsz / (min(t_plain) / 1000.0),
+                       "ms_per_batch": min(t_plain), "encrypted_model_ms_per_batch": ph["infer"],
+                       "speedup_vs_encrypted_model": ph["infer"] / min(t_plain),
+                       "load_ms": t_load, "plain_bytes": B.hw_plain_model_words(sess.ctx) * 8,
+                       "ext_products_per_sample": {"clear": alg_c["ext_clear_per_sample"],
+                                                   "encrypted": alg_c["ext_infer_per_sample"]},
+                       "responses_equal_to_encrypted_path": same}
+        del plain, pbufs, W
+
     # e2e through the C ABI with pinned host buffers, copies inside the timed region
     e2e = None
     if not args.no_e2e:
@@ -638,6 +680,7 @@ def gpu_arm(args, ws, rank, local, pg):
             "balancing": balancing,
             "horizontal_packing": packing,
             "packing_keyswitch": keyswitch,
+            "clear_model": clear_model,
             "roofline": roofline,
             "ntt": ntt,
             "geometry": sess.geometry,

@@ -218,6 +218,30 @@ int hw_infer_packed(hw_ctx* ctx, const uint64_t* model_dev, const uint64_t* rgsw
                     uint64_t* resp_dev, uint64_t* sums_dev, uint64_t* scratch_dev, size_t scratch_words,
                     void* stream);
 
+/* Inference against a model in clear (Section 3.6.2 remarks that inference
+ * is faster when the model is not encrypted; the algorithm is this
+ * library's reading).  The lookup tables of RAM j, class c are plaintext
+ * polynomials T_{j,c,v}, v < 2^zt with zt = max(0, z - L): coefficient k of
+ * T_{j,c,v} is the counter of address v + 2^zt k.  The blind rotation then
+ * depends on the sample only: R = (0, Delta) rotated by address bits
+ * zt..a-1 with weights X^-(2^0), X^-(2^1), ... runs once per (sample, RAM),
+ * and class c's response is ExtractLWE(R * T_{j,c,0}, 0) (zt = 0) or
+ * ExtractLWE(CMUX(C_{bit 0}, R * T_{j,c,1}, R * T_{j,c,0}), 0) (zt = 1):
+ * coefficient 0 of Delta X^-addr T(X) is Delta T[addr].  The noise of R is
+ * multiplied by the table's coefficient sum (the number of training samples
+ * of the class for a trained model).
+ * hw_plain_model_load: counts_dev [l][k0][2^a] int64 (Algorithm 4's W, as
+ * hw_decrypt gives a model back), reduced mod q_i -> plain_dev, the
+ * hw_plain_model_words(ctx) words of tables in the internal evaluation form
+ * (valid for contexts of the same geometry).
+ * hw_infer_plain: responses and sums laid out as hw_infer's (they decrypt to
+ * the same counters; the ciphertexts differ); scratch as hw_infer. */
+size_t hw_plain_model_words(const hw_ctx* ctx);
+int hw_plain_model_load(hw_ctx* ctx, const int64_t* counts_dev, uint64_t* plain_dev, void* stream);
+int hw_infer_plain(hw_ctx* ctx, const uint64_t* plain_dev, const uint64_t* rgsw_dev, size_t n,
+                   uint64_t* resp_dev, uint64_t* sums_dev, uint64_t* scratch_dev, size_t scratch_words,
+                   void* stream);
+
 /* DecRLWE / DecLWE (Section 2.4): phase b - a*s combined over the primes by
  * the CRT and rounded, m = floor((p*phi + floor(Q/2)) / Q) mod p.  what =
  * HW_DEC_RLWE: obj_dev holds count RLWEs, out_dev gets count*N values;

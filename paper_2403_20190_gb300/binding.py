@@ -81,6 +81,9 @@ _SIGS = {
     "hw_export_rgsw": (ctypes.c_int, [_VP, _VP, _SZ, _VP, _VP]),
     "hw_import_rgsw": (ctypes.c_int, [_VP, _VP, _SZ, _VP, _VP]),
     "hw_count_scratch_words": (_SZ, [_VP, _SZ]),
+    "hw_plain_model_words": (_SZ, [_VP]),
+    "hw_plain_model_load": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "hw_infer_plain": (ctypes.c_int, [_VP, _VP, _VP, _SZ, _VP, _VP, _VP, _SZ, _VP]),
     "hw_ksk_words": (_SZ, [_VP]),
     "hw_ksk_gen": (ctypes.c_int, [_VP, _VP, _U64, _VP, _VP]),
     "hw_pack_scratch_words": (_SZ, [_VP]),
@@ -278,6 +281,20 @@ def hw_infer(ctx, model, rgsw, n, resp, sums, scratch, stream=None):
 def hw_infer_packed(ctx, model, rgsw, n, resp, sums, scratch, stream=None):
     _check(load().hw_infer_packed(ctx.handle, _ptr(model), _ptr(rgsw), n, _ptr(resp), _ptr(sums),
                                   _ptr(scratch), scratch.numel(), _stream(stream)), "hw_infer_packed")
+
+
+def hw_plain_model_words(ctx) -> int:
+    return int(load().hw_plain_model_words(ctx.handle))
+
+
+def hw_plain_model_load(ctx, counts, plain, stream=None):
+    _check(load().hw_plain_model_load(ctx.handle, _ptr(counts), _ptr(plain), _stream(stream)),
+           "hw_plain_model_load")
+
+
+def hw_infer_plain(ctx, plain, rgsw, n, resp, sums, scratch, stream=None):
+    _check(load().hw_infer_plain(ctx.handle, _ptr(plain), _ptr(rgsw), n, _ptr(resp), _ptr(sums),
+                                 _ptr(scratch), scratch.numel(), _stream(stream)), "hw_infer_plain")
 
 
 def hw_infer_static_scratch(ctx, model, rgsw, n, resp, sums, stream=None):

@@ -743,6 +743,30 @@ extern "C" int hw_infer_packed(hw_ctx* c, const uint64_t* model, const uint64_t*
     return HW_OK;
 }
 
+extern "C" size_t hw_plain_model_words(const hw_ctx* c) { return c ? hw_plain_words_li(c->li) : 0; }
+
+extern "C" int hw_plain_model_load(hw_ctx* c, const int64_t* counts, uint64_t* plain, void* stream) {
+    CHECK_CTX(c);
+    if (!counts || !plain) return fail(HW_EINVAL, "hw_plain_model_load: null buffer");
+    CUDA_TRY(launch_plain_load(c->li, counts, plain, (cudaStream_t)stream));
+    return HW_OK;
+}
+
+extern "C" int hw_infer_plain(hw_ctx* c, const uint64_t* plain, const uint64_t* rgsw, size_t n, uint64_t* resp,
+                              uint64_t* sums, uint64_t* scratch, size_t scratch_words, void* stream) {
+    CHECK_CTX(c);
+    if (n == 0) return HW_OK;
+    if (!plain || !rgsw || !resp || !sums || !scratch) return fail(HW_EINVAL, "hw_infer_plain: null buffer");
+    size_t need = hw_infer_scratch_words(c, n);
+    if (scratch_words < need)
+        return fail(HW_ENOMEM, "hw_infer_plain: scratch has %zu words, needs %zu", scratch_words, need);
+    if (n * (size_t)c->sz.k0 > 0x7fffffff) return fail(HW_EINVAL, "hw_infer_plain: batch too large");
+    cudaStream_t st = (cudaStream_t)stream;
+    CUDA_TRY(launch_vp_plain(c->li, plain, rgsw, n, resp, scratch, c->li.ext_grid, st));
+    CUDA_TRY(launch_class_sums(c->li, resp, n, sums, st));
+    return HW_OK;
+}
+
 extern "C" int hw_decrypt(hw_ctx* c, const uint64_t* key, int what, const uint64_t* obj,
                           size_t count, int64_t* out, void* stream) {
     CHECK_CTX(c);

@@ -388,6 +388,211 @@ __global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP, SM>::T, ExtCfg<LOGN, LO
     }
 }
 
+// Evaluation form of an RLWE (2 r polynomials, fully reduced, thread-major
+// positions) written by the block.
+template <int LOGN, int LOGE, int NP>
+__device__ __forceinline__ void rlwe_to_eval(const DevCtx& C, const u64* src, u64* dstn, Xchg& xc) {
+    constexpr int N = Ring<LOGN, LOGE>::N, T = Ring<LOGN, LOGE>::T, E = 1 << LOGE;
+    constexpr int NPI = NP < 2 ? NP : 2;  // the two components together
+    const int tid = threadIdx.x, r = C.r;
+    for (int jp = 0; jp < r; jp++) {
+        const PrimeConst P = C.P[jp];
+        for (int oc0 = 0; oc0 < 2; oc0 += NPI) {
+            u64 v[NPI][E];
+#pragma unroll
+            for (int pp = 0; pp < NPI; pp++)
+#pragma unroll
+                for (int kk = 0; kk < E; kk++) v[pp][kk] = src[((size_t)(oc0 + pp) * r + jp) * N + tid + kk * T];
+            ntt_fwd<LOGN, LOGE, NPI>(v, xc, C, jp);
+#pragma unroll
+            for (int pp = 0; pp < NPI; pp++)
+#pragma unroll
+                for (int e = 0; e < E; e++)
+                    dstn[((size_t)(oc0 + pp) * r + jp) * N + e * T + tid] = reduce_full(v[pp][e], P);
+        }
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Inference against a model in clear (Section 3.6.2).  One block per item
+// (sample i, RAM j), persistent over items.  The lookup tables are
+// plaintexts, so the blind rotation depends only on the sample:
+// R = (0, Delta) rotated by address bits zt..a-1 (zt = max(0, z - L)) with
+// weights +2^0, +2^1, ... (X^-2^k), in evaluation form afterwards.  For every
+// class c the products R * T_{j,c,v} with its tables (plain: [RAM][class]
+// [leaf v < 2^zt][prime][N], evaluation form, Montgomery) give its response:
+// zt = 0: ExtractLWE(R * T, 0) -- the a part transformed back, b' = coefficient
+// 0 of R_b * T, N^-1 times the sum of its evaluation values;
+// zt = 1: ExtractLWE(CMUX(C, R T_1, R T_0), 0) with address bit 0 in control.
+// Responses are stored [sample][class][RAM] as VP's.  Per-block scratch as for
+// VP: two RLWEs (the rotation, then the two tree inputs) and, outside mode 1,
+// the evaluation form of R.
+// ---------------------------------------------------------------------------
+template <int LOGN, int LOGE, int NP, int SM>
+__global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP, SM>::T, ExtCfg<LOGN, LOGE, NP, SM>::MINB)
+    k_vp_plain(const DevCtx* __restrict__ Cp, const u64* __restrict__ plain,
+               const u64* __restrict__ rgsw, int n_items, u64* __restrict__ resp,
+               u64* __restrict__ scratch) {
+    using X = ExtCfg<LOGN, LOGE, NP, SM>;
+    constexpr int N = Ring<LOGN>::N, E = 1 << LOGE, T = X::T;
+    constexpr int NPI = NP < 2 ? NP : 2;
+    extern __shared__ u64 smem[];
+    Xchg xc{smem, SM ? smem : smem + NP * X::PADDED, X::PADDED, 0};
+    if (SM == 2) xc.accs = smem + NP * X::PADDED;
+    const DevCtx& C = *Cp;
+    const int tid = threadIdx.x, r = C.r, l = C.n_classes;
+    const size_t rl = C.rlwe_words;
+    u64* blk = scratch + (size_t)blockIdx.x * (SM == 1 ? 2 : 3) * rl;
+    u64* acc[2] = {blk, blk + rl};
+    u64* accn = SM == 1 ? smem + NP * X::PADDED : blk + 2 * rl;
+    const int zt = C.z > C.L ? C.z - C.L : 0;
+    const int nleaf = 1 << zt;
+    const int kbits = C.L + C.a;
+    const int t0 = C.L + zt;  // LUT-index bit of the first rotation bit
+    u64* red = xc.b0;         // block reduction of the b' sums (between transforms)
+    constexpr int NR = T >= 32 ? T / 32 : T;  // partial sums per class and prime
+    for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+        const int i = item / C.k0, j = item % C.k0;
+        const u64* sample = rgsw + (size_t)i * C.sample_words;
+        for (size_t w = tid; w < rl; w += T) {
+            const size_t comp = w / ((size_t)r * N), rem = w % ((size_t)r * N);
+            const int p = (int)(rem / N), x = (int)(rem % N);
+            acc[0][w] = (comp == 1 && x == 0) ? C.delta[p] : 0;
+            accn[w] = comp == 1 ? C.delta[p] : 0;
+        }
+        __syncthreads();
+        int cur = 0;
+        bool rotated = false;
+        for (int t = t0; t < kbits; t++) {
+            const int slot = bit_slot(C, j, t);
+            if (slot < 0) continue;  // constant-0 address bit: no rotation
+            const int k = t - t0;
+            int nslot = -1;
+            for (int t2 = t + 1; t2 < kbits && nslot < 0; t2++) nslot = bit_slot(C, j, t2);
+            if (nslot < 0 && zt > 0) nslot = bit_slot(C, j, C.L);
+            ext_product<LOGN, LOGE, NP, SM == 2>(
+                C, sample + (size_t)slot * C.rgsw_words, acc[cur], 2 * N - (1 << k), acc[cur], 0, EXT_ADD,
+                acc[cur ^ 1], xc,
+                ExtNtt{accn, accn, k, 1, nslot >= 0 ? sample + (size_t)nslot * C.rgsw_words : nullptr, 1});
+            cur ^= 1;
+            rotated = true;
+        }
+        // with one digit per prime the products kept accn up to date
+        if (rotated && !C.diag) rlwe_to_eval<LOGN, LOGE, NP>(C, acc[cur], accn, xc);
+        const u64* Tj = plain + (size_t)j * l * nleaf * r * N;
+        if (zt == 0) {
+            for (int c0 = 0; c0 < l; c0 += NP) {
+                // b' = N^-1 sum_k (R_b * T)^_k, per class and prime: per-thread
+                // partial sums, reduced over each warp, then over the warps
+                __syncthreads();  // the exchange buffer (red) is free
+#pragma unroll
+                for (int pp = 0; pp < NP; pp++)
+                    for (int jp = 0; jp < r; jp++) {
+                        const PrimeConst P = C.P[jp];
+                        const int c = c0 + pp < l ? c0 + pp : l - 1;
+                        const u64* rb = accn + (size_t)(r + jp) * N + tid;
+                        const u64* tm = Tj + ((size_t)c * r + jp) * N + tid;
+                        u64 sacc = 0;
+#pragma unroll
+                        for (int e = 0; e < E; e++) sacc = add_mod(sacc, mont_mul(rb[e * T], tm[e * T], P), P.q);
+                        if constexpr (T >= 32) {
+#pragma unroll
+                            for (int off = 16; off > 0; off >>= 1)
+                                sacc = add_mod(sacc, __shfl_down_sync(0xffffffffu, sacc, off), P.q);
+                            if ((tid & 31) == 0) red[(pp * HW_MAXP + jp) * NR + (tid >> 5)] = sacc;
+                        } else {
+                            red[(pp * HW_MAXP + jp) * NR + tid] = sacc;
+                        }
+                    }
+                __syncthreads();
+                for (int idx = tid; idx < NP * r; idx += T) {
+                    const int pp = idx / r, jp = idx % r, c = c0 + pp;
+                    if (c < l) {
+                        const PrimeConst P = C.P[jp];
+                        u64 sacc = 0;
+                        for (int w = 0; w < NR; w++) sacc = add_mod(sacc, red[(pp * HW_MAXP + jp) * NR + w], P.q);
+                        u64* lw = resp + (((size_t)i * l + c) * C.k0 + j) * C.lwe_words + (size_t)jp * (N + 1);
+                        lw[N] = shoup_mul(sacc, C.n_inv[jp], C.n_inv_s[jp], P.q);
+                    }
+                }
+                __syncthreads();  // red is read before the transforms reuse the buffer
+                // a': the a parts of NP classes transformed back together
+                for (int jp = 0; jp < r; jp++) {
+                    const PrimeConst P = C.P[jp];
+                    const u64 q = P.q, ninv = C.n_inv[jp], ninv_s = C.n_inv_s[jp];
+                    const u64* ra = accn + (size_t)jp * N + tid;
+                    u64 v[NP][E];
+#pragma unroll
+                    for (int pp = 0; pp < NP; pp++) {
+                        const int c = c0 + pp < l ? c0 + pp : l - 1;
+                        const u64* tm = Tj + ((size_t)c * r + jp) * N + tid;
+#pragma unroll
+                        for (int e = 0; e < E; e++)
+                            v[pp][e] = shoup_mul_lazy(mont_mul(ra[e * T], tm[e * T], P), ninv, ninv_s, q);
+                    }
+                    ntt_inv<LOGN, LOGE, NP>(v, xc, C, jp);
+#pragma unroll
+                    for (int pp = 0; pp < NP; pp++) {
+                        const int c = c0 + pp;
+                        if (c >= l) continue;
+                        u64* lw = resp + (((size_t)i * l + c) * C.k0 + j) * C.lwe_words + (size_t)jp * (N + 1);
+#pragma unroll
+                        for (int kk = 0; kk < E; kk++) {
+                            const int x = tid + kk * T;
+                            const u64 val = v[pp][kk] >= q ? v[pp][kk] - q : v[pp][kk];
+                            if (x == 0)
+                                lw[0] = val;
+                            else
+                                lw[N - x] = neg_mod(val, q);
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        } else {
+            const int tslot = bit_slot(C, j, C.L);  // address bit 0 drives the tree
+            for (int c = 0; c < l; c++) {
+                u64* lwe = resp + (((size_t)i * l + c) * C.k0 + j) * C.lwe_words;
+                // the two leaves R * T_0 -> acc[0], R * T_1 -> acc[1], coefficient form
+                for (int v = 0; v < 2; v++)
+                    for (int jp = 0; jp < r; jp++) {
+                        const PrimeConst P = C.P[jp];
+                        const u64 q = P.q, ninv = C.n_inv[jp], ninv_s = C.n_inv_s[jp];
+                        const u64* tm = Tj + (((size_t)c * nleaf + v) * r + jp) * N + tid;
+                        for (int oc0 = 0; oc0 < 2; oc0 += NPI) {
+                            u64 w[NPI][E];
+#pragma unroll
+                            for (int pp = 0; pp < NPI; pp++) {
+                                const u64* rc = accn + ((size_t)(oc0 + pp) * r + jp) * N + tid;
+#pragma unroll
+                                for (int e = 0; e < E; e++)
+                                    w[pp][e] = shoup_mul_lazy(mont_mul(rc[e * T], tm[e * T], P), ninv, ninv_s, q);
+                            }
+                            ntt_inv<LOGN, LOGE, NPI>(w, xc, C, jp);
+#pragma unroll
+                            for (int pp = 0; pp < NPI; pp++) {
+                                u64* dd = acc[v] + ((size_t)(oc0 + pp) * r + jp) * N;
+#pragma unroll
+                                for (int kk = 0; kk < E; kk++)
+                                    dd[tid + kk * T] = w[pp][kk] >= q ? w[pp][kk] - q : w[pp][kk];
+                            }
+                        }
+                    }
+                __syncthreads();
+                if (tslot < 0) {  // constant-0 control: the CMUX keeps leaf 0
+                    extract_lwe_at(C, acc[0], 0, lwe);
+                    __syncthreads();
+                } else {
+                    ext_product<LOGN, LOGE, NP, SM == 2>(C, sample + (size_t)tslot * C.rgsw_words, acc[1], 0,
+                                                      acc[0], 0, EXT_LWE, lwe, xc,
+                                                      ExtNtt{nullptr, nullptr, -1, 0, nullptr, 0});
+                }
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Launch table of one geometry
 // ---------------------------------------------------------------------------
@@ -413,6 +618,9 @@ struct ExtVariant {
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k_count_classes<LOGN, LOGE, NP, SM>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_vp_plain<LOGN, LOGE, NP, SM>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         return e;
     }
@@ -475,6 +683,12 @@ struct ExtVariant {
         return cudaLaunchKernelEx(&L.cfg, k_vp_infer<LOGN, LOGE, NP, SM, 0>, li.dctx, (const u64*)model,
                                   (const u64*)rgsw, items, (u64*)resp, (u64*)acc);
     }
+    static cudaError_t vp_plain(const LaunchInfo& li, const uint64_t* plain, const uint64_t* rgsw, int items,
+                                uint64_t* resp, uint64_t* acc, int grid, cudaStream_t st) {
+        Launch L(li, grid, st, acc, (size_t)grid * SCRATCH_RLWE * li.rlwe_words * sizeof(u64));
+        return cudaLaunchKernelEx(&L.cfg, k_vp_plain<LOGN, LOGE, NP, SM>, li.dctx, (const u64*)plain,
+                                  (const u64*)rgsw, items, (u64*)resp, (u64*)acc);
+    }
     static cudaError_t count(const LaunchInfo& li, const uint64_t* rgsw, int items, uint64_t* out,
                              uint64_t* acc, int grid, cudaStream_t st) {
         Launch L(li, grid, st, acc, 0);
@@ -483,7 +697,7 @@ struct ExtVariant {
     }
     static ExtOps ops() {
         return ExtOps{LOGE, NP, SM, SCRATCH_RLWE, X::T, X::FIXED_BYTES, ENC_SMEM, &init, &occupancy,
-                      &encrypt, &ivp, &vp, &count};
+                      &encrypt, &ivp, &vp, &count, &vp_plain};
     }
 };
 

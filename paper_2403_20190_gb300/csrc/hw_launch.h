@@ -28,6 +28,8 @@ struct ExtOps {
                       uint64_t* resp, uint64_t* acc, int grid, int packed, cudaStream_t);
     cudaError_t (*count)(const LaunchInfo&, const uint64_t* rgsw, int items, uint64_t* out,
                          uint64_t* acc, int grid, cudaStream_t);
+    cudaError_t (*vp_plain)(const LaunchInfo&, const uint64_t* plain, const uint64_t* rgsw, int items,
+                            uint64_t* resp, uint64_t* acc, int grid, cudaStream_t);
 };
 
 struct LaunchInfo {
@@ -68,6 +70,12 @@ cudaError_t launch_accumulate(const LaunchInfo& li, uint64_t* model, const uint6
 cudaError_t launch_vp_infer(const LaunchInfo& li, const uint64_t* model, const uint64_t* rgsw,
                             size_t n, uint64_t* resp, uint64_t* acc, int grid, cudaStream_t st,
                             int packed = 0);
+// Unencrypted-model inference: the clear counters into plaintext tables, and
+// the responses against them.
+size_t hw_plain_words_li(const LaunchInfo& li);
+cudaError_t launch_plain_load(const LaunchInfo& li, const int64_t* counts, uint64_t* plain, cudaStream_t st);
+cudaError_t launch_vp_plain(const LaunchInfo& li, const uint64_t* plain, const uint64_t* rgsw, size_t n,
+                            uint64_t* resp, uint64_t* acc, int grid, cudaStream_t st);
 cudaError_t launch_count_classes(const LaunchInfo& li, uint64_t* counts, const uint64_t* rgsw, size_t n,
                                  uint64_t* out, uint64_t* acc, int grid, cudaStream_t st);
 cudaError_t launch_pdact_balanced(const LaunchInfo& li, const int64_t* counts, const int64_t* class_counts,

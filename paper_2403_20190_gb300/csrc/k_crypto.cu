@@ -350,6 +350,41 @@ __global__ void __launch_bounds__(Geo<LOGN>::T)
         out[poly * N + eval_addr(16 * tid + e, LOGN, C.ext_loge)] = to_mont(reduce_full(v[e], P), P);
 }
 
+// Clear counters -> the plaintext tables of unencrypted-model inference.  One
+// block per polynomial [RAM j][class c][leaf v][prime]: coefficient k of
+// leaf v is counts[c][j][v + 2^zt k] (zt = max(0, z - L); 0 past the RAM's
+// 2^a addresses), reduced into the prime, transformed, and stored in the
+// external product's evaluation layout in Montgomery form.
+template <int LOGN>
+__global__ void __launch_bounds__(Ring<LOGN>::T)
+    k_plain_load(const DevCtx* __restrict__ Cp, const int64_t* __restrict__ counts, u64* __restrict__ out) {
+    extern __shared__ u64 smem[];
+    constexpr int N = Ring<LOGN>::N, T = Ring<LOGN>::T;
+    Xchg xc{smem, smem + Ring<LOGN>::PADDED, Ring<LOGN>::PADDED, 0};
+    const DevCtx& C = *Cp;
+    const int tid = threadIdx.x;
+    const size_t poly = blockIdx.x;
+    const int jp = (int)(poly % C.r);
+    const int zt = C.z > C.L ? C.z - C.L : 0;
+    const size_t rest = poly / C.r;
+    const int v = (int)(rest & ((1u << zt) - 1));
+    const size_t jc = rest >> zt;
+    const int c = (int)(jc % C.n_classes), j = (int)(jc / C.n_classes);
+    const PrimeConst P = C.P[jp];
+    const size_t n_addr = (size_t)1 << C.a;
+    const int64_t* row = counts + ((size_t)c * C.k0 + j) * n_addr;
+    u64 vv[16];
+#pragma unroll
+    for (int kk = 0; kk < 16; kk++) {
+        const size_t addr = (size_t)v + ((size_t)(tid + kk * T) << zt);
+        vv[kk] = addr < n_addr ? from_signed(row[addr], P.q) : 0;
+    }
+    ntt_fwd1<LOGN>(vv, xc, C, jp);
+#pragma unroll
+    for (int e = 0; e < 16; e++)
+        out[poly * N + eval_addr(16 * tid + e, LOGN, C.ext_loge)] = to_mont(reduce_full(vv[e], P), P);
+}
+
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
@@ -471,6 +506,24 @@ cudaError_t launch_import_rgsw(const LaunchInfo& li, const uint64_t* in, size_t 
     return HW_LAUNCHED();
 }
 
+size_t hw_plain_words_li(const LaunchInfo& li) {
+    const int zt = li.z > li.L ? li.z - li.L : 0;
+    return (size_t)li.k0 * li.n_classes * ((size_t)1 << zt) * li.r * li.n;
+}
+
+cudaError_t launch_plain_load(const LaunchInfo& li, const int64_t* counts, uint64_t* plain, cudaStream_t st) {
+    const size_t polys = hw_plain_words_li(li) / li.n;
+    if (polys == 0) return cudaSuccess;
+    if (polys >= ((size_t)1 << 31)) return cudaErrorInvalidValue;
+#define B(L)                                                                                  \
+    case L:                                                                                   \
+        k_plain_load<L><<<(unsigned)polys, Geo<L>::T, Geo<L>::XCHG_BYTES, st>>>(li.dctx, counts, plain); \
+        break;
+    HW_DISPATCH(li.log_n, B)
+#undef B
+    return HW_LAUNCHED();
+}
+
 extern cudaError_t hw_ntt_kernels_init(const LaunchInfo& li);
 
 cudaError_t hw_kernels_init(const LaunchInfo& li) {
@@ -483,6 +536,7 @@ cudaError_t hw_kernels_init(const LaunchInfo& li) {
         A(k_rlwe_phase, L, Geo<L>::XCHG_BYTES) \
         A(k_export_rgsw, L, Geo<L>::XCHG_BYTES) \
         A(k_import_rgsw, L, Geo<L>::XCHG_BYTES) \
+        A(k_plain_load, L, Geo<L>::XCHG_BYTES) \
         break;
     switch (li.log_n) {
         HW_FOR_EACH_LOGN(X)

@@ -109,6 +109,16 @@ cudaError_t launch_vp_infer(const LaunchInfo& li, const uint64_t* model, const u
     return e;
 }
 
+cudaError_t launch_vp_plain(const LaunchInfo& li, const uint64_t* plain, const uint64_t* rgsw, size_t n,
+                            uint64_t* resp, uint64_t* acc, int grid, cudaStream_t st) {
+    int items = (int)(n * li.k0);
+    if (items == 0) return cudaSuccess;
+    if (grid > items) grid = items;
+    cudaError_t e = li.ext->vp_plain(li, plain, rgsw, items, resp, acc, grid, st);
+    (*li.launches)++;
+    return e;
+}
+
 cudaError_t launch_count_classes(const LaunchInfo& li, uint64_t* counts, const uint64_t* rgsw, size_t n,
                                  uint64_t* out, uint64_t* acc, int grid, cudaStream_t st) {
     if (n == 0) return cudaSuccess;

@@ -73,6 +73,21 @@ class Session:
         fn(self.ctx, model, rgsw, n, resp, sums, scratch, stream)
         return resp, sums
 
+    # -------------------------------------- unencrypted-model inference
+    def plain_model(self, counts, stream=None):
+        """Plaintext tables of a model in clear from its counters W[c][j][addr]
+        (an int64 device tensor (l, k0, 2^a))."""
+        counts = counts.to(device=self.device, dtype=torch.int64).contiguous()
+        assert counts.numel() == self.cfg.n_classes * self.sz["k0"] * (1 << self.sz["a"])
+        plain = self.words(B.hw_plain_model_words(self.ctx), zero=False)
+        B.hw_plain_model_load(self.ctx, counts, plain, stream)
+        return plain
+
+    def infer_plain(self, plain, rgsw, n, bufs=None, stream=None):
+        resp, sums, scratch = bufs if bufs is not None else self.infer_buffers(n)
+        B.hw_infer_plain(self.ctx, plain, rgsw, n, resp, sums, scratch, stream)
+        return resp, sums
+
     # ---------------------------------------------------------------- client
     def decrypt_rlwe(self, key, obj, count, stream=None):
         out = torch.empty(int(count) * self.sz["n"], dtype=torch.int64, device=self.device)
