@@ -66,7 +66,8 @@ def parse():
 # from bit_slot to the VP kernel's end) and the headers of the external
 # product and the modular arithmetic.
 PROFILED_VP_TRAFFIC = {
-    "config": "cfg2", "ext_loge": 3, "ext_np": 2, "ext_smem": 1, "bytes_per_test_sample": 2.1424e9,
+    "config": "cfg2", "ext_loge": 3, "ext_np": 2, "ext_smem": 1, "ext_blocks_per_sm": 1, "l2_persist": 0,
+    "bytes_per_test_sample": 2.1424e9,
     "sources": (("paper_2403_20190_gb300/csrc/hw_ext.cuh", "// Encrypted bit slot that drives",
                  "// EncRGSW."),
                 ("paper_2403_20190_gb300/csrc/hw_ext.cuh", "// ExtractLWE(ct, k) written by the block",
@@ -98,7 +99,8 @@ def profiled_sources_sha(root=None):
 
 def profiled_traffic(config, geometry, n_test):
     t = PROFILED_VP_TRAFFIC
-    if config != t["config"] or any(geometry.get(k) != t[k] for k in ("ext_loge", "ext_np", "ext_smem")):
+    if config != t["config"] or any(geometry.get(k) != t[k] for k in
+                                    ("ext_loge", "ext_np", "ext_smem", "ext_blocks_per_sm", "l2_persist")):
         return None
     if profiled_sources_sha() != t["sha256"]:
         return None  # the kernel changed since the counters were taken

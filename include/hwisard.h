@@ -148,7 +148,8 @@ typedef struct hw_tune_entry {
 
 /* Autotuner (no counterpart in the paper): times every built external-
  * product geometry (and, where it matters, a halved resident-block count;
- * then the fastest one again with l2_persist) on one step of n_probe training and n_probe test samples -- encryption,
+ * then the fastest one again with l2_persist, kept only when at least 2 %
+ * faster) on one step of n_probe training and n_probe test samples -- encryption,
  * training, inference -- and every batched-NTT variant on a batch of
  * polynomials larger than L2, each `reps` times (best time kept), on
  * synthetic inputs in buffers it allocates and frees itself.  *best gets
