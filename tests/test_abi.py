@@ -80,7 +80,7 @@ def test_geometry_lists_need_no_gpu(lib):
     from paper_2403_20190_gb300 import binding
     from synthdata import get_config
     expect_default = {6: (3, 2, 0), 10: (3, 2, 0), 12: (3, 2, 0), 13: (3, 1, 0)}
-    for name, log_n, n_expect in (("cfg1", 6, 10), ("cfg1", 10, 9), ("cfg2", 12, 11), ("cfg3", 13, 3)):
+    for name, log_n, n_expect in (("cfg1", 6, 12), ("cfg1", 10, 9), ("cfg2", 12, 12), ("cfg3", 13, 4)):
         geos = binding.hw_list_geometries(get_config(name, log_n=log_n))
         assert len(geos) == n_expect
         key = [(g["ext_loge"], g["ext_np"], g["ext_smem"]) for g in geos]
