@@ -1,8 +1,10 @@
 // hw_ext.cuh -- the kernels built on the external product, templated on the
 // context's geometry (2^LOGE residues per thread, NP polynomials per
-// transform): RGSW encryption, IVP training and VP inference.  Each ring
-// size's translation unit instantiates its geometries and exposes them as a
-// table of launchers (ExtOps) that the context picks from.
+// transform): RGSW encryption, IVP training, VP inference (with horizontal
+// packing), the class-count IVP of dataset balancing and inference against a
+// model in clear.  Each ring size's translation unit instantiates its
+// geometries and exposes them as a table of launchers (ExtOps) that the
+// context picks from.
 #pragma once
 #include "cdt.cuh"
 #include "hw_internal.cuh"

@@ -1,7 +1,8 @@
 // k_wisard.cu -- the accumulation of a training batch into the model and the
 // per-class response sums; dispatch of the IVP training (Algorithm 6 via the
-// Inverse Vertical Packing of Algorithm 5) and VP inference (Algorithm 7 via
-// the Vertical Packing of Algorithm 3) kernels of hw_ext.cuh.
+// Inverse Vertical Packing of Algorithm 5), VP inference (Algorithm 7 via
+// the Vertical Packing of Algorithm 3), clear-model inference and class-count
+// kernels of hw_ext.cuh.
 #include "hw_internal.cuh"
 #include "hw_launch.h"
 
