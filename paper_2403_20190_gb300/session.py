@@ -15,7 +15,12 @@ class Session:
         if geometry == "auto":
             from .tuning import tuned_geometry
             geometry = tuned_geometry(cfg, device)[0]
-        if geometry:
+            try:
+                self.ctx = B.hw_create_tuned(cfg, geometry, device)
+            except B.HwError:  # a cached choice this library cannot take: measure again
+                geometry = tuned_geometry(cfg, device, refresh=True)[0]
+                self.ctx = B.hw_create_tuned(cfg, geometry, device)
+        elif geometry:
             self.ctx = B.hw_create_tuned(cfg, geometry, device)
         else:
             self.ctx = B.hw_create(cfg, device)

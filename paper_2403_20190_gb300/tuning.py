@@ -18,10 +18,13 @@ CACHE = os.path.join(_build.OUT, "tuning.json")
 
 
 def _key(cfg, device, n_probe):
+    """GPU name, parameters, probe size and the geometries the loaded library
+    builds for them: a library with other candidates measures again."""
     p = B.params_from_config(cfg)
     fields = [f for f, _ in B.HwParams._fields_ if f != "reserved"]
     prm = ",".join(f"{f}={getattr(p, f)}" for f in fields)
-    return f"{torch.cuda.get_device_name(device)}|{prm}|n_probe={n_probe}"
+    built = ";".join(f"{g['ext_loge']}.{g['ext_np']}.{g['ext_smem']}" for g in B.hw_list_geometries(cfg))
+    return f"{torch.cuda.get_device_name(device)}|{prm}|n_probe={n_probe}|built={built}"
 
 
 def _load():
