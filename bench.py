@@ -33,6 +33,9 @@ FALLBACK_HBM_GBS = 6800.0
 # (high half of x*w': 4 partial products; low halves of x*w and qhat*q: 3 each).
 IMAD_PER_CLK_PER_SM = 64
 MULS_PER_MODMUL = 10
+# ... and of one 32-bit Shoup product (low halves of x*w and qhat*q, high
+# half of x*w'), for contexts whose external products run in 32-bit words.
+MULS_PER_MODMUL32 = 3
 
 
 def parse():
@@ -67,20 +70,22 @@ def parse():
 # product and the modular arithmetic.
 PROFILED_VP_TRAFFIC = {
     "config": "cfg2", "ext_loge": 3, "ext_np": 2, "ext_smem": 1, "ext_blocks_per_sm": 1, "l2_persist": 0,
-    "bytes_per_test_sample": 2.1424e9,
+    "bytes_per_test_sample": 2.1133e9,
     "sources": (("paper_2403_20190_gb300/csrc/hw_ext.cuh", "// Encrypted bit slot that drives",
                  "// EncRGSW."),
                 ("paper_2403_20190_gb300/csrc/hw_ext.cuh", "// ExtractLWE(ct, k) written by the block",
                  "// Dataset balancing (Section 3.6.1)"),
                 ("paper_2403_20190_gb300/csrc/hw_internal.cuh", None, None),
                 ("paper_2403_20190_gb300/csrc/modarith.cuh", None, None)),
-    "sha256": "73315347666d96d45f17e4eb1ceaeb3b4353e41f6c41667c14d6edecfd72cba8",
+    "sha256": "1b1c5d9b6538dd97528c71efa032a025f17669d8cca0d819f28b729fc8fef19d",
 }
 # Register-only 64-bit lazy Cooley-Tukey butterflies per second on one GB300
 # at 2070 MHz (profiles/butterfly_ceiling.md): what the integer pipes issue
 # for this arithmetic, beside the multiply-count peak.
 BUTTERFLY_CEILING = {"ct64_t_per_s": 0.8414, "gs64_t_per_s": 0.8755,
                      "source": "microbench/bfly_ceiling.cu"}
+BUTTERFLY_CEILING32 = {"ct32_t_per_s": 3.1435, "gs32_t_per_s": 3.0782,
+                       "source": "microbench/bfly_ceiling.cu"}
 
 
 def profiled_sources_sha(root=None):
@@ -546,7 +551,9 @@ def gpu_arm(args, ws, rank, local, pg):
     alg = algorithmic_counts(sess, cfg)
     sm_count = torch.cuda.get_device_properties(local).multi_processor_count
     sm_mhz = pk.get("sm_max_mhz", 2070.0)
-    peak_modmul = sm_count * IMAD_PER_CLK_PER_SM * sm_mhz * 1e6 / MULS_PER_MODMUL
+    bits = sz["word_bits"]  # the external product's word width in this context
+    muls = MULS_PER_MODMUL32 if bits == 32 else MULS_PER_MODMUL
+    peak_modmul = sm_count * IMAD_PER_CLK_PER_SM * sm_mhz * 1e6 / muls
     infer_modmul = alg["ext_infer_per_sample"] * bsz * alg["per_ext_modmul"]
     # average duration of the inference graph (k_vp_infer + the per-class
     # sums, < 0.5 %) over the timed steps, CUDA events on the launching stream
@@ -556,9 +563,9 @@ def gpu_arm(args, ws, rank, local, pg):
                 "peak": peak_modmul / 1e12, "unit": "T modmul/s", "frac": achieved / peak_modmul,
                 "traffic": profiled_traffic(args.config, sess.geometry, bsz),
                 "launch_ms": vp_ms,
-                "butterfly_ceiling": BUTTERFLY_CEILING,
+                "butterfly_ceiling": BUTTERFLY_CEILING32 if bits == 32 else BUTTERFLY_CEILING,
                 "peak_kind": f"derived: {sm_count} SMs x {IMAD_PER_CLK_PER_SM} int32 multiplies/clk x "
-                             f"{sm_mhz:.0f} MHz / {MULS_PER_MODMUL} per 64-bit modular product"}
+                             f"{sm_mhz:.0f} MHz / {muls} per {bits}-bit modular product"}
     train_modmul = alg["ext_train_per_sample"] * bsz * alg["per_ext_modmul"]
 
     # batched NTT throughput (forward transforms, one read + one write per

@@ -86,6 +86,10 @@ typedef struct hw_sizes {
     size_t sample_words;    /* n_slots rgsw_words: one encrypted sample */
     size_t resp_words;      /* l k0 lwe_words: responses of one test sample */
     size_t sums_words;      /* l lwe_words: class sums of one test sample */
+    int32_t word_bits;      /* 32: external products and encryption transforms run in 32-bit
+                               words (every q_i < 2^30, several gadget digits per prime,
+                               N <= 2048); 64 otherwise.  Results are the same either way. */
+    int32_t reserved;
 } hw_sizes;
 
 /* Create a context on `cuda_device` for the given parameters: finds the

@@ -32,7 +32,7 @@ class HwSizes(ctypes.Structure):
         "n", "r", "L", "a", "s", "k0", "k1", "z", "dpp", "dnum", "n_data", "n_slots")] + [
         ("q", ctypes.c_uint64 * 4)] + [(name, ctypes.c_size_t) for name in (
             "rlwe_words", "lwe_words", "rgsw_words", "key_words", "model_words", "sample_words",
-            "resp_words", "sums_words")]
+            "resp_words", "sums_words")] + [("word_bits", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 GEOMETRY_FIELDS = ("ext_loge", "ext_np", "ext_blocks_per_sm", "ntt_loge", "ntt_limbs", "ext_smem",
@@ -234,7 +234,7 @@ def hw_autotune(params, device: int = 0, n_probe: int = 4, reps: int = 2):
 def hw_get_sizes(ctx) -> dict:
     s = HwSizes()
     _check(load().hw_get_sizes(ctx.handle, ctypes.byref(s)), "hw_get_sizes")
-    d = {f: getattr(s, f) for f, _ in HwSizes._fields_ if f != "q"}
+    d = {f: getattr(s, f) for f, _ in HwSizes._fields_ if f not in ("q", "reserved")}
     d["q"] = [int(v) for v in s.q][: s.r]
     return d
 

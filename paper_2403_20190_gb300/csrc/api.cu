@@ -425,6 +425,19 @@ extern "C" int hw_create_tuned(const hw_params* p, const hw_geometry* g, int cud
             H.n_inv32_s[i] = (uint32_t)((ni << 32) / qi);
         }
 
+    // 32-bit external product: 30-bit primes, several digits per prime, a
+    // MAC sum of 2 dnum products (q - 1)^2 that fits 64 bits, and a ring the
+    // 32-bit path is compiled for (N <= 2048)
+    H.ext32 = 0;
+    if (small_q && !H.diag && log_n <= 11) {
+        unsigned __int128 bound = 0;
+        for (int i = 0; i < r; i++) {
+            const unsigned __int128 m = (unsigned __int128)(q[i] - 1) * (q[i] - 1) * (2 * (u64)dnum);
+            if (m > bound) bound = m;
+        }
+        H.ext32 = bound < ((unsigned __int128)1 << 64) ? 1 : 0;
+    }
+
     // digits must lift without reduction: |d| <= (q_i - 1)/2 < q_j
     for (int i = 0; i < r; i++)
         for (int j = 0; j < r; j++)
@@ -531,6 +544,7 @@ extern "C" int hw_create_tuned(const hw_params* p, const hw_geometry* g, int cud
     S.sample_words = H.sample_words;
     S.resp_words = (size_t)p->n_classes * k0 * H.lwe_words;
     S.sums_words = (size_t)p->n_classes * H.lwe_words;
+    S.word_bits = H.ext32 ? 32 : 64;
 
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, cuda_device);

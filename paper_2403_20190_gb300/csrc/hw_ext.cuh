@@ -78,11 +78,35 @@ __global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP>::T, ExtCfg<LOGN, LOGE, 
             v[0][kk] = A[x];
             v[1][kk] = shoup_mul(from_signed((int64_t)ebuf[x], q), mr, mr_s, q);  // e R
         }
-        if constexpr (NP == 2) {
-            ntt_fwd<LOGN, LOGE, 2>(v, xc, C, j);
-        } else {
-            ntt_fwd<LOGN, LOGE, 1>(reinterpret_cast<u64(&)[1][E]>(v[0]), xc, C, j);
-            ntt_fwd<LOGN, LOGE, 1>(reinterpret_cast<u64(&)[1][E]>(v[1]), xc, C, j);
+        bool done = false;
+        if constexpr (LOGN <= 11) {
+            if (C.ext32) {  // primes below 2^30: the same transform in 32-bit words
+                u32 w[2][E];
+#pragma unroll
+                for (int pp = 0; pp < 2; pp++)
+#pragma unroll
+                    for (int kk = 0; kk < E; kk++) w[pp][kk] = (u32)v[pp][kk];
+                const uint2* tw = C.tw32_fwd + (size_t)j * N;
+                if constexpr (NP == 2) {
+                    fwd_from32<LOGN, LOGE, 2, 0>(w, xc, tw, (u32)q, 2 * (u32)q);
+                } else {
+                    fwd_from32<LOGN, LOGE, 1, 0>(reinterpret_cast<u32(&)[1][E]>(w[0]), xc, tw, (u32)q, 2 * (u32)q);
+                    fwd_from32<LOGN, LOGE, 1, 0>(reinterpret_cast<u32(&)[1][E]>(w[1]), xc, tw, (u32)q, 2 * (u32)q);
+                }
+#pragma unroll
+                for (int pp = 0; pp < 2; pp++)
+#pragma unroll
+                    for (int e = 0; e < E; e++) v[pp][e] = w[pp][e];  // < 4q, reduced below
+                done = true;
+            }
+        }
+        if (!done) {
+            if constexpr (NP == 2) {
+                ntt_fwd<LOGN, LOGE, 2>(v, xc, C, j);
+            } else {
+                ntt_fwd<LOGN, LOGE, 1>(reinterpret_cast<u64(&)[1][E]>(v[0]), xc, C, j);
+                ntt_fwd<LOGN, LOGE, 1>(reinterpret_cast<u64(&)[1][E]>(v[1]), xc, C, j);
+            }
         }
         const u64 gM = (bit && j == gi) ? to_mont(C.gconst[rho], P) : 0;
         const u64* sM = key + (size_t)(r + j) * N;
@@ -707,6 +731,15 @@ struct ExtVariant {
 // Defines hw_ext_table_<L>: the geometries instantiated for N = 2^L.
 #define HW_EXT_TABLE(L, LIST)                                 \
     const ExtOps* hw_ext_table_##L(int* count) {              \
+        static const ExtOps table[] = {LIST};                 \
+        *count = (int)(sizeof(table) / sizeof(table[0]));     \
+        return table;                                         \
+    }
+// Defines hw_ext_table_<L>_p<PART>: one part of the geometries of N = 2^L,
+// for ring sizes whose instantiations are split over translation units so
+// that they compile in parallel (k_wisard.cu joins the parts, part 0 first).
+#define HW_EXT_TABLE_PART(L, PART, LIST)                      \
+    const ExtOps* hw_ext_table_##L##_p##PART(int* count) {    \
         static const ExtOps table[] = {LIST};                 \
         *count = (int)(sizeof(table) / sizeof(table[0]));     \
         return table;                                         \

@@ -52,6 +52,7 @@ struct DevCtx {
     const uint2* tw32_inv;
     uint32_t n_inv32[HW_MAXP], n_inv32_s[HW_MAXP];
     int diag;  // one digit per prime: the digit of prime i at prime i is the residue
+    int ext32;  // the external product runs in 32-bit words (ext_product32)
     size_t rlwe_words, rgsw_words, lwe_words, sample_words, model_words;
 };
 
@@ -611,10 +612,134 @@ struct Acc {
     }
 };
 
+// The external product in 32-bit words, for contexts whose primes are below
+// 2^30 and whose gadget has several digits per prime (no diagonal digit, so
+// no evaluation-form companions).  Digits are lifted to q_j and transformed
+// as 32-bit words; the MAC adds the exact 64-bit products d * row (d < q_j,
+// rows < q_j in Montgomery form x 2^64: a sum of 2 dnum terms stays below
+// 2^64, which the host checks before it sets C.ext32); each output residue is
+// reduced once and the rows' factor 2^64 taken off with one REDC.  The same
+// canonical results as the 64-bit path.
+template <int LOGN, int LOGE, int NP, int AS>
+__device__ __noinline__ void ext_product32(const DevCtx& C, const u64* __restrict__ rgsw,
+                                           const u64* srcA, int eA, const u64* srcB, int eB, int mode,
+                                           u64* dst, Xchg& xc, ExtNtt nt) {
+    constexpr int N = Ring<LOGN, LOGE>::N, T = Ring<LOGN, LOGE>::T, E = 1 << LOGE;
+    const int tid = threadIdx.x, r = C.r;
+    const int ndig = 2 * C.dnum;
+    const u64 rpol = rgsw_policy();
+    if (nt.prefetch_cur) prefetch_l2(rgsw, C.rgsw_words);
+    if (nt.next_rgsw) prefetch_l2(nt.next_rgsw, C.rgsw_words);
+    __syncthreads();  // exchange buffers are free
+    for (int j = 0; j < r; j++) {
+        const PrimeConst Pj = C.P[j];
+        const u64 qj = Pj.q;
+        const u32 q32 = (u32)qj, q2 = 2 * q32;
+        Acc<E, T, AS != 0> acc(xc.accs);
+#pragma unroll
+        for (int e = 0; e < E; e++) {
+            acc.set(0, e, 0);
+            acc.set(1, e, 0);
+        }
+        for (int u0 = 0; u0 < ndig; u0 += NP) {
+            u32 v[NP][E];
+            int comps[NP], rhos[NP];
+#pragma unroll
+            for (int pp = 0; pp < NP; pp++) {
+                const int u = u0 + pp;
+                const int comp = u / C.dnum, rho = u % C.dnum;
+                comps[pp] = comp;
+                rhos[pp] = rho;
+                const int i = rho / C.dpp, k = rho % C.dpp;
+                const u64 qi = C.P[i].q;
+                const u64* pa = srcA + ((size_t)comp * r + i) * N;
+                const u64* pb = srcB ? srcB + ((size_t)comp * r + i) * N : nullptr;
+#pragma unroll
+                for (int kk = 0; kk < E; kk++) {
+                    const int x = tid + kk * T;
+                    u64 val = rot_read(pa, x, eA, N, qi);
+                    if (pb) val = sub_mod(val, rot_read(pb, x, eB, N, qi), qi);
+                    v[pp][kk] = (u32)lift_small(gadget_digit(centre(val, qi), k, C.dpp, C.log_beta), qj);
+                }
+            }
+            fwd_from32<LOGN, LOGE, NP, 0>(v, xc, C.tw32_fwd + (size_t)j * N, q32, q2);
+#pragma unroll
+            for (int pp = 0; pp < NP; pp++) {
+                const int comp = comps[pp], rho = rhos[pp];
+                const int row = comp == 1 ? rho : C.dnum + rho;
+                const u64* Ra = rgsw + ((size_t)(row * 2 + 0) * r + j) * N + tid;
+                const u64* Rb = rgsw + ((size_t)(row * 2 + 1) * r + j) * N + tid;
+#pragma unroll
+                for (int e = 0; e < E; e++) {
+                    u32 d = v[pp][e];  // < 4q
+                    d = d >= q2 ? d - q2 : d;
+                    d = d >= q32 ? d - q32 : d;
+                    const u32 ra = (u32)ld_rgsw(Ra + e * T, rpol), rb = (u32)ld_rgsw(Rb + e * T, rpol);
+                    acc.add(0, e, (u64)d * ra);
+                    acc.add(1, e, (u64)d * rb);
+                }
+            }
+        }
+        const u32 ninv = C.n_inv32[j], ninv_s = C.n_inv32_s[j];
+        constexpr int NPI = NP < 2 ? NP : 2;  // the two output components
+        for (int oc0 = 0; oc0 < 2; oc0 += NPI) {
+            u32 v[NPI][E];
+#pragma unroll
+            for (int pp = 0; pp < NPI; pp++)
+#pragma unroll
+                for (int e = 0; e < E; e++) {
+                    // (sum d * row) mod q carries the rows' 2^64: REDC takes it off
+                    const u64 sred = redc(0, reduce64(acc.get(oc0 + pp, e), Pj), Pj);
+                    v[pp][e] = shoup32_lazy((u32)sred, ninv, ninv_s, q32);
+                }
+            inv_from32<LOGN, LOGE, NPI, 0>(v, xc, C.tw32_inv + (size_t)j * N, q32, q2);
+#pragma unroll
+            for (int pp = 0; pp < NPI; pp++) {
+                const int oc = oc0 + pp;
+                const u64* base = srcB ? srcB + ((size_t)oc * r + j) * N : nullptr;
+                if (mode == EXT_LWE) {
+                    u64* lw = dst + (size_t)j * (N + 1);
+                    if (oc == 0) {
+#pragma unroll
+                        for (int kk = 0; kk < E; kk++) {
+                            const int x = tid + kk * T;
+                            u64 val = v[pp][kk] >= q32 ? v[pp][kk] - q32 : v[pp][kk];
+                            val = add_mod(val, rot_read(base, x, eB, N, qj), qj);
+                            if (x == 0)
+                                lw[0] = val;
+                            else
+                                lw[N - x] = neg_mod(val, qj);
+                        }
+                    } else if (tid == 0) {
+                        u64 val = v[pp][0] >= q32 ? v[pp][0] - q32 : v[pp][0];
+                        lw[N] = add_mod(val, rot_read(base, 0, eB, N, qj), qj);
+                    }
+                } else {
+                    u64* dd = dst + ((size_t)oc * r + j) * N;
+#pragma unroll
+                    for (int kk = 0; kk < E; kk++) {
+                        const int x = tid + kk * T;
+                        u64 val = v[pp][kk] >= q32 ? v[pp][kk] - q32 : v[pp][kk];
+                        if (mode == EXT_ADD) val = add_mod(val, rot_read(base, x, eB, N, qj), qj);
+                        dd[x] = val;
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();  // dst complete for the whole block
+}
+
 template <int LOGN, int LOGE, int NP, int AS = 0>
 __device__ __noinline__ void ext_product(const DevCtx& C, const u64* __restrict__ rgsw,
                                          const u64* srcA, int eA, const u64* srcB, int eB, int mode,
                                          u64* dst, Xchg& xc, ExtNtt nt) {
+    if constexpr (LOGN <= 11) {  // the rings of the 30-bit parameter sets
+        if (C.ext32) {
+            ext_product32<LOGN, LOGE, NP, AS>(C, rgsw, srcA, eA, srcB, eB, mode, dst, xc, nt);
+            return;
+        }
+    }
     constexpr int N = Ring<LOGN, LOGE>::N, T = Ring<LOGN, LOGE>::T, E = 1 << LOGE;
     const int tid = threadIdx.x, r = C.r;
     const bool cmux_rot = nt.rot_t >= 0;

@@ -51,9 +51,16 @@ struct LaunchInfo {
 
 // Geometry tables, one per ring size (k_ext_*.cu), and lookup.
 #define HW_EXT_TABLE_DECL(L) const ExtOps* hw_ext_table_##L(int* count);
-HW_EXT_TABLE_DECL(6) HW_EXT_TABLE_DECL(7) HW_EXT_TABLE_DECL(8) HW_EXT_TABLE_DECL(9)
-HW_EXT_TABLE_DECL(10) HW_EXT_TABLE_DECL(11) HW_EXT_TABLE_DECL(12) HW_EXT_TABLE_DECL(13)
+HW_EXT_TABLE_DECL(7) HW_EXT_TABLE_DECL(8) HW_EXT_TABLE_DECL(9)
+HW_EXT_TABLE_DECL(11) HW_EXT_TABLE_DECL(13)
 #undef HW_EXT_TABLE_DECL
+// N = 64, 1024 and 4096 are split in two parts (k_ext_l6a/b.cu, ...).
+const ExtOps* hw_ext_table_6_p0(int* count);
+const ExtOps* hw_ext_table_6_p1(int* count);
+const ExtOps* hw_ext_table_10_p0(int* count);
+const ExtOps* hw_ext_table_10_p1(int* count);
+const ExtOps* hw_ext_table_12_p0(int* count);
+const ExtOps* hw_ext_table_12_p1(int* count);
 const ExtOps* hw_ext_table(int log_n, int* count);
 const ExtOps* hw_ext_find(int log_n, int loge, int np, int sm);
 

@@ -6,6 +6,8 @@
 #include "hw_internal.cuh"
 #include "hw_launch.h"
 
+#include <vector>
+
 // H[j][t] += sum over the batch of out[i][j][t] (mod q), one word per thread.
 __global__ void k_accumulate(const DevCtx* __restrict__ Cp, u64* __restrict__ model,
                              const u64* __restrict__ out, int n) {
@@ -57,13 +59,40 @@ __global__ void k_class_sums(const DevCtx* __restrict__ Cp, const u64* __restric
 // ---------------------------------------------------------------------------
 // launchers: the external-product kernels go through the context's ExtOps
 // ---------------------------------------------------------------------------
+// The two parts of a split ring size as one table, part 0 (the default
+// first) then part 1.
+static std::vector<ExtOps> join_parts(const ExtOps* (*p0)(int*), const ExtOps* (*p1)(int*)) {
+    std::vector<ExtOps> t;
+    for (auto part : {p0, p1}) {
+        int n = 0;
+        const ExtOps* x = part(&n);
+        t.insert(t.end(), x, x + n);
+    }
+    return t;
+}
+
 const ExtOps* hw_ext_table(int log_n, int* count) {
     *count = 0;
     switch (log_n) {
+        case 6: {
+            static const std::vector<ExtOps> t = join_parts(hw_ext_table_6_p0, hw_ext_table_6_p1);
+            *count = (int)t.size();
+            return t.data();
+        }
+        case 10: {
+            static const std::vector<ExtOps> t = join_parts(hw_ext_table_10_p0, hw_ext_table_10_p1);
+            *count = (int)t.size();
+            return t.data();
+        }
+        case 12: {
+            static const std::vector<ExtOps> t = join_parts(hw_ext_table_12_p0, hw_ext_table_12_p1);
+            *count = (int)t.size();
+            return t.data();
+        }
 #define X(L) \
     case L:  \
         return hw_ext_table_##L(count);
-        HW_FOR_EACH_LOGN(X)
+        X(7) X(8) X(9) X(11) X(13)
 #undef X
     }
     return nullptr;

@@ -64,7 +64,14 @@ def test_autotune_picks_a_built_geometry_and_keeps_parity():
     assert any(e["geometry"]["ext_smem"] == 1 for e in step)
     # 55-bit primes: radix 8 and 16, 64-bit words only
     assert sorted((e["geometry"]["ntt_loge"], e["geometry"]["ntt_limbs"]) for e in ntt) == [(3, 2), (4, 2)]
-    fastest = min(step, key=lambda e: e["ms_encrypt"] + e["ms_train"] + e["ms_infer"])
+    def t(e):
+        return e["ms_encrypt"] + e["ms_train"] + e["ms_infer"]
+
+    # the fastest geometry, and L2 persistence on it only at a >= 2 % gain
+    fastest = min((e for e in step if e["geometry"]["l2_persist"] == 0), key=t)
+    l2 = [e for e in step if e["geometry"]["l2_persist"] == 1]
+    if l2 and t(l2[0]) < 0.98 * t(fastest):
+        fastest = l2[0]
     keys = ("ext_loge", "ext_np", "ext_blocks_per_sm", "ext_smem", "l2_persist")
     assert tuple(best[k] for k in keys) == tuple(fastest["geometry"][k] for k in keys)
     tiny_full_parity("zltL_h3", best)
