@@ -273,7 +273,6 @@ def algorithmic_counts(sess, cfg):
     per_ext = 2 * dnum * r * bfly + 2 * r * bfly + 2 * 2 * dnum * r * n
     slots = B.hw_get_ram_slots(sess.ctx)
     ext_train = ext_infer = ext_clear = 0
-    gates = {1: 0}
     for j in range(k0):
         enc = [slots[j * a + i] >= 0 for i in range(a)]
         # training: rotation bits z..L+a-1 that are encrypted (labels always are)
@@ -288,7 +287,6 @@ def algorithmic_counts(sess, cfg):
         # class when zt = 1
         zt = max(0, z - L)
         ext_clear += sum(1 for i in range(zt, a) if enc[i]) + (l if zt and enc[0] else 0)
-    _ = gates
     # pruned CDEMUX gates per RAM (same for every RAM when their tree bits are encrypted)
     V = set()
     for c in range(l):

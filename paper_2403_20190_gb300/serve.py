@@ -35,7 +35,7 @@ equals sequential training of all train requests (addition mod q commutes).
 import collections
 import copy
 import time
-from dataclasses import dataclass, field
+from dataclasses import dataclass
 
 import numpy as np
 import torch

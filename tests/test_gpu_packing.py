@@ -7,7 +7,7 @@ import pytest
 import torch
 
 from oracle import Oracle, wisard
-from synthdata import get_config, make_dataset
+from synthdata import get_config
 from test_gpu_parity import TINY, run_pipeline, tiny_cfg, u64
 
 pytestmark = pytest.mark.gpu
