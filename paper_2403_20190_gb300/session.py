@@ -93,6 +93,22 @@ class Session:
         B.hw_infer_plain(self.ctx, plain, rgsw, n, resp, sums, scratch, stream)
         return resp, sums
 
+    # ----------------------------------------------------- checkpoint
+    def save_model(self, path, model, samples):
+        """Checkpoint of the model after `samples` training samples."""
+        from .checkpoint import save
+        torch.cuda.synchronize(self.device)
+        save(path, self.cfg, model, samples)
+
+    def load_model(self, path):
+        """(model on this device, samples trained) from a checkpoint of the
+        same parameter set; training continues from it bit-exactly."""
+        from .checkpoint import load
+        model, samples = load(path, self.cfg, self.device)
+        if model.numel() != self.sz["model_words"]:
+            raise ValueError(f"{path}: {model.numel()} words, the model has {self.sz['model_words']}")
+        return model, samples
+
     # ---------------------------------------------------------------- client
     def decrypt_rlwe(self, key, obj, count, stream=None):
         out = torch.empty(int(count) * self.sz["n"], dtype=torch.int64, device=self.device)
