@@ -97,6 +97,9 @@ typedef struct hw_sizes {
  * matrix, and uploads them.  The RNS modulus and noise distribution are the
  * readings of Section 2.4 (Setup) listed with the project's design notes. */
 int hw_create(const hw_params* params, int cuda_device, hw_ctx** out);
+/* (Testing hook: with HW_FAULT_ALLOC=k in the environment, the k-th device
+ * allocation of each hw_create fails as if the device were out of memory;
+ * the call returns HW_ECUDA having freed what it allocated.) */
 int hw_destroy(hw_ctx* ctx);
 
 /* Kernel geometry of a context.  It has no counterpart in the paper and

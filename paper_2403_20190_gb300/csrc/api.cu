@@ -8,6 +8,7 @@
 
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -37,6 +38,19 @@ static int fail(int code, const char* fmt, ...) {
             return fail(HW_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
                         __LINE__);                                                              \
     } while (0)
+
+// Host-side fault injection for tests: with HW_FAULT_ALLOC=k in the
+// environment, the k-th device allocation of each hw_create fails as if the
+// device were out of memory (the allocation is not attempted).
+static cudaError_t ctx_malloc(void** p, size_t bytes, int* nth) {
+    ++*nth;
+    const char* f = getenv("HW_FAULT_ALLOC");
+    if (f && atoi(f) == *nth) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
 
 struct hw_ctx {
     hw_params prm;
@@ -476,11 +490,15 @@ extern "C" int hw_create_tuned(const hw_params* p, const hw_geometry* g, int cud
     size_t total = al(bytes_tw) + al(bytes_rs) + al(bytes_perm) + al(bytes_h3) + 2 * al(bytes_rot) +
                    al(bytes_tw32) + al(sizeof(DevCtx));
     c->phase_chunk = 64;
+    c->tables = nullptr;
+    c->phase_scratch = nullptr;
+    int n_alloc = 0;
     cudaError_t e = cudaSetDevice(cuda_device);
-    if (e == cudaSuccess) e = cudaMalloc(&c->tables, total);
+    if (e == cudaSuccess) e = ctx_malloc(&c->tables, total, &n_alloc);
     if (e == cudaSuccess)
-        e = cudaMalloc(&c->phase_scratch, c->phase_chunk * (size_t)r * n * sizeof(u64));
+        e = ctx_malloc((void**)&c->phase_scratch, c->phase_chunk * (size_t)r * n * sizeof(u64), &n_alloc);
     if (e != cudaSuccess) {
+        if (c->tables) cudaFree(c->tables);
         delete c;
         return fail(HW_ECUDA, "device allocation failed: %s", cudaGetErrorString(e));
     }
