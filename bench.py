@@ -325,7 +325,24 @@ def gpu_arm(args, ws, rank, local, pg):
         t0 = time.perf_counter()
         geometry, entries, cached = tuned_geometry(cfg, local)
         tune = {"cached": cached, "seconds": round(time.perf_counter() - t0, 2), "candidates": entries}
+        # every other parameter set the legs use is tuned now, before this
+        # process holds any context or buffer: the tuner's probe contexts come
+        # and go while nothing else is resident, and the legs find the cache
+        others = set()
+        if not (args.no_ntt and args.no_packing) and args.config != "cfg1":
+            others.add("cfg1")
+        if not args.no_serve:
+            others.update(("cfg1", "cfg2", "cfg3", "cfg4"))
+        for nm in sorted(others - {args.config}):
+            tuned_geometry(get_config(nm), local)
     sess = Session(cfg, local, geometry=geometry)
+
+    def healthy(where):
+        """Stop before launching on a context whose device tables changed."""
+        try:
+            B.hw_check_context(sess.ctx)
+        except B.HwError as e:
+            raise RuntimeError(f"context check failed after {where}: {e}") from None
     if tune is not None:
         tune["chosen"] = sess.geometry
     dev = sess.device
@@ -434,6 +451,8 @@ def gpu_arm(args, ws, rank, local, pg):
     keys = ["encrypt_train", "train", "encrypt_test", "infer", "decrypt_pdact"]
     ph = {kn: evs[a].elapsed_time(evs[b]) for a, b, kn in zip(names[:-1], names[1:], keys)}
 
+    healthy("the timed steps")
+
     # dataset balancing (Section 3.6.1) on the same step: the label-bit IVP
     # over the training batch into the class-count ciphertext, its
     # decryption and the balanced PD-act of the test batch
@@ -457,6 +476,8 @@ def gpu_arm(args, ws, rank, local, pg):
                      "share_of_step": (t_count + t_post) / (elapsed_ms / args.steps),
                      "ext_products_per_sample": sz["L"]}
         del bal_scr
+
+    healthy("the balancing leg")
 
     # PackingKeySwitching (Section 2.4): the test batch's responses packed
     # into one RLWE per sample (what Algorithm 7 returns for PD-act)
@@ -483,6 +504,8 @@ def gpu_arm(args, ws, rank, local, pg):
                      "response_bytes_per_sample": {"lwe": sz["resp_words"] * 8, "packed": sz["rlwe_words"] * 8},
                      "share_of_infer": min(t_pack) / ph["infer"]}
         del ksk, pscr
+
+    healthy("the key-switching leg")
 
     # inference against the model in clear (Section 3.6.2): the owner's
     # decrypted counters as plaintext tables, one blind rotation per (sample,
@@ -519,6 +542,8 @@ def gpu_arm(args, ws, rank, local, pg):
                        "responses_equal_to_encrypted_path": same}
         del plain, pbufs, W
 
+    healthy("the clear-model leg")
+
     # e2e through the C ABI with pinned host buffers, copies inside the timed region
     e2e = None
     if not args.no_e2e:
@@ -544,13 +569,15 @@ def gpu_arm(args, ws, rank, local, pg):
                "h2d_bytes_per_step": int(h_tr.numel() + h_lab.numel() * 4 + h_te.numel()),
                "d2h_bytes_per_step": int(h_out.numel() * 4)}
 
+    healthy("the end-to-end leg")
+
     # roofline of the dominant kernel (the VP inference kernel)
     pk, pk_kind = peaks()
     alg = algorithmic_counts(sess, cfg)
     sm_count = torch.cuda.get_device_properties(local).multi_processor_count
     sm_mhz = pk.get("sm_max_mhz", 2070.0)
-    bits = sz["word_bits"]  # the external product's word width in this context
-    muls = MULS_PER_MODMUL32 if bits == 32 else MULS_PER_MODMUL
+    word_bits = sz["word_bits"]  # the external product's word width in this context
+    muls = MULS_PER_MODMUL32 if word_bits == 32 else MULS_PER_MODMUL
     peak_modmul = sm_count * IMAD_PER_CLK_PER_SM * sm_mhz * 1e6 / muls
     infer_modmul = alg["ext_infer_per_sample"] * bsz * alg["per_ext_modmul"]
     # average duration of the inference graph (k_vp_infer + the per-class
@@ -561,9 +588,9 @@ def gpu_arm(args, ws, rank, local, pg):
                 "peak": peak_modmul / 1e12, "unit": "T modmul/s", "frac": achieved / peak_modmul,
                 "traffic": profiled_traffic(args.config, sess.geometry, bsz),
                 "launch_ms": vp_ms,
-                "butterfly_ceiling": BUTTERFLY_CEILING32 if bits == 32 else BUTTERFLY_CEILING,
+                "butterfly_ceiling": BUTTERFLY_CEILING32 if word_bits == 32 else BUTTERFLY_CEILING,
                 "peak_kind": f"derived: {sm_count} SMs x {IMAD_PER_CLK_PER_SM} int32 multiplies/clk x "
-                             f"{sm_mhz:.0f} MHz / {muls} per {bits}-bit modular product"}
+                             f"{sm_mhz:.0f} MHz / {muls} per {word_bits}-bit modular product"}
     train_modmul = alg["ext_train_per_sample"] * bsz * alg["per_ext_modmul"]
 
     # batched NTT throughput (forward transforms, one read + one write per
@@ -597,6 +624,8 @@ def gpu_arm(args, ws, rank, local, pg):
             s1 = Session(get_config("cfg1"), local, geometry="auto" if args.geometry == "auto" else None)
             ntt["cfg1"] = ntt_rate(s1, 262144)
             del s1
+
+    healthy("the NTT leg")
 
     # horizontal packing (Section 6): plain vs packed inference on the
     # Wisconsin-shaped ring (label bits low, z = 0: one VP answers both
@@ -634,6 +663,8 @@ def gpu_arm(args, ws, rank, local, pg):
         if ps is not sess:
             del ps
 
+    healthy("the packing leg")
+
     # the same workload one request at a time: each request one train and one
     # test sample, encoded, encrypted, trained, inferred, decrypted, waited for
     single = None
@@ -656,6 +687,7 @@ def gpu_arm(args, ws, rank, local, pg):
 
     serving = None
     if not args.no_serve:
+        healthy("the one-at-a-time requests")
         del st, tr_vals_d, tr_lab_d, te_vals_d, bits
         torch.cuda.synchronize()
         torch.cuda.empty_cache()

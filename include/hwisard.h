@@ -134,6 +134,13 @@ typedef struct hw_geometry {
  * out of range; hw_list_geometries() gives the pairs that are built. */
 int hw_create_tuned(const hw_params* params, const hw_geometry* geometry, int cuda_device,
                     hw_ctx** out);
+/* Self-check (no counterpart in the paper): HW_OK while the context's device
+ * tables (transform, rotation and index tables and the device copy of the
+ * context) are byte for byte what hw_create uploaded, HW_EMISMATCH if
+ * anything has written into them since.  Synchronous; copies the tables
+ * back (a few MB).  Lets a long-running caller detect a stray write before
+ * it launches work on a damaged context. */
+int hw_check_context(const hw_ctx* ctx);
 /* The context's geometry with every default resolved. */
 int hw_get_geometry(const hw_ctx* ctx, hw_geometry* out);
 /* The external-product geometries built for params->log_n (ext_loge,

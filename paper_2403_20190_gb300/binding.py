@@ -66,6 +66,7 @@ _SIGS = {
                                    ctypes.POINTER(HwGeometry), _VP, _SZ, ctypes.POINTER(_SZ)]),
     "hw_destroy": (ctypes.c_int, [_VP]),
     "hw_get_sizes": (ctypes.c_int, [_VP, ctypes.POINTER(HwSizes)]),
+    "hw_check_context": (ctypes.c_int, [_VP]),
     "hw_get_ram_slots": (ctypes.c_int, [_VP, _VP, _SZ]),
     "hw_train_scratch_words": (_SZ, [_VP, _SZ]),
     "hw_infer_scratch_words": (_SZ, [_VP, _SZ]),
@@ -128,13 +129,17 @@ def _check(rc, what):
 
 
 def _ptr(t):
+    """Device address of a buffer argument: a contiguous torch tensor (or
+    None where the call allows it).  Anything else -- a number passed where
+    a buffer belongs -- is refused here, before it can reach a kernel as an
+    address."""
     if t is None:
         return None
     if isinstance(t, torch.Tensor):
         if not t.is_contiguous():
             raise HwError("buffers must be contiguous")
         return ctypes.c_void_p(t.data_ptr())
-    return ctypes.c_void_p(t)
+    raise HwError(f"a buffer argument must be a torch tensor, not {type(t).__name__}")
 
 
 def _stream(stream):
@@ -229,6 +234,11 @@ def hw_autotune(params, device: int = 0, n_probe: int = 4, reps: int = 2):
         entries.append(dict(geometry=_geometry_dict(e.geometry), ms_encrypt=e.ms_encrypt, ms_train=e.ms_train,
                             ms_infer=e.ms_infer, ms_ntt=e.ms_ntt, status=int(e.status)))
     return _geometry_dict(best), entries
+
+
+def hw_check_context(ctx):
+    """Raises HwError (HW_EMISMATCH) if the context's device tables changed."""
+    _check(load().hw_check_context(ctx.handle), "hw_check_context")
 
 
 def hw_get_sizes(ctx) -> dict:

@@ -39,6 +39,16 @@ static int fail(int code, const char* fmt, ...) {
                         __LINE__);                                                              \
     } while (0)
 
+// FNV-1a over a byte range (the context self-check's fingerprint).
+static uint64_t fnv1a(const unsigned char* p, size_t n) {
+    uint64_t h = 0xcbf29ce484222325ULL;
+    for (size_t i = 0; i < n; i++) {
+        h ^= p[i];
+        h *= 0x100000001b3ULL;
+    }
+    return h;
+}
+
 // Host-side fault injection for tests: with HW_FAULT_ALLOC=k in the
 // environment, the k-th device allocation of each hw_create fails as if the
 // device were out of memory (the allocation is not attempted).
@@ -59,6 +69,8 @@ struct hw_ctx {
     DevCtx host;          // host copy (device pointers filled in)
     DevCtx* dctx;         // device copy
     void* tables;         // one device block for all tables
+    size_t tables_bytes;  // its size, and the FNV-1a hash of what was uploaded
+    uint64_t tables_hash;
     u64* phase_scratch;   // decryption phases, chunk * r * N words
     size_t phase_chunk;
     LaunchInfo li;
@@ -504,6 +516,7 @@ extern "C" int hw_create_tuned(const hw_params* p, const hw_geometry* g, int cud
     }
     char* base = (char*)c->tables;
     size_t off = 0;
+    cudaMemset(base, 0, total);  // padding between tables hashes as zeros
     auto put = [&](const void* src, size_t nb) {
         char* d = base + off;
         cudaMemcpy(d, src, nb, cudaMemcpyHostToDevice);
@@ -526,6 +539,13 @@ extern "C" int hw_create_tuned(const hw_params* p, const hw_geometry* g, int cud
     H.ext_loge = G.ext_loge;
     H.ext_np = G.ext_np;
     c->dctx = (DevCtx*)put(&H, sizeof(DevCtx));
+    c->tables_bytes = total;
+    c->tables_hash = 0;
+    {
+        std::vector<unsigned char> img(total);
+        if (cudaMemcpy(img.data(), base, total, cudaMemcpyDeviceToHost) == cudaSuccess)
+            c->tables_hash = fnv1a(img.data(), total);
+    }
     LaunchInfo& li = c->li;
     li.log_n = log_n;
     li.ext = hw_ext_find(log_n, G.ext_loge, G.ext_np, G.ext_smem);
@@ -657,6 +677,17 @@ extern "C" int hw_destroy(hw_ctx* c) {
     cudaFree(c->tables);
     cudaFree(c->phase_scratch);
     delete c;
+    return HW_OK;
+}
+
+extern "C" int hw_check_context(const hw_ctx* c) {
+    if (!c) return fail(HW_EINVAL, "hw_check_context: null context");
+    cudaSetDevice(c->device);
+    std::vector<unsigned char> img(c->tables_bytes);
+    cudaError_t e = cudaMemcpy(img.data(), c->tables, c->tables_bytes, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return fail(HW_ECUDA, "hw_check_context: copy failed: %s", cudaGetErrorString(e));
+    if (fnv1a(img.data(), img.size()) != c->tables_hash)
+        return fail(HW_EMISMATCH, "hw_check_context: the context's device tables changed since creation");
     return HW_OK;
 }
 

@@ -107,3 +107,17 @@ def test_bad_geometries_rejected_before_cuda(lib):
         h = ctypes.c_void_p()
         assert lib.hw_create_tuned(ctypes.byref(p), ctypes.byref(g), 0, ctypes.byref(h)) == -1, geo
         assert lib.hw_last_error()
+
+
+def test_buffer_arguments_must_be_tensors():
+    """A number where a buffer belongs is refused on the host, before it can
+    reach a kernel as a device address."""
+    import torch
+    from paper_2403_20190_gb300 import binding
+    with pytest.raises(binding.HwError):
+        binding._ptr(64)
+    assert binding._ptr(None) is None
+    t = torch.zeros(4, dtype=torch.int64)
+    assert binding._ptr(t).value == t.data_ptr()
+    with pytest.raises(binding.HwError):
+        binding._ptr(torch.zeros(4, 4)[:, 1])

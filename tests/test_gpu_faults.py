@@ -29,3 +29,15 @@ def test_allocation_failures_leave_nothing_behind(monkeypatch):
     assert free0 - free1 < (8 << 20), "a failed creation leaked device memory"
     ctx = B.hw_create(cfg, 0)  # the device still serves a new context
     assert B.hw_get_sizes(ctx)["n"] == 4096
+
+
+def test_context_self_check_passes_after_work():
+    """hw_check_context: the tables a context uploaded are unchanged after a
+    full encrypt / train / infer pipeline on it and on another context."""
+    from paper_2403_20190_gb300 import binding as B
+    from test_gpu_parity import run_pipeline, tiny_cfg
+    R = run_pipeline(get_config("cfg1"), 3, 2)
+    B.hw_check_context(R["sess"].ctx)
+    other = run_pipeline(tiny_cfg("zgtL"), 3, 2)
+    B.hw_check_context(other["sess"].ctx)
+    B.hw_check_context(R["sess"].ctx)
