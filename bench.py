@@ -260,24 +260,40 @@ def workload_name(cfg):
 
 # ------------------------------------------------------------ the GPU arm
 def algorithmic_counts(sess, cfg):
+    """algorithmic_work() for a context: its sizes and RAM bit table."""
+    from paper_2403_20190_gb300 import binding as B
+    return algorithmic_work(sess.sz, B.hw_get_ram_slots(sess.ctx), cfg.n_classes)
+
+
+def algorithmic_work(sz, slots, l):
     """Modular multiplications of the VP kernel per test sample and of the
     IVP kernel per train sample, counted from the algorithm: every external
     product runs 2*dnum*r forward and 2*r inverse transforms of (N/2) log2 N
-    butterflies each, and 2*(2*dnum)*r*N products in evaluation form."""
-    from paper_2403_20190_gb300 import binding as B
-    sz = sess.sz
-    n, r, dnum, L, z, a, k0, l = (sz["n"], sz["r"], sz["dnum"], sz["L"], sz["z"], sz["a"],
-                                  sz["k0"], cfg.n_classes)
+    butterflies each, and 2*(2*dnum)*r*N products in evaluation form.
+    slots[j*a + i] is the encrypted bit slot of RAM j's address bit i (-1: a
+    constant 0, which costs no external product)."""
+    n, r, dnum, L, z, a, k0 = (sz["n"], sz["r"], sz["dnum"], sz["L"], sz["z"], sz["a"], sz["k0"])
     logn = n.bit_length() - 1
     bfly = (n // 2) * logn
     per_ext = 2 * dnum * r * bfly + 2 * r * bfly + 2 * 2 * dnum * r * n
-    slots = B.hw_get_ram_slots(sess.ctx)
+    # the pruned CDEMUX tree: gate (level i, j) runs iff a stored index v has
+    # v mod 2^(i+1) = j + 2^i (its control is LUT bit i)
+    V = set()
+    for c in range(l):
+        for x in range(1 << max(0, z - L)):
+            V.add((c + (x << L)) % (1 << z))
+    gate_levels = [i for i in range(z) for jj in range(1 << i)
+                   if any(v % (1 << (i + 1)) == jj + (1 << i) for v in V)]
     ext_train = ext_infer = ext_clear = 0
     for j in range(k0):
         enc = [slots[j * a + i] >= 0 for i in range(a)]
-        # training: rotation bits z..L+a-1 that are encrypted (labels always are)
-        rot = sum(1 for t in range(z, L + a) if (t < L or enc[t - L]))
-        ext_train += rot
+
+        def encrypted(t):  # LUT bit t: label bits are always encrypted
+            return t < L or enc[t - L]
+        # training: encrypted rotation bits z..L+a-1, then the gates whose
+        # control is encrypted
+        ext_train += sum(1 for t in range(z, L + a) if encrypted(t))
+        ext_train += sum(1 for i in gate_levels if encrypted(i))
         # inference: encrypted address bits among the rotation bits, plus a tree CMUX if z > L
         rot_i = sum(1 for t in range(max(z, L), L + a) if enc[t - L])
         tree_i = 1 if (z > L and enc[z - 1 - L]) else 0
@@ -287,14 +303,6 @@ def algorithmic_counts(sess, cfg):
         # class when zt = 1
         zt = max(0, z - L)
         ext_clear += sum(1 for i in range(zt, a) if enc[i]) + (l if zt and enc[0] else 0)
-    # pruned CDEMUX gates per RAM (same for every RAM when their tree bits are encrypted)
-    V = set()
-    for c in range(l):
-        for x in range(1 << max(0, z - L)):
-            V.add((c + (x << L)) % (1 << z))
-    g = sum(1 for i in range(z) for jj in range(1 << i)
-            if any(v % (1 << (i + 1)) == jj + (1 << i) for v in V))
-    ext_train += k0 * g
     return {"per_ext_modmul": per_ext, "ext_train_per_sample": ext_train,
             "ext_infer_per_sample": ext_infer, "ext_clear_per_sample": ext_clear,
             "rgsw_bytes": sz["rgsw_words"] * 8}
