@@ -67,42 +67,54 @@ def thermometer(values: np.ndarray, T: int) -> np.ndarray:
     return bits.reshape(values.shape[0], -1)
 
 
-def encode(P, values: np.ndarray) -> np.ndarray:
+def h3_hash(tuples: np.ndarray, Hm: np.ndarray) -> np.ndarray:
+    """H3 hash of each row of `tuples` (n, tuple_bits) of 0/1 bits:
+    h(x) = XOR of the matrix rows Hm[i] whose bit x_i is 1."""
+    n = tuples.shape[0]
+    h = np.zeros(n, dtype=np.int64)
+    for i in range(tuples.shape[1]):
+        h ^= np.where(tuples[:, i] == 1, int(Hm[i]), 0)
+    return h
+
+
+def encode(P, values: np.ndarray, perm=None, h3=None) -> np.ndarray:
     """Data bits the client encrypts, shape (n, n_data).  Plain workloads
     send the thermometer bits in their original order (the server applies
     pi_r); hashed workloads apply pi_r, cut a tuple of tuple_bits per RAM
-    and send its addr_bits hash, h(x) = XOR of H3 rows i with x_i = 1."""
+    and send its addr_bits hash, h(x) = XOR of H3 rows i with x_i = 1, hash
+    bit i as the RAM's address bit i.  perm / h3 replace the seeded pi_r /
+    H3 matrix (worked examples)."""
     cfg = P.cfg
     tb = thermometer(values, cfg.therm_bits)
     if not cfg.hash_h3:
         return tb
-    perm = permutation(cfg.model_seed, P.s)
+    if perm is None:
+        perm = permutation(cfg.model_seed, P.s)
     t = tb[:, perm]
-    Hm = h3_matrix(cfg.model_seed, cfg.tuple_bits, P.a)
+    Hm = h3_matrix(cfg.model_seed, cfg.tuple_bits, P.a) if h3 is None else np.asarray(h3, dtype=np.int64)
     n = values.shape[0]
     out = np.zeros((n, P.k0 * P.a), dtype=np.uint8)
     for j in range(P.k0):
         lo = j * cfg.tuple_bits
-        tup = t[:, lo:lo + cfg.tuple_bits]
-        h = np.zeros(n, dtype=np.int64)
-        for i in range(tup.shape[1]):
-            h ^= np.where(tup[:, i] == 1, Hm[i], 0)
+        h = h3_hash(t[:, lo:lo + cfg.tuple_bits], Hm)
         for i in range(P.a):
             out[:, j * P.a + i] = (h >> i) & 1
     return out
 
 
-def ram_bits(P) -> np.ndarray:
+def ram_bits(P, perm=None) -> np.ndarray:
     """For RAM j and address bit i, the index of the data bit it reads, or -1
     for the constant-0 bits that pad a short last tuple.  The tuple of RAM j
-    is t_{ja} .. t_{ja+a-1} of the permuted input (Definition 1, f_comp)."""
+    is t_{ja} .. t_{ja+a-1} of the permuted input t_p = T_{perm[p]}
+    (Definition 1, f_comp); perm defaults to the seeded pi_r."""
     cfg = P.cfg
     tab = np.full((P.k0, P.a), -1, dtype=np.int64)
     if cfg.hash_h3:
         for j in range(P.k0):
             tab[j] = j * P.a + np.arange(P.a)
         return tab
-    perm = permutation(cfg.model_seed, P.s)
+    if perm is None:
+        perm = permutation(cfg.model_seed, P.s)
     for j in range(P.k0):
         for i in range(P.a):
             idx = j * P.a + i
@@ -111,9 +123,9 @@ def ram_bits(P) -> np.ndarray:
     return tab
 
 
-def addresses(P, data_bits: np.ndarray) -> np.ndarray:
+def addresses(P, data_bits: np.ndarray, perm=None) -> np.ndarray:
     """f_comp for every RAM: address = sum_i bit_i 2^i, shape (n, k0)."""
-    tab = ram_bits(P)
+    tab = ram_bits(P, perm)
     n = data_bits.shape[0]
     addr = np.zeros((n, P.k0), dtype=np.int64)
     for i in range(P.a):
@@ -125,10 +137,10 @@ def addresses(P, data_bits: np.ndarray) -> np.ndarray:
     return addr
 
 
-def integer_wisard_train(P, data_bits, labels) -> np.ndarray:
+def integer_wisard_train(P, data_bits, labels, perm=None) -> np.ndarray:
     """Algorithm 4: W[L_i][j][f_comp(t, j)] += 1; W has shape (l, k0, 2^a)."""
     W = np.zeros((P.cfg.n_classes, P.k0, 1 << P.a), dtype=np.int64)
-    addr = addresses(P, data_bits)
+    addr = addresses(P, data_bits, perm)
     for i in range(data_bits.shape[0]):
         W[labels[i], np.arange(P.k0), addr[i]] += 1
     return W
