@@ -8,7 +8,8 @@ model per configuration resident in HBM and runs a loop that
     scratch) fits in the free budget,
   * groups admitted requests of the same (configuration, kind) into one
     batched launch on a free CUDA stream, so batches of different models
-    overlap on the device,
+    overlap on the device; a model has at most one training batch in
+    flight (training adds into the model's delta in place),
   * retires batches whose completion events have fired and records each
     request's latency (arrival to completion).
 
@@ -211,11 +212,15 @@ class Server:
         per = self.cost.get((rm.cfg.name, kind))
         return n * (per if per is not None else rm.prior_cost(kind))
 
-    def _groups(self, pending):
+    def _groups(self, pending, training=()):
         """Candidate batches: per (configuration, kind), pending requests in
-        arrival order up to the batch limit."""
+        arrival order up to the batch limit.  Models named in `training`
+        have a training batch in flight: their training requests wait, since
+        two training batches of one model would both add into its delta."""
         groups = {}
         for r in pending:
+            if r.kind == "train" and r.cfg_name in training:
+                continue
             key = (r.cfg_name, r.kind)
             g = groups.setdefault(key, [[], 0])
             if g[1] + r.n > self.max_batch and g[0]:
@@ -250,7 +255,8 @@ class Server:
             while pending and free_streams:
                 now = time.perf_counter() - t0
                 ranked = []
-                for (nm, kind), (group, n) in self._groups(pending).items():
+                training = {b.rm.cfg.name for b in inflight if b.kind == "train"}
+                for (nm, kind), (group, n) in self._groups(pending, training).items():
                     rm = self.models[nm]
                     oldest = min(r.t_arrive for r in group)
                     score = self.expected(rm, kind, n) - self.aging * (now - oldest)

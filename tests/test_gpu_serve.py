@@ -120,3 +120,36 @@ def test_admission_respects_the_budget():
         Server(models, hbm_budget_bytes=one - 1).run(
             [Request(rid=9, t_arrive=0.0, cfg_name="cfg1", kind="train", values=v, labels=lab, seed=1)],
             realtime=False)
+
+
+def test_training_batches_of_one_model_never_overlap():
+    """Many small training requests for one model, several free streams and
+    a small batch limit: the server must not run two training batches of the
+    model at once (both would add into its delta).  The mixed delta equals
+    the sum of the deltas of the requests trained alone."""
+    from paper_2403_20190_gb300 import build
+    from paper_2403_20190_gb300.merge import add_models
+    from paper_2403_20190_gb300.serve import Request, Server
+    build.build()
+    cfgs = {"tiny_rns": _configs()["tiny_rns"]}
+    models = _models(cfgs, pretrain=False)
+    rm = models["tiny_rns"]
+    v, lab = make_dataset(cfgs["tiny_rns"], "train", n=24, seed=5)
+    reqs = [Request(rid=i, t_arrive=0.0, cfg_name="tiny_rns", kind="train",
+                    values=np.ascontiguousarray(v[2 * i:2 * i + 2]),
+                    labels=np.ascontiguousarray(lab[2 * i:2 * i + 2]), seed=100 + i)
+            for i in range(12)]
+    srv = Server(models, hbm_budget_bytes=4 << 30, n_streams=4, max_batch_samples=2)
+    srv.run(reqs, realtime=False)
+    torch.cuda.synchronize()
+    mixed = rm.delta.clone()
+    q, n = rm.sess.sz["q"], rm.sess.sz["n"]
+    total = torch.zeros_like(mixed)
+    for r in reqs:
+        rm.delta.zero_()
+        Server(models, hbm_budget_bytes=1 << 30, n_streams=1).run([Request(
+            rid=r.rid, t_arrive=0.0, cfg_name=r.cfg_name, kind="train", values=r.values,
+            labels=r.labels, seed=r.seed)], realtime=False)
+        total = add_models(total, rm.delta, q, n)
+    torch.cuda.synchronize()
+    assert torch.equal(mixed, total)

@@ -77,3 +77,13 @@ def test_latency_statistics():
     assert st["samples"] == 20 and st["requests"] == 10
     assert abs(st["span_s"] - (0.9 + 0.1)) < 1e-9
     assert abs(st["samples_per_s"] - 20 / 1.0) < 1e-9
+
+
+def test_a_model_with_training_in_flight_gets_no_second_training_batch():
+    srv = _server(max_batch=4)
+    pending = [_req(0, 0.0, "cfg1", "train", 2), _req(1, 0.1, "cfg1", "infer", 2),
+               _req(2, 0.2, "cfg2", "train", 2)]
+    g = srv._groups(pending, training={"cfg1"})
+    assert sorted(g) == [("cfg1", "infer"), ("cfg2", "train")]
+    g = srv._groups(pending)
+    assert ("cfg1", "train") in g
