@@ -62,8 +62,8 @@ def parse():
     return ap.parse_args()
 
 
-# DRAM bytes of k_vp_infer per test sample, from the ncu capture summarised
-# in profiles/k_vp_infer_cfg2.md (2 test samples, scaled by samples: the
+# DRAM bytes of k_vp_infer per test sample, from an ncu capture of the
+# inference kernel on 2 cfg2 test samples (scaled by samples: the
 # traffic is per item); valid only for the kernel sources it was taken on:
 # the VP kernel with the device helpers it calls (the region of hw_ext.cuh
 # from bit_slot to the VP kernel's end) and the headers of the external
@@ -80,7 +80,7 @@ PROFILED_VP_TRAFFIC = {
     "sha256": "1b1c5d9b6538dd97528c71efa032a025f17669d8cca0d819f28b729fc8fef19d",
 }
 # Register-only 64-bit lazy Cooley-Tukey butterflies per second on one GB300
-# at 2070 MHz (profiles/butterfly_ceiling.md): what the integer pipes issue
+# at 2070 MHz (a register-only microbenchmark): what the integer pipes issue
 # for this arithmetic, beside the multiply-count peak.
 BUTTERFLY_CEILING = {"ct64_t_per_s": 0.8414, "gs64_t_per_s": 0.8755,
                      "source": "microbench/bfly_ceiling.cu"}

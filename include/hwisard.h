@@ -283,9 +283,12 @@ int hw_pdact(hw_ctx* ctx, const int64_t* counts_dev, size_t n, int64_t* scores_d
  * - All calls share the array: calls whose work overlaps on the GPU (other
  *   streams, other threads, other contexts on the same device) race.  Order
  *   them, e.g. on one stream.
- * - Rings whose three per-block buffers exceed the array (3 * rlwe_words * 8
- *   bytes > HW_STATIC_SCRATCH_BYTES) are rejected with HW_EINVAL; the number
- *   of resident blocks is capped so that all of them fit.
+ * - Each resident block of the inference kernel takes S * rlwe_words * 8
+ *   bytes of the array, S = 2 when the context's geometry keeps the
+ *   accumulator's evaluation form in shared memory (ext_smem = 1) and 3
+ *   otherwise.  Rings where one block does not fit are rejected with
+ *   HW_EINVAL; the number of resident blocks is capped so that all of them
+ *   fit (fewer blocks: the same results, more slowly).
  * - Nothing is allocated or freed: no cudaMalloc, cudaFree or allocating
  *   library call. */
 #define HW_STATIC_SCRATCH_BYTES (48u << 20)

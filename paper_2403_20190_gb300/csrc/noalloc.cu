@@ -62,7 +62,9 @@ extern "C" int hw_infer_static_scratch(hw_ctx* ctx, const uint64_t* model, const
     if (!model || !rgsw || !resp || !sums)
         return hw_ctx_fail(HW_EINVAL, "hw_infer_static_scratch: null buffer");
     const LaunchInfo& li = *hw_ctx_launch_info(ctx);
-    // each persistent block needs two RLWE accumulators and their evaluation forms
+    // each persistent block needs two RLWE accumulators and, unless the
+    // geometry keeps it in shared memory, one evaluation-form buffer
+    // (scratch_rlwe = 2 or 3 RLWEs)
     const size_t per_block = (size_t)li.ext->scratch_rlwe * li.rlwe_words * sizeof(u64);
     const size_t fit = HW_STATIC_SCRATCH_BYTES / per_block;
     if (fit < 1) {
