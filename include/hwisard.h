@@ -51,8 +51,9 @@ extern "C" {
 #define HW_ACT_BIN 2
 
 /* What hw_decrypt decrypts. */
-#define HW_DEC_RLWE 0 /* count RLWE ciphertexts -> count*N values */
-#define HW_DEC_LWE 1  /* count LWE ciphertexts  -> count values */
+#define HW_DEC_RLWE 0  /* count RLWE ciphertexts -> count*N values */
+#define HW_DEC_LWE 1   /* count LWE ciphertexts  -> count values */
+#define HW_DEC_MODEL 2 /* one model H -> its l*k0*2^a counters W[c][j][addr] */
 
 typedef struct hw_params {
     int32_t log_n;      /* ring dimension N = 2^log_n, 10 <= log_n <= 13 */
@@ -260,9 +261,54 @@ int hw_infer_plain(hw_ctx* ctx, const uint64_t* plain_dev, const uint64_t* rgsw_
 /* DecRLWE / DecLWE (Section 2.4): phase b - a*s combined over the primes by
  * the CRT and rounded, m = floor((p*phi + floor(Q/2)) / Q) mod p.  what =
  * HW_DEC_RLWE: obj_dev holds count RLWEs, out_dev gets count*N values;
- * HW_DEC_LWE: count LWEs, count values.  out_dev: int64 device array. */
+ * HW_DEC_LWE: count LWEs, count values; HW_DEC_MODEL: obj_dev is one model
+ * (count = 1), out_dev gets its l*k0*2^a counters [class][RAM][address]
+ * (see hw_model_words).  out_dev: int64 device array. */
 int hw_decrypt(hw_ctx* ctx, const uint64_t* key_dev, int what, const uint64_t* obj_dev,
                size_t count, int64_t* out_dev, void* stream);
+
+/* The model H of Definition 2: k0 RAMs x k1 stored RLWEs (the LUT index
+ * m = c + 2^L addr of class c, address addr -- label bits low, as
+ * Algorithm 6 orders the bits -- is coefficient m >> z of stored ciphertext
+ * slot(m mod 2^z); only the slots a label < l reaches are stored).  The
+ * model is a caller buffer of hw_model_words(ctx) device words.
+ * hw_model_zero: H <- {0} (Algorithm 6's initial model: trivial encryptions
+ * of 0), on the stream.
+ * hw_decrypt(..., HW_DEC_MODEL, model_dev, 1, out_dev, ...) writes the
+ * l * k0 * 2^a counters [class c][RAM j][address] (Algorithm 4's W after
+ * homomorphic training), int64 in [0, p). */
+size_t hw_model_words(const hw_ctx* ctx);
+int hw_model_zero(hw_ctx* ctx, uint64_t* model_dev, void* stream);
+
+/* Exported model (no counterpart in the paper; the model is additive,
+ * Section 3.6.2, so training can stop after any batch and resume from the
+ * saved model with bit-identical results).  Layout, uint64 words:
+ *   [0] HW_MODEL_MAGIC  [1] HW_MODEL_VERSION  [2] hw_params_digest
+ *   [3] samples trained (the caller's count, stored as given)
+ *   [4] k0  [5] k1  [6] r  [7] N  [8] model words M
+ *   then the M canonical words of H ([RAM][slot][RLWE], residues < q_i).
+ * hw_model_export: model_dev -> out_host (hw_model_export_words(ctx)
+ * words); synchronous (waits for the stream).
+ * hw_model_import: in_host -> model_dev after checking the header (magic,
+ * version, the parameter digest: HW_EMISMATCH for another parameter set,
+ * the shape) and that every word is reduced mod its prime (HW_EINVAL);
+ * *samples gets the stored count.  Synchronous.
+ * hw_model_header_check: the header checks alone, host only (no context,
+ * no GPU): HW_EINVAL (not a model, other version, word count),
+ * HW_EMISMATCH (other parameters).
+ * hw_params_digest: FNV-1a 64 over every hw_params field but `reserved`
+ * (each as a little-endian 64-bit word, model_seed last); host only. */
+#define HW_MODEL_MAGIC 0x3144524153495748ULL /* "HWISARD1" little-endian */
+#define HW_MODEL_VERSION 1
+#define HW_MODEL_HEADER_WORDS 9
+int hw_params_digest(const hw_params* params, uint64_t* out);
+size_t hw_model_export_words(const hw_ctx* ctx);
+int hw_model_export(hw_ctx* ctx, const uint64_t* model_dev, uint64_t samples, uint64_t* out_host,
+                    size_t n_words, void* stream);
+int hw_model_import(hw_ctx* ctx, const uint64_t* in_host, size_t n_words, uint64_t* model_dev,
+                    uint64_t* samples, void* stream);
+int hw_model_header_check(const hw_params* params, const uint64_t* in_host, size_t n_words,
+                          uint64_t* samples);
 
 /* PD-act (Section 3.5.1): counts_dev [n][l][k0] decrypted responses ->
  * scores_dev [n][l] (sum of activated counts) and labels_dev [n] (arg-max,

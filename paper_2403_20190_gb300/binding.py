@@ -18,6 +18,12 @@ HW_OK = 0
 HW_ACT = {"log": 0, "blog": 1, "bin": 2}
 HW_DEC_RLWE = 0
 HW_DEC_LWE = 1
+HW_DEC_MODEL = 2
+HW_EINVAL = -1
+HW_EMISMATCH = -5
+HW_MODEL_MAGIC = 0x3144524153495748
+HW_MODEL_VERSION = 1
+HW_MODEL_HEADER_WORDS = 9
 
 
 class HwParams(ctypes.Structure):
@@ -50,7 +56,9 @@ class HwTuneEntry(ctypes.Structure):
 
 
 class HwError(RuntimeError):
-    pass
+    def __init__(self, msg, code=None):
+        super().__init__(msg)
+        self.code = code
 
 
 _VP = ctypes.c_void_p
@@ -91,6 +99,13 @@ _SIGS = {
     "hw_pack_responses": (ctypes.c_int, [_VP, _VP, _VP, _SZ, _VP, _VP, _SZ, _VP]),
     "hw_count_classes": (ctypes.c_int, [_VP, _VP, _VP, _SZ, _VP, _SZ, _VP]),
     "hw_pdact_balanced": (ctypes.c_int, [_VP, _VP, _VP, _SZ, _VP, _VP, _VP]),
+    "hw_model_words": (_SZ, [_VP]),
+    "hw_model_zero": (ctypes.c_int, [_VP, _VP, _VP]),
+    "hw_params_digest": (ctypes.c_int, [ctypes.POINTER(HwParams), ctypes.POINTER(_U64)]),
+    "hw_model_export_words": (_SZ, [_VP]),
+    "hw_model_export": (ctypes.c_int, [_VP, _VP, _U64, _VP, _SZ, _VP]),
+    "hw_model_import": (ctypes.c_int, [_VP, _VP, _SZ, _VP, ctypes.POINTER(_U64), _VP]),
+    "hw_model_header_check": (ctypes.c_int, [ctypes.POINTER(HwParams), _VP, _SZ, ctypes.POINTER(_U64)]),
     "hw_ntt_forward": (ctypes.c_int, [_VP, _VP, _SZ, _VP]),
     "hw_ntt_inverse": (ctypes.c_int, [_VP, _VP, _SZ, _VP]),
     "hw_launch_count": (_U64, [_VP]),
@@ -125,7 +140,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
 def _check(rc, what):
     if rc != HW_OK:
         msg = load().hw_last_error().decode(errors="replace")
-        raise HwError(f"{what} failed ({rc}): {msg}")
+        raise HwError(f"{what} failed ({rc}): {msg}", rc)
 
 
 def _ptr(t):
@@ -363,6 +378,55 @@ def hw_count_classes(ctx, counts, rgsw, n, scratch, stream=None):
 def hw_pdact_balanced(ctx, counts, class_counts, n, scores, labels, stream=None):
     _check(load().hw_pdact_balanced(ctx.handle, _ptr(counts), _ptr(class_counts), n, _ptr(scores), _ptr(labels),
                                     _stream(stream)), "hw_pdact_balanced")
+
+
+def hw_model_words(ctx) -> int:
+    return int(load().hw_model_words(ctx.handle))
+
+
+def hw_model_zero(ctx, model, stream=None):
+    _check(load().hw_model_zero(ctx.handle, _ptr(model), _stream(stream)), "hw_model_zero")
+
+
+def hw_params_digest(params) -> int:
+    d = _U64(0)
+    _check(load().hw_params_digest(ctypes.byref(_params(params)), ctypes.byref(d)), "hw_params_digest")
+    return int(d.value)
+
+
+def hw_model_export_words(ctx) -> int:
+    return int(load().hw_model_export_words(ctx.handle))
+
+
+def _host_words(a):
+    """A host uint64 numpy array as a buffer argument (contiguous)."""
+    import numpy as np
+    if not (isinstance(a, np.ndarray) and a.dtype == np.uint64 and a.flags["C_CONTIGUOUS"]):
+        raise HwError("host word buffers must be contiguous numpy uint64 arrays")
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def hw_model_export(ctx, model, samples, out, stream=None):
+    """out: numpy uint64 array of hw_model_export_words(ctx) words (host)."""
+    _check(load().hw_model_export(ctx.handle, _ptr(model), int(samples), _host_words(out), out.size,
+                                  _stream(stream)), "hw_model_export")
+
+
+def hw_model_import(ctx, words, model, stream=None) -> int:
+    """words: numpy uint64 array (host); returns the stored sample count."""
+    smp = _U64(0)
+    _check(load().hw_model_import(ctx.handle, _host_words(words), words.size, _ptr(model), ctypes.byref(smp),
+                                  _stream(stream)), "hw_model_import")
+    return int(smp.value)
+
+
+def hw_model_header_check(params, words) -> int:
+    """Host-only header check of exported model words; returns the stored
+    sample count."""
+    smp = _U64(0)
+    _check(load().hw_model_header_check(ctypes.byref(_params(params)), _host_words(words), words.size,
+                                        ctypes.byref(smp)), "hw_model_header_check")
+    return int(smp.value)
 
 
 def hw_ntt_forward(ctx, poly, count, stream=None):

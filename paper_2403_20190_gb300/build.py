@@ -2,7 +2,8 @@
 
 Each .cu translation unit is compiled in parallel into _build/, then linked
 into paper_2403_20190_gb300/_build/libhwisard.so.  A rebuild happens only when
-a source or header is newer than the library.
+a source or header is newer than the library, and recompiles only the units
+whose source (or any header) is newer than their object.
 """
 import concurrent.futures
 import glob
@@ -51,8 +52,16 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     nvcc = _nvcc()
     srcs = _sources()
 
+    headers = [d for d in _deps() if not d.endswith(".cu")]
+    t_headers = max(os.path.getmtime(h) for h in headers)
+
     def compile_one(src):
         obj = os.path.join(OUT, os.path.basename(src)[:-3] + ".o")
+        # an object newer than its source and every header is kept (unless
+        # forced or built with other flags)
+        if (not force and not extra_flags and os.path.exists(obj)
+                and os.path.getmtime(obj) >= max(os.path.getmtime(src), t_headers)):
+            return obj
         cmd = [nvcc, *ARCH, *FLAGS, *extra_flags, "-c", src, "-o", obj]
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode != 0:

@@ -840,6 +840,9 @@ extern "C" int hw_decrypt(hw_ctx* c, const uint64_t* key, int what, const uint64
         CUDA_TRY(launch_decrypt_rlwe(c->li, key, obj, count, out, c->phase_scratch, c->phase_chunk, st));
     } else if (what == HW_DEC_LWE) {
         CUDA_TRY(launch_decrypt_lwe(c->li, key, obj, count, out, st));
+    } else if (what == HW_DEC_MODEL) {
+        if (count != 1) return fail(HW_EINVAL, "hw_decrypt: HW_DEC_MODEL decrypts one model (count = 1)");
+        CUDA_TRY(launch_decrypt_model(c->li, key, obj, c->sz.a, out, c->phase_scratch, c->phase_chunk, st));
     } else {
         return fail(HW_EINVAL, "hw_decrypt: unknown object kind %d", what);
     }
@@ -939,5 +942,103 @@ extern "C" int hw_ntt_inverse(hw_ctx* c, uint64_t* poly, size_t count, void* str
     CHECK_CTX(c);
     if (count && !poly) return fail(HW_EINVAL, "hw_ntt_inverse: null buffer");
     CUDA_TRY(launch_ntt_batch(c->li, poly, count, 1, (cudaStream_t)stream));
+    return HW_OK;
+}
+
+// ------------------------------------------------------------------ model
+// Definition 2's model H as a caller buffer: creation (H <- {0}), and the
+// canonical words with a header naming the parameter set, for saving a
+// model and resuming training elsewhere (the model is additive,
+// Section 3.6.2).
+
+static void digest_word(uint64_t* h, uint64_t v) {
+    for (int b = 0; b < 8; b++) {
+        *h ^= (v >> (8 * b)) & 0xff;
+        *h *= 0x100000001b3ULL;
+    }
+}
+
+extern "C" int hw_params_digest(const hw_params* p, uint64_t* out) {
+    if (!p || !out) return fail(HW_EINVAL, "hw_params_digest: null argument");
+    uint64_t h = 0xcbf29ce484222325ULL;
+    const int32_t f[] = {p->log_n,     p->n_primes,   p->prime_bits, p->log_beta, p->log_p,
+                         p->n_classes, p->n_values,   p->therm_bits, p->tuple_bits, p->addr_bits,
+                         p->hash_h3,   p->act,        p->act_arg};
+    for (int32_t v : f) digest_word(&h, (uint64_t)(int64_t)v);
+    digest_word(&h, p->model_seed);
+    *out = h;
+    return HW_OK;
+}
+
+extern "C" size_t hw_model_words(const hw_ctx* c) { return c ? c->sz.model_words : 0; }
+
+extern "C" int hw_model_zero(hw_ctx* c, uint64_t* model, void* stream) {
+    CHECK_CTX(c);
+    if (!model) return fail(HW_EINVAL, "hw_model_zero: null buffer");
+    CUDA_TRY(cudaMemsetAsync(model, 0, c->sz.model_words * sizeof(u64), (cudaStream_t)stream));
+    return HW_OK;
+}
+
+extern "C" size_t hw_model_export_words(const hw_ctx* c) {
+    return c ? HW_MODEL_HEADER_WORDS + c->sz.model_words : 0;
+}
+
+extern "C" int hw_model_header_check(const hw_params* p, const uint64_t* in, size_t n_words,
+                                     uint64_t* samples) {
+    if (!p || !in) return fail(HW_EINVAL, "hw_model_header_check: null argument");
+    if (n_words < HW_MODEL_HEADER_WORDS || in[0] != HW_MODEL_MAGIC)
+        return fail(HW_EINVAL, "hw_model_header_check: not an exported model");
+    if (in[1] != HW_MODEL_VERSION)
+        return fail(HW_EINVAL, "hw_model_header_check: format version %llu, this library reads %d",
+                    (unsigned long long)in[1], HW_MODEL_VERSION);
+    uint64_t d = 0;
+    hw_params_digest(p, &d);
+    if (in[2] != d) return fail(HW_EMISMATCH, "hw_model_header_check: model made for another parameter set");
+    if (in[8] != (uint64_t)(n_words - HW_MODEL_HEADER_WORDS))
+        return fail(HW_EINVAL, "hw_model_header_check: %zu model words follow the header, it announces %llu",
+                    n_words - HW_MODEL_HEADER_WORDS, (unsigned long long)in[8]);
+    if (samples) *samples = in[3];
+    return HW_OK;
+}
+
+extern "C" int hw_model_export(hw_ctx* c, const uint64_t* model, uint64_t samples, uint64_t* out,
+                               size_t n_words, void* stream) {
+    CHECK_CTX(c);
+    if (!model || !out) return fail(HW_EINVAL, "hw_model_export: null buffer");
+    const size_t need = HW_MODEL_HEADER_WORDS + c->sz.model_words;
+    if (n_words < need) return fail(HW_ENOMEM, "hw_model_export: needs %zu words, got %zu", need, n_words);
+    uint64_t d = 0;
+    hw_params_digest(&c->prm, &d);
+    const uint64_t head[HW_MODEL_HEADER_WORDS] = {HW_MODEL_MAGIC, HW_MODEL_VERSION, d, samples,
+                                                  (uint64_t)c->sz.k0, (uint64_t)c->sz.k1, (uint64_t)c->sz.r,
+                                                  (uint64_t)c->sz.n, (uint64_t)c->sz.model_words};
+    memcpy(out, head, sizeof(head));
+    cudaStream_t st = (cudaStream_t)stream;
+    CUDA_TRY(cudaMemcpyAsync(out + HW_MODEL_HEADER_WORDS, model, c->sz.model_words * sizeof(u64),
+                             cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return HW_OK;
+}
+
+extern "C" int hw_model_import(hw_ctx* c, const uint64_t* in, size_t n_words, uint64_t* model,
+                               uint64_t* samples, void* stream) {
+    CHECK_CTX(c);
+    if (!in || !model) return fail(HW_EINVAL, "hw_model_import: null buffer");
+    uint64_t smp = 0;
+    int rc = hw_model_header_check(&c->prm, in, n_words, &smp);
+    if (rc != HW_OK) return rc;
+    if (in[4] != (uint64_t)c->sz.k0 || in[5] != (uint64_t)c->sz.k1 || in[6] != (uint64_t)c->sz.r ||
+        in[7] != (uint64_t)c->sz.n || in[8] != (uint64_t)c->sz.model_words)
+        return fail(HW_EMISMATCH, "hw_model_import: model shape differs from this context's");
+    // every word is a residue of its prime: [RAM][slot][component][prime][N]
+    const u64* w = in + HW_MODEL_HEADER_WORDS;
+    const size_t n = (size_t)c->sz.n, r = (size_t)c->sz.r;
+    for (size_t i = 0; i < c->sz.model_words; i++)
+        if (w[i] >= c->sz.q[(i / n) % r])
+            return fail(HW_EINVAL, "hw_model_import: word %zu is not reduced mod its prime", i);
+    cudaStream_t st = (cudaStream_t)stream;
+    CUDA_TRY(cudaMemcpyAsync(model, w, c->sz.model_words * sizeof(u64), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (samples) *samples = smp;
     return HW_OK;
 }

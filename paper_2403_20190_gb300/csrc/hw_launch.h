@@ -92,6 +92,9 @@ cudaError_t launch_class_sums(const LaunchInfo& li, const uint64_t* resp, size_t
 cudaError_t launch_decrypt_rlwe(const LaunchInfo& li, const uint64_t* key, const uint64_t* ct,
                                 size_t count, int64_t* out, uint64_t* phase_scratch,
                                 size_t chunk, cudaStream_t st);
+// Definition 2's counters W[c][j][addr] of a whole model (HW_DEC_MODEL).
+cudaError_t launch_decrypt_model(const LaunchInfo& li, const uint64_t* key, const uint64_t* model, int a,
+                                 int64_t* out, uint64_t* phase_scratch, size_t chunk, cudaStream_t st);
 cudaError_t launch_decrypt_lwe(const LaunchInfo& li, const uint64_t* key, const uint64_t* ct,
                                size_t count, int64_t* out, cudaStream_t st);
 cudaError_t launch_pdact(const LaunchInfo& li, const int64_t* counts, size_t n, int64_t* scores,

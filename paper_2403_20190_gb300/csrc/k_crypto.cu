@@ -195,6 +195,31 @@ __global__ void k_decode_phase(const DevCtx* __restrict__ Cp, const u64* __restr
     }
 }
 
+// The counters W[c][j][addr] of Definition 2's model from the phases of
+// RAMs j0 .. j0+nj-1 (ph: [ciphertext (j - j0) * k1 + slot][prime][N]): the
+// LUT index m = c + 2^L addr (label bits low, Algorithm 6) sits in stored
+// ciphertext slot_of[m mod 2^z] at coefficient m >> z.  One thread per
+// counter; out is [class][RAM][address].
+__global__ void k_decode_model(const DevCtx* __restrict__ Cp, const u64* __restrict__ ph, int j0, int nj,
+                               int64_t* __restrict__ out) {
+    const DevCtx& C = *Cp;
+    const size_t A = (size_t)1 << C.a;
+    const size_t total = (size_t)C.n_classes * nj * A;
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const size_t addr = idx % A, rest = idx / A;
+        const int jj = (int)(rest % nj), c = (int)(rest / nj);
+        const u64 m = (u64)c + ((u64)addr << C.L);
+        const int v = (int)(m & (((u64)1 << C.z) - 1));
+        const size_t coef = (size_t)(m >> C.z);
+        const int slot = C.slot_of[v];
+        u64 phi[HW_MAXP];
+        const u64* p = ph + ((size_t)jj * C.k1 + slot) * C.r * C.n + coef;
+        for (int j = 0; j < C.r; j++) phi[j] = p[(size_t)j * C.n];
+        out[((size_t)c * C.k0 + j0 + jj) * A + addr] = decode_residues(C, phi);
+    }
+}
+
 // One block per LWE: phase b' - <a', s> per prime (s is ternary), decode.
 __global__ void k_decrypt_lwe(const DevCtx* __restrict__ Cp, const u64* __restrict__ key,
                               const u64* __restrict__ ct, int64_t* __restrict__ out) {
@@ -451,6 +476,35 @@ cudaError_t launch_decrypt_rlwe(const LaunchInfo& li, const uint64_t* key, const
         if (blocks > (size_t)li.sm_count * 32) blocks = (size_t)li.sm_count * 32;
         k_decode_phase<<<(unsigned)blocks, 256, 0, st>>>(li.dctx, phase_scratch, m,
                                                           out + t0 * li.n);
+        (*li.launches)++;
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// The model's counters: the phases of whole RAMs (as many as the phase
+// scratch holds), then the counters those RAMs store.
+cudaError_t launch_decrypt_model(const LaunchInfo& li, const uint64_t* key, const uint64_t* model, int a,
+                                 int64_t* out, uint64_t* phase_scratch, size_t chunk, cudaStream_t st) {
+    const int rams = (int)(chunk / (size_t)li.k1) < 1 ? 1 : (int)(chunk / (size_t)li.k1);
+    for (int j0 = 0; j0 < li.k0; j0 += rams) {
+        const int nj = li.k0 - j0 < rams ? li.k0 - j0 : rams;
+        const size_t m = (size_t)nj * li.k1;
+#define B(L)                                                                              \
+    case L:                                                                               \
+        k_rlwe_phase<L><<<(unsigned)(m * li.r), Geo<L>::T, Geo<L>::XCHG_BYTES, st>>>(     \
+            li.dctx, key, model + (size_t)j0 * li.k1 * li.rlwe_words, phase_scratch);     \
+        break;
+        HW_DISPATCH(li.log_n, B)
+#undef B
+        (*li.launches)++;
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        const size_t total = (size_t)li.n_classes * nj << a;
+        size_t blocks = (total + 255) / 256;
+        if (blocks > (size_t)li.sm_count * 32) blocks = (size_t)li.sm_count * 32;
+        k_decode_model<<<(unsigned)blocks, 256, 0, st>>>(li.dctx, phase_scratch, j0, nj, out);
         (*li.launches)++;
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;

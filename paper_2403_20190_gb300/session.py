@@ -37,8 +37,11 @@ class Session:
         B.hw_keygen(self.ctx, seed, key, stream)
         return key
 
-    def new_model(self):
-        return self.words(self.sz["model_words"])
+    def new_model(self, stream=None):
+        """Definition 2's model H <- {0} (hw_model_zero)."""
+        model = self.words(B.hw_model_words(self.ctx), zero=False)
+        B.hw_model_zero(self.ctx, model, stream)
+        return model
 
     # ---------------------------------------------------------------- client
     def encode(self, values, stream=None):
@@ -95,19 +98,17 @@ class Session:
 
     # ----------------------------------------------------- checkpoint
     def save_model(self, path, model, samples):
-        """Checkpoint of the model after `samples` training samples."""
+        """Checkpoint of the model after `samples` training samples
+        (hw_model_export)."""
         from .checkpoint import save
-        torch.cuda.synchronize(self.device)
-        save(path, self.cfg, model, samples)
+        save(path, self, model, samples)
 
     def load_model(self, path):
         """(model on this device, samples trained) from a checkpoint of the
-        same parameter set; training continues from it bit-exactly."""
+        same parameter set (hw_model_import); training continues from it
+        bit-exactly."""
         from .checkpoint import load
-        model, samples = load(path, self.cfg, self.device)
-        if model.numel() != self.sz["model_words"]:
-            raise ValueError(f"{path}: {model.numel()} words, the model has {self.sz['model_words']}")
-        return model, samples
+        return load(path, self)
 
     # ---------------------------------------------------------------- client
     def decrypt_rlwe(self, key, obj, count, stream=None):
@@ -170,23 +171,12 @@ class Session:
         return scores.view(n, l), labels
 
     def decrypt_model_counts(self, key, model, stream=None):
-        """Decrypted counters W[c][j][addr] (l, k0, 2^a) from the model."""
+        """Decrypted counters W[c][j][addr] (l, k0, 2^a) from the model
+        (hw_decrypt, HW_DEC_MODEL)."""
         sz = self.sz
-        n, z, L, a = sz["n"], sz["z"], sz["L"], sz["a"]
-        vals = self.decrypt_rlwe(key, model, sz["k0"] * sz["k1"], stream).view(sz["k0"], sz["k1"], n)
-        slot_of = {}
-        k = 0
-        for v in range(1 << z):
-            if any(((c + (x << L)) % (1 << z)) == v for c in range(self.cfg.n_classes)
-                   for x in range(1 << max(0, z - L))):
-                slot_of[v] = k
-                k += 1
-        l = self.cfg.n_classes
-        m = torch.arange(1 << a, device=self.device)[None, :] * (1 << L) + torch.arange(l, device=self.device)[:, None]
-        ct = m % (1 << z)
-        coef = m >> z
-        slot = torch.tensor([slot_of.get(int(v), 0) for v in range(1 << z)], device=self.device)[ct]
-        return vals[:, slot, coef].permute(1, 0, 2).contiguous()
+        out = torch.empty(self.cfg.n_classes * sz["k0"] << sz["a"], dtype=torch.int64, device=self.device)
+        B.hw_decrypt(self.ctx, key, B.HW_DEC_MODEL, model, 1, out, stream)
+        return out.view(self.cfg.n_classes, sz["k0"], 1 << sz["a"])
 
     def responses_counts(self, key, resp, n, stream=None):
         """Decrypted responses u[i][c][j] (n, l, k0)."""

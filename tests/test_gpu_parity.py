@@ -111,7 +111,9 @@ def tiny_full_parity(name, geometry):
     assert np.array_equal(u64(R["sums"]).reshape(osums.shape), osums)
     # decryption and PD-act
     W = wisard.integer_wisard_train(P, obits, R["labels"])
-    assert np.array_equal(sess.decrypt_model_counts(R["key"], R["model"]).cpu().numpy(), W)
+    dec = sess.decrypt_model_counts(R["key"], R["model"]).cpu().numpy()
+    assert np.array_equal(dec, o.decrypt_model(s, H))  # HW_DEC_MODEL, element by element
+    assert np.array_equal(dec, W)
     counts = sess.responses_counts(R["key"], R["resp"], 3)
     assert np.array_equal(counts.cpu().numpy(), wisard.lookups(P, W, otb))
     sums_dec = sess.decrypt_lwe(R["key"], R["sums"], 3 * cfg.n_classes).view(3, cfg.n_classes)
@@ -229,12 +231,14 @@ def workload_sampled_parity(name, n_train, n_test, rams, geometry):
     assert np.array_equal(gresp[:, :, rams], oresp)
 
 
-@pytest.mark.parametrize("name,n_train,n_test", [("cfg1", 200, 100), ("cfg2", 64, 32)])
+@pytest.mark.parametrize("name,n_train,n_test", [("cfg1", 200, 100), ("cfg2", 64, 32), ("cfg3", 16, 16),
+                                                  ("cfg4", 4, 4)])
 def test_batch_invariants(name, n_train, n_test):
-    """At batch size: decrypted counters == Algorithm 4 counts for every RAM,
-    decrypted responses == plaintext lookups, class sums == Algorithm 2 scores
-    (cfg2; cfg1's 30-bit modulus leaves class sums undecodable by design),
-    PD-act labels == plaintext labels."""
+    """At batch size (cfg3 and cfg4: the bench's batches): decrypted
+    counters == Algorithm 4 counts for every RAM, decrypted responses ==
+    plaintext lookups, class sums == Algorithm 2 scores (cfg2-4; cfg1's
+    30-bit modulus leaves class sums undecodable by design), PD-act labels
+    == plaintext labels."""
     cfg = get_config(name)
     o = Oracle(cfg)
     P = o.P

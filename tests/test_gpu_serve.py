@@ -37,17 +37,18 @@ def _configs():
     return out
 
 
-def _models(cfgs, pretrain=True):
+def _models(cfgs, pretrain=True, n_pre=8):
     from paper_2403_20190_gb300.serve import ResidentModel
     models = {}
     for k, (nm, cfg) in enumerate(sorted(cfgs.items())):
         rm = ResidentModel(cfg, 0, key_seed=40 + k)
         if pretrain:
             s = rm.sess
-            v, lab = make_dataset(cfg, "train", n=8, seed=11)
+            v, lab = make_dataset(cfg, "train", n=n_pre, seed=11)
             bits = s.encode(torch.from_numpy(v).to(s.device))
             rg = s.encrypt(rm.key, bits, torch.from_numpy(lab.astype(np.int32)).to(s.device), seed=5)
-            s.train(rm.model, rg, 8)
+            s.train(rm.model, rg, n_pre)
+            del rg
         models[nm] = rm
     torch.cuda.synchronize()
     return models
@@ -55,16 +56,28 @@ def _models(cfgs, pretrain=True):
 
 @pytest.mark.parametrize("packed", [False, True])
 def test_alone_equals_in_the_mix(packed):
+    alone_equals_in_the_mix(_configs(), {"tiny_rns": 8, "tiny_tree": 8, "cfg1": 16}, n_requests=18,
+                            budget=8 << 30, n_pre=8, packed=packed)
+
+
+def test_alone_equals_in_the_mix_workload_rings():
+    """The digit workload (N = 4096, two primes) and the skewed colour
+    workload (N = 8192, three primes, an encrypted tree level) in one
+    stream with cfg1: 1-2 samples per request for cfg2, 1 for cfg4."""
+    cfgs = {nm: get_config(nm) for nm in ("cfg1", "cfg2", "cfg4")}
+    alone_equals_in_the_mix(cfgs, {"cfg1": 16, "cfg2": 2, "cfg4": 1}, n_requests=10,
+                            budget=64 << 30, n_pre=2, packed=False, seed=4)
+
+
+def alone_equals_in_the_mix(cfgs, max_samples, n_requests, budget, n_pre, packed, seed=9):
     from paper_2403_20190_gb300 import build
     from paper_2403_20190_gb300.merge import add_models
     from paper_2403_20190_gb300.serve import Server, poisson_stream
     build.build()
-    cfgs = _configs()
-    mixed_models = _models(cfgs)
+    mixed_models = _models(cfgs, n_pre=n_pre)
     base = {nm: rm.model.clone() for nm, rm in mixed_models.items()}
-    reqs = poisson_stream(cfgs, n_requests=18, rate=200.0, seed=9,
-                          max_samples={"tiny_rns": 8, "tiny_tree": 8, "cfg1": 16})
-    srv = Server(mixed_models, hbm_budget_bytes=8 << 30, n_streams=4, max_batch_samples=64,
+    reqs = poisson_stream(cfgs, n_requests=n_requests, rate=200.0, seed=seed, max_samples=max_samples)
+    srv = Server(mixed_models, hbm_budget_bytes=budget, n_streams=4, max_batch_samples=64,
                  keep_responses=True, packed_infer=packed)
     done = srv.run(reqs, realtime=False)
     assert all(r.t_done is not None for r in done)
@@ -72,7 +85,8 @@ def test_alone_equals_in_the_mix(packed):
     assert batched > 0 and any(r.kind == "train" for r in done)
 
     from paper_2403_20190_gb300.arena import DeviceArena
-    arena = DeviceArena(8 << 30, torch.device("cuda", 0))
+    del srv
+    arena = DeviceArena(budget, torch.device("cuda", 0))
     alone_models = _models(cfgs, pretrain=False)
     for nm in cfgs:
         alone_models[nm].model.copy_(base[nm])
