@@ -4,10 +4,14 @@
 A step is one pass of the whole path over one batch: B training samples are
 encoded, RGSW-encrypted and trained into the resident model (IVP +
 accumulate), and B test samples are encoded, encrypted, inferred (VP,
-ExtractLWE, class sums), decrypted and classified with PD-act.  The workload
-is the batched 10-class 28x28 digit configuration (N = 4096, two ~50-bit RNS
-primes, 131 RAMs of 2^12 entries).  Raw samples sit in HBM before the timed
-region; encrypted batches (~50 GB per step) are far larger than L2.
+ExtractLWE, class sums), decrypted and classified with PD-act.  The headline
+workload is the at-scale digit configuration (10 classes, 28x28 images,
+3-level thermometer, 16-bit tuples H3-hashed to 12 address bits, N = 8192,
+three ~55-bit RNS primes; B = 16).  Raw samples sit in HBM before the timed
+region; encrypted batches (~125 GB per step) are far larger than L2.
+`per_config` in the same line repeats a shorter measurement on the other
+workloads (the 2-class feature set, the 10-class digits at N = 4096 and the
+7-class colour images at N = 8192).
 
 --impl reference times the CPU oracle on the host cores instead, on a
 bounded sample of the same workload.
@@ -37,6 +41,13 @@ MULS_PER_MODMUL = 10
 # half of x*w'), for contexts whose external products run in 32-bit words.
 MULS_PER_MODMUL32 = 3
 
+DEFAULT_CONFIG = "cfg3"
+# samples per step: cfg1's whole test set; for the larger rings, what keeps one
+# encrypted batch (786 MiB, 3.9 GiB, 15.5 GiB per sample) plus scratch well
+# inside HBM
+DEFAULT_BATCH = {"cfg1": 100, "cfg2": 64, "cfg3": 16, "cfg4": 4}
+ALL_CONFIGS = ("cfg1", "cfg2", "cfg3", "cfg4")
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -44,9 +55,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--config", default="cfg2")
+    ap.add_argument("--config", default=DEFAULT_CONFIG)
     ap.add_argument("--batch", type=int, default=0,
                     help="samples per step (0: the workload's default, sized to fit HBM)")
+    ap.add_argument("--per-config-steps", type=int, default=3,
+                    help="timed steps of each other workload in per_config (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-ntt", action="store_true")
@@ -62,37 +75,27 @@ def parse():
     return ap.parse_args()
 
 
-# DRAM bytes of k_vp_infer per test sample, from an ncu capture of the
-# inference kernel on 2 cfg2 test samples (scaled by samples: the
-# traffic is per item); valid only for the kernel sources it was taken on:
-# the VP kernel with the device helpers it calls (the region of hw_ext.cuh
-# from bit_slot to the VP kernel's end) and the headers of the external
-# product and the modular arithmetic.
-PROFILED_VP_TRAFFIC = {
-    "config": "cfg2", "ext_loge": 3, "ext_np": 2, "ext_smem": 1, "ext_blocks_per_sm": 1, "l2_persist": 0,
-    "bytes_per_test_sample": 2.1133e9,
-    "sources": (("paper_2403_20190_gb300/csrc/hw_ext.cuh", "// Encrypted bit slot that drives",
-                 "// EncRGSW."),
-                ("paper_2403_20190_gb300/csrc/hw_ext.cuh", "// ExtractLWE(ct, k) written by the block",
-                 "// Dataset balancing (Section 3.6.1)"),
-                ("paper_2403_20190_gb300/csrc/hw_internal.cuh", None, None),
-                ("paper_2403_20190_gb300/csrc/modarith.cuh", None, None)),
-    "sha256": "1b1c5d9b6538dd97528c71efa032a025f17669d8cca0d819f28b729fc8fef19d",
-}
-# Register-only 64-bit lazy Cooley-Tukey butterflies per second on one GB300
-# at 2070 MHz (a register-only microbenchmark): what the integer pipes issue
-# for this arithmetic, beside the multiply-count peak.
-BUTTERFLY_CEILING = {"ct64_t_per_s": 0.8414, "gs64_t_per_s": 0.8755,
-                     "source": "microbench/bfly_ceiling.cu"}
-BUTTERFLY_CEILING32 = {"ct32_t_per_s": 3.1435, "gs32_t_per_s": 3.0782,
-                       "source": "microbench/bfly_ceiling.cu"}
+# DRAM bytes of the VP inference kernel per test sample, from ncu captures of
+# small cases of each workload (scaled by samples: the traffic is per item);
+# valid only for the kernel sources they were taken on: the VP kernel with
+# the device helpers it calls (the region of hw_ext.cuh from bit_slot to the
+# VP kernel's end) and the headers of the external product and the modular
+# arithmetic.  Filled per (workload, geometry) when a capture of the current
+# sources exists.
+PROFILED_VP_TRAFFIC = []
+PROFILED_SOURCES = (("paper_2403_20190_gb300/csrc/hw_ext.cuh", "// Encrypted bit slot that drives",
+                     "// EncRGSW."),
+                    ("paper_2403_20190_gb300/csrc/hw_ext.cuh", "// ExtractLWE(ct, k) written by the block",
+                     "// Dataset balancing (Section 3.6.1)"),
+                    ("paper_2403_20190_gb300/csrc/hw_internal.cuh", None, None),
+                    ("paper_2403_20190_gb300/csrc/modarith.cuh", None, None))
 
 
 def profiled_sources_sha(root=None):
     """sha256 over the profiled source regions (whole file where no markers)."""
     import hashlib
     h = hashlib.sha256()
-    for f, start, end in PROFILED_VP_TRAFFIC["sources"]:
+    for f, start, end in PROFILED_SOURCES:
         with open(os.path.join(root or ROOT, f), encoding="utf-8") as fh:
             text = fh.read()
         if start is not None:
@@ -102,14 +105,18 @@ def profiled_sources_sha(root=None):
     return h.hexdigest()
 
 
+GEOMETRY_KEYS = ("ext_loge", "ext_np", "ext_smem", "ext_blocks_per_sm", "l2_persist")
+
+
 def profiled_traffic(config, geometry, n_test):
-    t = PROFILED_VP_TRAFFIC
-    if config != t["config"] or any(geometry.get(k) != t[k] for k in
-                                    ("ext_loge", "ext_np", "ext_smem", "ext_blocks_per_sm", "l2_persist")):
-        return None
-    if profiled_sources_sha() != t["sha256"]:
-        return None  # the kernel changed since the counters were taken
-    return t["bytes_per_test_sample"] * n_test
+    sha = None
+    for t in PROFILED_VP_TRAFFIC:
+        if config != t["config"] or any(geometry.get(k) != t[k] for k in GEOMETRY_KEYS):
+            continue
+        sha = sha or profiled_sources_sha()
+        if sha == t["sha256"]:  # otherwise the kernel changed since the counters were taken
+            return t["bytes_per_test_sample"] * n_test
+    return None
 
 
 # ----------------------------------------------------------------- helpers
@@ -181,81 +188,121 @@ def dist_setup(args):
     return ws, rank, local, pg
 
 
+def workload_name(cfg):
+    return (f"{cfg.name}: {cfg.n_classes}-class synthetic {cfg.data_kind}, {cfg.n_values} values x "
+            f"{cfg.therm_bits}-bit thermometer, {cfg.tuple_bits}-bit tuples"
+            f"{' H3-hashed to ' if cfg.hash_h3 else ', '}{cfg.addr_bits}-bit RAM addresses, "
+            f"N=2^{cfg.log_n}, {cfg.n_primes}x{cfg.prime_bits}-bit RNS primes")
+
+
+def bench_config(cfg, bsz, ws, sample_bytes):
+    """The `config` object of both arms' lines (the same workload);
+    sample_bytes: one encrypted sample."""
+    return {"workload": workload_name(cfg), "batch_train": bsz, "batch_test": bsz,
+            "l2": "inputs larger than L2 (one step's encrypted batches ~%.0f GB)" %
+                  (2 * bsz * sample_bytes / 1e9),
+            "parallelism": "replicas" if ws > 1 else "single GPU"}
+
+
 # -------------------------------------------------------------- the oracle
 def _oracle_worker(job):
-    """One worker of the CPU baseline: the oracle encrypts one train and one
-    test sample's bits for its RAMs, runs the IVP of each RAM and the VP of
-    each (RAM, class); returns the seconds it took."""
-    cfg_name, rams = job
+    """One worker of the CPU baseline: for its RAM j (and class c) the
+    oracle encrypts one sample's bits of that RAM, runs the RAM's IVP
+    (Algorithm 6) and the VP of class c (Algorithm 7) on them (the work of
+    neither depends on the bit values).  Returns single-core seconds per
+    encrypted bit slot, per training RAM item and per inference (RAM,
+    class) item."""
+    cfg_name, j, c, k = job
     sys.path.insert(0, ROOT)
-    import numpy as np
     from oracle import Oracle, wisard
     from synthdata import get_config, make_dataset
     cfg = get_config(cfg_name)
-    t0 = time.perf_counter()
     o = Oracle(cfg)
-    vals, labels = make_dataset(cfg, "train", n=1)
-    tvals, _ = make_dataset(cfg, "test", n=1)
+    vals, labels = make_dataset(cfg, "train", n=1, seed=101 + k)
     s = o.keygen(cfg.key_seed)
     bits = wisard.encode(o.P, vals)
-    tbits = wisard.encode(o.P, tvals)
-    H = o.train(o.new_model(), s, 101, bits, labels, rams=rams)
-    o.infer(H, s, 202, tbits, rams=rams)
-    _ = np
-    return time.perf_counter() - t0
+    H = o.new_model()
+    t0 = time.perf_counter()
+    slots = o.slots_for_rams([j])
+    rg = o.encrypt_slots(s, 101, 0, bits[0], labels[0], slots)
+    t1 = time.perf_counter()
+    o.ivp_item(rg, j)
+    t2 = time.perf_counter()
+    o.vp_item(H, rg, j, c)
+    t3 = time.perf_counter()
+    return (t1 - t0) / len(slots), t2 - t1, t3 - t2
 
 
-def oracle_sample(cfg_name, k0, workers, rams_per_worker=1):
+def oracle_sample(cfg_name, workers, step=0):
+    """The oracle on `workers` processes at once, each on its own (RAM,
+    class) of the workload; returns the W-core rate in samples/s
+    (one training and one test sample per two samples), the wall time and
+    the items measured.  A sample's work is n_slots encrypted bits plus k0
+    IVP items (training) or n_data encrypted bits plus k0 * l VP items
+    (inference), from the per-item times of the workers."""
     import multiprocessing as mp
+    from oracle import Oracle
+    from synthdata import get_config
+    cfg = get_config(cfg_name)
+    P = Oracle(cfg).P
+    l = cfg.n_classes
     jobs = []
-    stride = max(1, k0 // (workers * rams_per_worker))
-    r = 0
     for w in range(workers):
-        rams = [(r + t * stride) % k0 for t in range(rams_per_worker)]
-        r += 1
-        jobs.append((cfg_name, rams))
+        k = step * workers + w
+        j = (k * 37) % P.k0
+        jobs.append((cfg_name, j, (k * 7) % l, k))
     ctx = mp.get_context("spawn")
     t0 = time.perf_counter()
     with ctx.Pool(workers) as pool:
-        pool.map(_oracle_worker, jobs)
+        res = pool.map(_oracle_worker, jobs)
     wall = time.perf_counter() - t0
-    rams_done = workers * rams_per_worker
-    samples = 2.0 * rams_done / k0  # one train + one test sample, over all k0 RAMs
-    return samples / wall, wall, rams_done
+    enc = statistics.mean(r[0] for r in res)
+    ivp = statistics.mean(r[1] for r in res)
+    vp = statistics.mean(r[2] for r in res)
+    t_train = enc * P.n_slots + ivp * P.k0
+    t_test = enc * P.n_data + vp * P.k0 * l
+    rate = workers * 2.0 / (t_train + t_test)
+    return rate, wall, {"items": workers, "enc_s_per_slot": enc, "ivp_s_per_ram": ivp,
+                        "vp_s_per_ram_class": vp, "k0": P.k0, "classes": l,
+                        "sample_bytes": P.n_slots * o_rgsw_bytes(P)}
+
+
+def o_rgsw_bytes(P):
+    return 2 * P.dnum * 2 * P.r * P.n * 8
+
+
+def oracle_sample_text(info, wall):
+    return (f"{info['items']} worker processes at once, each encrypting one sample's bits of one RAM "
+            f"and running that RAM's IVP and one (RAM, class) VP on them; per-sample "
+            f"time = per-slot encryption x slots + IVP x {info['k0']} RAMs (training) + VP x "
+            f"{info['k0']} x {info['classes']} (inference), {wall:.1f} s wall")
 
 
 def reference_arm(args, ws, rank):
     if ws > 1 and rank != 0:
         return
     from synthdata import get_config
-    from oracle import Oracle
     cfg = get_config(args.config)
-    k0 = Oracle(cfg).P.k0
+    bsz = args.batch or DEFAULT_BATCH.get(args.config, 16)
     cores = min(os.cpu_count() or 1, 16)
     times = []
+    info = None
     for it in range(args.warmup + args.steps):
-        rate, wall, rams = oracle_sample(args.config, k0, cores)
+        rate, wall, info = oracle_sample(args.config, cores, step=it)
         if it >= args.warmup:
-            times.append((rate, wall, rams))
+            times.append((rate, wall))
     rate = statistics.mean(t[0] for t in times)
-    sample = (f"per step: 1 train + 1 test sample restricted to {times[0][2]} of {k0} RAMs "
-              f"(one RAM per worker process), scaled by {k0}/{times[0][2]}")
+    sample = oracle_sample_text(info, statistics.mean(t[1] for t in times))
     line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 * statistics.mean(t[1] for t in times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
             "data": "synthetic",
-            "config": {"workload": workload_name(cfg), "sample": sample},
+            "config": bench_config(cfg, bsz, ws, info["sample_bytes"]),
             "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
-
-
-def workload_name(cfg):
-    return (f"{cfg.name}: {cfg.n_classes}-class synthetic {cfg.data_kind}, {cfg.n_values} values x "
-            f"{cfg.therm_bits}-bit thermometer, {cfg.addr_bits}-bit RAM addresses, "
-            f"N=2^{cfg.log_n}, {cfg.n_primes}x{cfg.prime_bits}-bit RNS primes")
 
 
 # ------------------------------------------------------------ the GPU arm
@@ -308,10 +355,195 @@ def algorithmic_work(sz, slots, l):
             "rgsw_bytes": sz["rgsw_words"] * 8}
 
 
-# samples per step: cfg1's whole test set; for the larger rings, what keeps one
-# encrypted batch (786 MiB, 3.9 GiB, 15.5 GiB per sample) plus scratch well
-# inside HBM
-DEFAULT_BATCH = {"cfg1": 100, "cfg2": 64, "cfg3": 16, "cfg4": 4}
+class Workload:
+    """One workload on one GPU: a session in its tuned geometry, the train and
+    test sets resident in HBM as raw bytes, a key, the resident model and the
+    server side of a step captured as CUDA graphs (ServerStep)."""
+
+    def __init__(self, name, local, bsz, geometry, rank=0):
+        import numpy as np
+        import torch
+
+        from paper_2403_20190_gb300.session import ServerStep, Session
+        from synthdata import get_config, make_dataset
+        self.name, self.bsz = name, bsz
+        self.cfg = cfg = get_config(name)
+        self.sess = sess = Session(cfg, local, geometry=geometry)
+        self.sz = sz = sess.sz
+        dev = self.dev = sess.device
+        n_pool = max(cfg.n_train, bsz)
+        self.tr_vals, self.tr_lab = make_dataset(cfg, "train", n=n_pool)
+        self.te_vals, _ = make_dataset(cfg, "test", n=max(cfg.n_test, bsz))
+        self.tr_vals_d = torch.from_numpy(self.tr_vals).to(dev)
+        self.tr_lab_d = torch.from_numpy(self.tr_lab.astype(np.int32)).to(dev)
+        self.te_vals_d = torch.from_numpy(self.te_vals).to(dev)
+        self.key = sess.keygen(cfg.key_seed)
+        self.model = sess.new_model()
+        self.st = ServerStep(sess, self.key, self.model, bsz, bsz)
+        self.bits = torch.empty((bsz, sz["n_data"]), dtype=torch.uint8, device=dev)
+        self.stream = torch.cuda.current_stream()
+        self.offset = rank * 7919  # replicas draw different samples
+        self.vp_events = []  # (before, after) the inference graph of every timed step
+
+    def client(self, k, host=None):
+        """encode + encrypt one train and one test batch (fresh seeds)"""
+        from paper_2403_20190_gb300 import binding as B
+        bsz, s, st = self.bsz, self.sess, self.st
+        n_tr, n_te = self.tr_vals_d.shape[0], self.te_vals_d.shape[0]
+        i0 = min(((k * bsz + self.offset) % n_tr), n_tr - bsz)
+        j0 = min(((k * bsz + self.offset) % n_te), n_te - bsz)
+        if host is not None:
+            tv, tl, tev = self.tr_vals_d[:bsz], self.tr_lab_d[:bsz], self.te_vals_d[:bsz]
+            tv.copy_(host[0], non_blocking=True)
+            tl.copy_(host[1], non_blocking=True)
+            tev.copy_(host[2], non_blocking=True)
+        else:
+            tv, tl = self.tr_vals_d[i0:i0 + bsz], self.tr_lab_d[i0:i0 + bsz]
+            tev = self.te_vals_d[j0:j0 + bsz]
+        B.hw_encode(s.ctx, tv, bsz, self.bits, self.stream)
+        B.hw_encrypt_sample(s.ctx, self.key, self.bits, tl, bsz, 1000 + k, 0, st.rgsw_train, self.stream)
+        B.hw_encode(s.ctx, tev, bsz, self.bits, self.stream)
+        B.hw_encrypt_sample(s.ctx, self.key, self.bits, None, bsz, 500000 + k, 0, st.rgsw_test, self.stream)
+
+    def step(self, k, host=None, time_vp=False):
+        import torch
+        self.client(k, host)
+        if time_vp:
+            pair = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            self.vp_events.append(pair)
+            self.st.replay(between=lambda i: pair[i].record(self.stream) if i < 2 else None)
+        else:
+            self.st.replay()
+        if host is not None:
+            host[3].copy_(self.st.labels, non_blocking=True)
+
+    def warm(self, warmup):
+        import torch
+        for k in range(warmup):
+            self.client(k)
+            self.st.run()
+        self.st.capture()  # the server side of a step as CUDA graphs (train, infer, post)
+        torch.cuda.synchronize()
+
+    def timed(self, k0, steps, barrier=lambda: None):
+        """Device time (ms) of `steps` steps, CUDA events on the launching
+        stream, a barrier and a synchronize on both sides."""
+        import torch
+        barrier()
+        torch.cuda.synchronize()
+        start = torch.cuda.Event(enable_timing=True)
+        end = torch.cuda.Event(enable_timing=True)
+        start.record(self.stream)
+        for k in range(steps):
+            self.step(k0 + k, time_vp=True)
+        end.record(self.stream)
+        torch.cuda.synchronize()
+        barrier()
+        return start.elapsed_time(end)
+
+    def phases(self, k):
+        """Per-call device times (ms) of one eager step with events between
+        the calls."""
+        import torch
+
+        from paper_2403_20190_gb300 import binding as B
+        s, st, bsz, stream = self.sess, self.st, self.bsz, self.stream
+        names = ["t0", "t1", "t2", "t3", "t4", "t5"]
+        evs = {nm: torch.cuda.Event(enable_timing=True) for nm in names}
+        evs["t0"].record(stream)
+        B.hw_encode(s.ctx, self.tr_vals_d[:bsz], bsz, self.bits, stream)
+        B.hw_encrypt_sample(s.ctx, self.key, self.bits, self.tr_lab_d[:bsz], bsz, 1000 + k, 0, st.rgsw_train,
+                            stream)
+        evs["t1"].record(stream)
+        B.hw_train_accumulate(s.ctx, self.model, st.rgsw_train, bsz, st.scratch, stream)
+        evs["t2"].record(stream)
+        B.hw_encode(s.ctx, self.te_vals_d[:bsz], bsz, self.bits, stream)
+        B.hw_encrypt_sample(s.ctx, self.key, self.bits, None, bsz, 500000 + k, 0, st.rgsw_test, stream)
+        evs["t3"].record(stream)
+        resp, sums, scr = st.ibufs
+        B.hw_infer(s.ctx, self.model, st.rgsw_test, bsz, resp, sums, scr, stream)
+        evs["t4"].record(stream)
+        B.hw_decrypt(s.ctx, self.key, B.HW_DEC_LWE, resp, bsz * self.cfg.n_classes * self.sz["k0"], st.counts,
+                     stream)
+        B.hw_pdact(s.ctx, st.counts, bsz, st.scores, st.labels, stream)
+        evs["t5"].record(stream)
+        torch.cuda.synchronize()
+        keys = ["encrypt_train", "train", "encrypt_test", "infer", "decrypt_pdact"]
+        return {kn: evs[a].elapsed_time(evs[b]) for a, b, kn in zip(names[:-1], names[1:], keys)}
+
+    def rooflines(self, ph, local):
+        """Roofline of the VP kernel (the dominant one: its graph's average
+        duration over the timed steps) and of the IVP kernel (the training
+        call of the phase breakdown), against the integer-multiply peak."""
+        import torch
+        pk, _ = peaks()
+        alg = algorithmic_counts(self.sess, self.cfg)
+        sm_count = torch.cuda.get_device_properties(local).multi_processor_count
+        sm_mhz = pk.get("sm_max_mhz", 2070.0)
+        word_bits = self.sz["word_bits"]  # the external product's word width in this context
+        muls = MULS_PER_MODMUL32 if word_bits == 32 else MULS_PER_MODMUL
+        peak_modmul = sm_count * IMAD_PER_CLK_PER_SM * sm_mhz * 1e6 / muls
+        peak_kind = (f"derived: {sm_count} SMs x {IMAD_PER_CLK_PER_SM} int32 multiplies/clk x "
+                     f"{sm_mhz:.0f} MHz / {muls} per {word_bits}-bit modular product")
+        infer_modmul = alg["ext_infer_per_sample"] * self.bsz * alg["per_ext_modmul"]
+        vp_ms = (statistics.mean(a.elapsed_time(b) for a, b in self.vp_events) if self.vp_events
+                 else ph["infer"])
+        achieved = infer_modmul / (vp_ms / 1000.0)
+        vp = {"bound": "alu", "kernel": "k_vp_infer", "achieved": achieved / 1e12,
+              "peak": peak_modmul / 1e12, "unit": "T modmul/s", "frac": achieved / peak_modmul,
+              "traffic": profiled_traffic(self.name, self.sess.geometry, self.bsz),
+              "algorithmic_rgsw_bytes": alg["rgsw_bytes"] * alg["ext_infer_per_sample"] // self.cfg.n_classes
+              * self.bsz, "launch_ms": vp_ms, "peak_kind": peak_kind,
+              "work": f"{alg['ext_infer_per_sample']} external products x {alg['per_ext_modmul']} modular "
+                      f"products per test sample, {self.bsz} test samples per launch"}
+        train_modmul = alg["ext_train_per_sample"] * self.bsz * alg["per_ext_modmul"]
+        ivp_achieved = train_modmul / (ph["train"] / 1000.0)
+        ivp = {"bound": "alu", "kernel": "k_ivp_train + k_accumulate", "achieved": ivp_achieved / 1e12,
+               "peak": peak_modmul / 1e12, "unit": "T modmul/s", "frac": ivp_achieved / peak_modmul,
+               "launch_ms": ph["train"],
+               "work": f"{alg['ext_train_per_sample']} external products per training sample"}
+        return vp, ivp, alg
+
+    def ntt(self, count=None):
+        """Batched forward NTT of this ring (one read + one write per
+        polynomial, inputs larger than L2)."""
+        import torch
+
+        from paper_2403_20190_gb300 import binding as B
+        pk, pk_kind = peaks()
+        nn = self.sz["n"]
+        if count is None:
+            count = (1 << 31) // (nn * 8)  # 2 GiB of polynomials
+        polys = self.sess.words(count * nn)
+        for _ in range(3):
+            B.hw_ntt_forward(self.sess.ctx, polys, count, self.stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 5
+        e0.record(self.stream)
+        for _ in range(reps):
+            B.hw_ntt_forward(self.sess.ctx, polys, count, self.stream)
+        e1.record(self.stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / reps / 1000.0
+        gbs = 2.0 * count * nn * 8 / t / 1e9
+        del polys
+        g = self.sess.geometry
+        return {"gbs": gbs, "frac_of_hbm": gbs / pk["hbm_gbs"], "peak_gbs": pk["hbm_gbs"], "peak_kind": pk_kind,
+                "polys": count, "n": nn, "prime_bits": self.cfg.prime_bits, "ms_per_launch": t * 1000.0,
+                "variant": f"radix {1 << g['ntt_loge']}, {32 * g['ntt_limbs']}-bit words"}
+
+    def summary(self, elapsed_ms, steps, ws, local, with_ntt=True):
+        ph = self.phases(1000 + steps)
+        vp, ivp, _ = self.rooflines(ph, local)
+        out = {"workload": workload_name(self.cfg), "batch": self.bsz, "steps": steps,
+               "samples_per_s": 2 * self.bsz * steps * ws / (elapsed_ms / 1000.0),
+               "ms_per_step": elapsed_ms / steps,
+               "train_samples_per_s": self.bsz / (ph["train"] / 1000.0),
+               "inferences_per_s": self.bsz / (ph["infer"] / 1000.0),
+               "phases_ms": ph, "roofline": vp, "roofline_ivp": ivp, "geometry": self.sess.geometry}
+        if with_ntt:
+            out["ntt"] = self.ntt()
+        return out, ph
 
 
 def gpu_arm(args, ws, rank, local, pg):
@@ -320,30 +552,34 @@ def gpu_arm(args, ws, rank, local, pg):
 
     from paper_2403_20190_gb300 import binding as B
     from paper_2403_20190_gb300 import build as libbuild
-    from paper_2403_20190_gb300.session import ServerStep, Session
-    from synthdata import get_config, make_dataset
 
     libbuild.build()
     torch.cuda.set_device(local)
-    cfg = get_config(args.config)
     tune = None
     geometry = None
+    per_names = [nm for nm in ALL_CONFIGS if nm != args.config] if args.per_config_steps > 0 else []
     if args.geometry == "auto":
         from paper_2403_20190_gb300.tuning import tuned_geometry
+        from synthdata import get_config
         t0 = time.perf_counter()
-        geometry, entries, cached = tuned_geometry(cfg, local)
+        geometry, entries, cached = tuned_geometry(get_config(args.config), local)
         tune = {"cached": cached, "seconds": round(time.perf_counter() - t0, 2), "candidates": entries}
         # every other parameter set the legs use is tuned now, before this
         # process holds any context or buffer: the tuner's probe contexts come
         # and go while nothing else is resident, and the legs find the cache
-        others = set()
-        if not (args.no_ntt and args.no_packing) and args.config != "cfg1":
+        others = set(per_names)
+        if not args.no_packing:
             others.add("cfg1")
         if not args.no_serve:
-            others.update(("cfg1", "cfg2", "cfg3", "cfg4"))
+            others.update(ALL_CONFIGS)
         for nm in sorted(others - {args.config}):
             tuned_geometry(get_config(nm), local)
-    sess = Session(cfg, local, geometry=geometry)
+    geo = "auto" if args.geometry == "auto" else None
+    bsz = args.batch or DEFAULT_BATCH.get(args.config, 16)
+    w = Workload(args.config, local, bsz, geometry if geometry is not None else None, rank)
+    cfg, sess, sz, st, stream = w.cfg, w.sess, w.sz, w.st, w.stream
+    if tune is not None:
+        tune["chosen"] = sess.geometry
 
     def healthy(where):
         """Stop before launching on a context whose device tables changed."""
@@ -351,116 +587,29 @@ def gpu_arm(args, ws, rank, local, pg):
             B.hw_check_context(sess.ctx)
         except B.HwError as e:
             raise RuntimeError(f"context check failed after {where}: {e}") from None
-    if tune is not None:
-        tune["chosen"] = sess.geometry
-    dev = sess.device
-    bsz = args.batch or DEFAULT_BATCH.get(args.config, 16)
-    sz = sess.sz
-    n_pool = max(cfg.n_train, bsz)
-    # the whole train / test sets of the workload, resident in HBM as raw bytes
-    tr_vals, tr_lab = make_dataset(cfg, "train", n=n_pool)
-    te_vals, _ = make_dataset(cfg, "test", n=max(cfg.n_test, bsz))
-    tr_vals_d = torch.from_numpy(tr_vals).to(dev)
-    tr_lab_d = torch.from_numpy(tr_lab.astype(np.int32)).to(dev)
-    te_vals_d = torch.from_numpy(te_vals).to(dev)
-
-    key = sess.keygen(cfg.key_seed)
-    model = sess.new_model()
-    st = ServerStep(sess, key, model, bsz, bsz)
-    bits = torch.empty((bsz, sz["n_data"]), dtype=torch.uint8, device=dev)
-    stream = torch.cuda.current_stream()
-
-    n_tr = tr_vals_d.shape[0]
-    n_te = te_vals_d.shape[0]
-    offset = rank * 7919  # replicas draw different samples
-
-    def client(k, host=None):
-        """encode + encrypt one train and one test batch (fresh seeds)"""
-        i0 = min(((k * bsz + offset) % n_tr), n_tr - bsz)
-        j0 = min(((k * bsz + offset) % n_te), n_te - bsz)
-        if host is not None:
-            tv, tl, tev = tr_vals_d[:bsz], tr_lab_d[:bsz], te_vals_d[:bsz]
-            tv.copy_(host[0], non_blocking=True)
-            tl.copy_(host[1], non_blocking=True)
-            tev.copy_(host[2], non_blocking=True)
-        else:
-            tv, tl, tev = tr_vals_d[i0:i0 + bsz], tr_lab_d[i0:i0 + bsz], te_vals_d[j0:j0 + bsz]
-        B.hw_encode(sess.ctx, tv, bsz, bits, stream)
-        B.hw_encrypt_sample(sess.ctx, key, bits, tl, bsz, 1000 + k, 0, st.rgsw_train, stream)
-        B.hw_encode(sess.ctx, tev, bsz, bits, stream)
-        B.hw_encrypt_sample(sess.ctx, key, bits, None, bsz, 500000 + k, 0, st.rgsw_test, stream)
-
-    vp_events = []  # (before, after) the inference graph of every timed step
-
-    def step(k, host=None, time_vp=False):
-        client(k, host)
-        if time_vp:
-            pair = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-            vp_events.append(pair)
-            st.replay(between=lambda i: pair[i].record(stream) if i < 2 else None)
-        else:
-            st.replay()
-        if host is not None:
-            host[3].copy_(st.labels, non_blocking=True)
-
-    for k in range(args.warmup):
-        client(k)
-        st.run()
-    st.capture()  # the server side of a step as CUDA graphs (train, infer, post)
-    torch.cuda.synchronize()
 
     def barrier():
         if pg is not None:
             pg.barrier()
 
+    w.warm(args.warmup)
     clocks = ClockSampler(local)
     clocks.start()
     launches0 = B.hw_launch_count(sess.ctx)
-    barrier()
-    torch.cuda.synchronize()
-    start = torch.cuda.Event(enable_timing=True)
-    end = torch.cuda.Event(enable_timing=True)
-    start.record(stream)
-    for k in range(args.steps):
-        step(args.warmup + k, time_vp=True)
-    end.record(stream)
-    torch.cuda.synchronize()
-    barrier()
+    elapsed_ms = w.timed(args.warmup, args.steps, barrier)
     launches = B.hw_launch_count(sess.ctx) - launches0 + st.launches_per_step * args.steps
     clk = clocks.stop()
-    elapsed_ms = start.elapsed_time(end)
     if pg is not None:
-        t = torch.tensor([elapsed_ms], device=dev)
+        t = torch.tensor([elapsed_ms], device=w.dev)
         pg.all_reduce(t, op=pg.ReduceOp.MAX)
         elapsed_ms = float(t.item())
     total_samples = 2 * bsz * args.steps * ws
     value = total_samples / (elapsed_ms / 1000.0)
-
-    # phase breakdown from one extra eager step with events between the calls
-    names = ["t0", "t1", "t2", "t3", "t4", "t5"]
-    evs = {nm: torch.cuda.Event(enable_timing=True) for nm in names}
-    k = args.warmup + args.steps
-    evs["t0"].record(stream)
-    B.hw_encode(sess.ctx, tr_vals_d[:bsz], bsz, bits, stream)
-    B.hw_encrypt_sample(sess.ctx, key, bits, tr_lab_d[:bsz], bsz, 1000 + k, 0, st.rgsw_train, stream)
-    evs["t1"].record(stream)
-    B.hw_train_accumulate(sess.ctx, model, st.rgsw_train, bsz, st.scratch, stream)
-    evs["t2"].record(stream)
-    B.hw_encode(sess.ctx, te_vals_d[:bsz], bsz, bits, stream)
-    B.hw_encrypt_sample(sess.ctx, key, bits, None, bsz, 500000 + k, 0, st.rgsw_test, stream)
-    evs["t3"].record(stream)
-    resp, sums, scr = st.ibufs
-    B.hw_infer(sess.ctx, model, st.rgsw_test, bsz, resp, sums, scr, stream)
-    evs["t4"].record(stream)
-    B.hw_decrypt(sess.ctx, key, B.HW_DEC_LWE, resp, bsz * cfg.n_classes * sz["k0"], st.counts, stream)
-    B.hw_pdact(sess.ctx, st.counts, bsz, st.scores, st.labels, stream)
-    evs["t5"].record(stream)
-    torch.cuda.synchronize()
-    keys = ["encrypt_train", "train", "encrypt_test", "infer", "decrypt_pdact"]
-    ph = {kn: evs[a].elapsed_time(evs[b]) for a, b, kn in zip(names[:-1], names[1:], keys)}
-
+    ph = w.phases(args.warmup + args.steps)
+    roofline, roofline_ivp, alg = w.rooflines(ph, local)
     healthy("the timed steps")
 
+    key, model = w.key, w.model
     # dataset balancing (Section 3.6.1) on the same step: the label-bit IVP
     # over the training batch into the class-count ciphertext, its
     # decryption and the balanced PD-act of the test batch
@@ -484,7 +633,6 @@ def gpu_arm(args, ws, rank, local, pg):
                      "share_of_step": (t_count + t_post) / (elapsed_ms / args.steps),
                      "ext_products_per_sample": sz["L"]}
         del bal_scr
-
     healthy("the balancing leg")
 
     # PackingKeySwitching (Section 2.4): the test batch's responses packed
@@ -492,7 +640,7 @@ def gpu_arm(args, ws, rank, local, pg):
     keyswitch = None
     if not args.no_keyswitch:
         resp = st.ibufs[0]
-        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         ksk = sess.ksk_gen(key, cfg.key_seed + 1, stream=stream)
         e1.record(stream)
@@ -512,7 +660,6 @@ def gpu_arm(args, ws, rank, local, pg):
                      "response_bytes_per_sample": {"lwe": sz["resp_words"] * 8, "packed": sz["rlwe_words"] * 8},
                      "share_of_infer": min(t_pack) / ph["infer"]}
         del ksk, pscr
-
     healthy("the key-switching leg")
 
     # inference against the model in clear (Section 3.6.2): the owner's
@@ -521,7 +668,6 @@ def gpu_arm(args, ws, rank, local, pg):
     # phase breakdown's, whose decrypted counters it must reproduce
     clear_model = None
     if not args.no_clear_model:
-        alg_c = algorithmic_counts(sess, cfg)
         W = sess.decrypt_model_counts(key, model, stream=stream)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -545,146 +691,54 @@ def gpu_arm(args, ws, rank, local, pg):
                        "ms_per_batch": min(t_plain), "encrypted_model_ms_per_batch": ph["infer"],
                        "speedup_vs_encrypted_model": ph["infer"] / min(t_plain),
                        "load_ms": t_load, "plain_bytes": B.hw_plain_model_words(sess.ctx) * 8,
-                       "ext_products_per_sample": {"clear": alg_c["ext_clear_per_sample"],
-                                                   "encrypted": alg_c["ext_infer_per_sample"]},
+                       "ext_products_per_sample": {"clear": alg["ext_clear_per_sample"],
+                                                   "encrypted": alg["ext_infer_per_sample"]},
                        "responses_equal_to_encrypted_path": same}
         del plain, pbufs, W
-
     healthy("the clear-model leg")
 
     # e2e through the C ABI with pinned host buffers, copies inside the timed region
     e2e = None
     if not args.no_e2e:
-        h_tr = torch.from_numpy(tr_vals[:bsz].copy()).pin_memory()
-        h_lab = torch.from_numpy(tr_lab[:bsz].astype(np.int32)).pin_memory()
-        h_te = torch.from_numpy(te_vals[:bsz].copy()).pin_memory()
+        h_tr = torch.from_numpy(w.tr_vals[:bsz].copy()).pin_memory()
+        h_lab = torch.from_numpy(w.tr_lab[:bsz].astype(np.int32)).pin_memory()
+        h_te = torch.from_numpy(w.te_vals[:bsz].copy()).pin_memory()
         h_out = torch.empty(bsz, dtype=torch.int32).pin_memory()
         host = (h_tr, h_lab, h_te, h_out)
         torch.cuda.synchronize()
         barrier()
         t0 = time.perf_counter()
         for k in range(args.steps):
-            step(args.warmup + args.steps + 1 + k, host)
+            w.step(args.warmup + args.steps + 1 + k, host)
             torch.cuda.current_stream().synchronize()
             _ = int(h_out[0])
         t1 = time.perf_counter()
         e2e_s = t1 - t0
         if pg is not None:
-            t = torch.tensor([e2e_s], device=dev)
+            t = torch.tensor([e2e_s], device=w.dev)
             pg.all_reduce(t, op=pg.ReduceOp.MAX)
             e2e_s = float(t.item())
         e2e = {"value": total_samples / e2e_s, "unit": UNIT,
                "h2d_bytes_per_step": int(h_tr.numel() + h_lab.numel() * 4 + h_te.numel()),
                "d2h_bytes_per_step": int(h_out.numel() * 4)}
-
     healthy("the end-to-end leg")
 
-    # roofline of the dominant kernel (the VP inference kernel)
-    pk, pk_kind = peaks()
-    alg = algorithmic_counts(sess, cfg)
-    sm_count = torch.cuda.get_device_properties(local).multi_processor_count
-    sm_mhz = pk.get("sm_max_mhz", 2070.0)
-    word_bits = sz["word_bits"]  # the external product's word width in this context
-    muls = MULS_PER_MODMUL32 if word_bits == 32 else MULS_PER_MODMUL
-    peak_modmul = sm_count * IMAD_PER_CLK_PER_SM * sm_mhz * 1e6 / muls
-    infer_modmul = alg["ext_infer_per_sample"] * bsz * alg["per_ext_modmul"]
-    # average duration of the inference graph (k_vp_infer + the per-class
-    # sums, < 0.5 %) over the timed steps, CUDA events on the launching stream
-    vp_ms = statistics.mean(a.elapsed_time(b) for a, b in vp_events)
-    achieved = infer_modmul / (vp_ms / 1000.0)
-    roofline = {"bound": "alu", "kernel": "k_vp_infer", "achieved": achieved / 1e12,
-                "peak": peak_modmul / 1e12, "unit": "T modmul/s", "frac": achieved / peak_modmul,
-                "traffic": profiled_traffic(args.config, sess.geometry, bsz),
-                "launch_ms": vp_ms,
-                "butterfly_ceiling": BUTTERFLY_CEILING32 if word_bits == 32 else BUTTERFLY_CEILING,
-                "peak_kind": f"derived: {sm_count} SMs x {IMAD_PER_CLK_PER_SM} int32 multiplies/clk x "
-                             f"{sm_mhz:.0f} MHz / {muls} per {word_bits}-bit modular product"}
-    train_modmul = alg["ext_train_per_sample"] * bsz * alg["per_ext_modmul"]
-
-    # batched NTT throughput (forward transforms, one read + one write per
-    # polynomial): this workload's ring, and cfg1's 30-bit ring, where the
-    # 32-bit transform makes the NTT bound by HBM rather than by integer
-    # multiplies
-    ntt = None
-    if not args.no_ntt:
-        def ntt_rate(ctx_sess, count):
-            nn = ctx_sess.sz["n"]
-            polys = ctx_sess.words(count * nn)
-            for _ in range(3):
-                B.hw_ntt_forward(ctx_sess.ctx, polys, count, stream)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            reps = 5
-            e0.record(stream)
-            for _ in range(reps):
-                B.hw_ntt_forward(ctx_sess.ctx, polys, count, stream)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            t = e0.elapsed_time(e1) / reps / 1000.0
-            gbs = 2.0 * count * nn * 8 / t / 1e9
-            del polys
-            g = ctx_sess.geometry
-            return {"gbs": gbs, "frac_of_hbm": gbs / pk["hbm_gbs"], "polys": count, "n": nn,
-                    "prime_bits": ctx_sess.cfg.prime_bits, "ms_per_launch": t * 1000.0,
-                    "variant": f"radix {1 << g['ntt_loge']}, {32 * g['ntt_limbs']}-bit words"}
-        ntt = {"peak_gbs": pk["hbm_gbs"], "peak_kind": pk_kind,
-               args.config: ntt_rate(sess, 65536 if sz["n"] <= 4096 else 32768)}
-        if args.config != "cfg1":
-            s1 = Session(get_config("cfg1"), local, geometry="auto" if args.geometry == "auto" else None)
-            ntt["cfg1"] = ntt_rate(s1, 262144)
-            del s1
-
+    ntt = None if args.no_ntt else w.ntt()
     healthy("the NTT leg")
-
-    # horizontal packing (Section 6): plain vs packed inference on the
-    # Wisconsin-shaped ring (label bits low, z = 0: one VP answers both
-    # classes); the digit workloads keep a stored ciphertext per class
-    packing = None
-    if not args.no_packing:
-        pc = cfg if args.config == "cfg1" else get_config("cfg1")
-        ps = sess if args.config == "cfg1" else Session(pc, local, geometry="auto" if args.geometry == "auto" else None)
-        n_p = 100
-        pv, _ = make_dataset(pc, "test", n=n_p)
-        pkey = ps.keygen(pc.key_seed)
-        pbits = ps.encode(torch.from_numpy(pv).to(ps.device))
-        prg = ps.encrypt(pkey, pbits, None, seed=4242)
-        pmodel = ps.new_model()
-        pbufs = ps.infer_buffers(n_p)
-        rates = {}
-        for mode in (False, True):
-            ts = []
-            for k in range(4):
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record()
-                ps.infer(pmodel, prg, n_p, bufs=pbufs, packed=mode)
-                b.record()
-                torch.cuda.synchronize()
-                if k:
-                    ts.append(a.elapsed_time(b))
-            rates["packed" if mode else "plain"] = n_p / (min(ts) / 1000.0)
-        psz = ps.sz
-        groups = min(pc.n_classes, 1 << psz["z"]) if psz["z"] <= psz["L"] else pc.n_classes
-        packing = {"workload": "cfg1", "inferences_per_s_plain": rates["plain"],
-                   "inferences_per_s_packed": rates["packed"],
-                   "vp_per_sample": {"plain": pc.n_classes * psz["k0"], "packed": groups * psz["k0"]},
-                   "applies_to_bench_workload": sz["z"] <= sz["L"] and min(cfg.n_classes, 1 << sz["z"]) < cfg.n_classes}
-        del pbufs, prg
-        if ps is not sess:
-            del ps
-
-    healthy("the packing leg")
 
     # the same workload one request at a time: each request one train and one
     # test sample, encoded, encrypted, trained, inferred, decrypted, waited for
     single = None
     if not args.no_serve:
         n1 = 6
+        bits1 = w.bits
         t0 = time.perf_counter()
         for k in range(n1):
-            B.hw_encode(sess.ctx, tr_vals_d[k:k + 1], 1, bits, stream)
-            B.hw_encrypt_sample(sess.ctx, key, bits, tr_lab_d[k:k + 1], 1, 9000 + k, 0, st.rgsw_train, stream)
+            B.hw_encode(sess.ctx, w.tr_vals_d[k:k + 1], 1, bits1, stream)
+            B.hw_encrypt_sample(sess.ctx, key, bits1, w.tr_lab_d[k:k + 1], 1, 9000 + k, 0, st.rgsw_train, stream)
             B.hw_train_accumulate(sess.ctx, model, st.rgsw_train, 1, st.scratch, stream)
-            B.hw_encode(sess.ctx, te_vals_d[k:k + 1], 1, bits, stream)
-            B.hw_encrypt_sample(sess.ctx, key, bits, None, 1, 19000 + k, 0, st.rgsw_test, stream)
+            B.hw_encode(sess.ctx, w.te_vals_d[k:k + 1], 1, bits1, stream)
+            B.hw_encrypt_sample(sess.ctx, key, bits1, None, 1, 19000 + k, 0, st.rgsw_test, stream)
             resp, sums, scr = st.ibufs
             B.hw_infer(sess.ctx, model, st.rgsw_test, 1, resp, sums, scr, stream)
             B.hw_decrypt(sess.ctx, key, B.HW_DEC_LWE, resp, cfg.n_classes * sz["k0"], st.counts, stream)
@@ -692,22 +746,39 @@ def gpu_arm(args, ws, rank, local, pg):
             _ = int(st.labels[0].item())
         single = {"samples_per_s": 2 * n1 / (time.perf_counter() - t0), "requests": n1,
                   "request": "1 train + 1 test sample, synchronous"}
-
-    serving = None
-    if not args.no_serve:
         healthy("the one-at-a-time requests")
-        del st, tr_vals_d, tr_lab_d, te_vals_d, bits
+    sample_bytes = sz["sample_words"] * 8
+    del w, st, sess, key, model
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+
+    # horizontal packing (Section 6): plain vs packed inference on the
+    # Wisconsin-shaped ring (label bits low, z = 0: one VP answers both
+    # classes); the digit workloads keep a stored ciphertext per class
+    packing = None
+    if not args.no_packing:
+        packing = packing_leg(local, geo)
+
+    # the other workloads, shorter: the same step, its rooflines and the
+    # batched NTT at its primes
+    per_config = {}
+    for nm in per_names:
+        pw = Workload(nm, local, DEFAULT_BATCH[nm], geo, rank)
+        pw.warm(1)
+        pms = pw.timed(1, args.per_config_steps, barrier)
+        per_config[nm], _ = pw.summary(pms, args.per_config_steps, ws, local, with_ntt=not args.no_ntt)
+        del pw
         torch.cuda.synchronize()
         torch.cuda.empty_cache()
-        serving = serve_leg(args, local)
+
+    serving = serve_leg(args, local) if not args.no_serve else None
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cores = min(os.cpu_count() or 1, 16)
-        rate, wall, rams = oracle_sample(args.config, sz["k0"], cores)
+        rate, wall, info = oracle_sample(args.config, cores)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"1 train + 1 test sample restricted to {rams} of {sz['k0']} RAMs "
-                         f"(one per worker), {wall:.1f} s wall, scaled by {sz['k0']}/{rams}"}
+               "sample": oracle_sample_text(info, wall)}
 
     if rank == 0:
         line = {
@@ -715,22 +786,20 @@ def gpu_arm(args, ws, rank, local, pg):
             "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
             "data": "synthetic",
-            "config": {"workload": workload_name(cfg), "batch_train": bsz, "batch_test": bsz,
-                       "server_step": "CUDA graph (IVP + accumulate, VP + sums, decrypt, PD-act)",
-                       "l2": "inputs larger than L2 (encrypted batch ~%.0f GB)" %
-                             (bsz * sz["sample_words"] * 8 / 1e9),
-                       "parallelism": "replicas" if ws > 1 else "single GPU"},
+            "config": bench_config(cfg, bsz, ws, sample_bytes),
+            "server_step": "CUDA graphs (IVP + accumulate, VP + sums, decrypt + PD-act)",
             "train_samples_per_s": bsz / (ph["train"] / 1000.0),
             "inferences_per_s": bsz / (ph["infer"] / 1000.0),
-            "train_modmul_per_s": train_modmul / (ph["train"] / 1000.0),
             "phases_ms": ph,
+            "roofline": roofline,
+            "roofline_ivp": roofline_ivp,
+            "ntt": ntt,
+            "per_config": per_config,
             "balancing": balancing,
             "horizontal_packing": packing,
             "packing_keyswitch": keyswitch,
             "clear_model": clear_model,
-            "roofline": roofline,
-            "ntt": ntt,
-            "geometry": sess.geometry,
+            "geometry": tune["chosen"] if tune else None,
             "autotune": tune,
             "cpu_baseline": cpu,
             "e2e": e2e,
@@ -741,6 +810,39 @@ def gpu_arm(args, ws, rank, local, pg):
             "one_request_at_a_time": single,
         }
         print(json.dumps(line), flush=True)
+
+
+def packing_leg(local, geo):
+    import torch
+
+    from paper_2403_20190_gb300.session import Session
+    from synthdata import get_config, make_dataset
+    pc = get_config("cfg1")
+    ps = Session(pc, local, geometry=geo)
+    n_p = 100
+    pv, _ = make_dataset(pc, "test", n=n_p)
+    pkey = ps.keygen(pc.key_seed)
+    pbits = ps.encode(torch.from_numpy(pv).to(ps.device))
+    prg = ps.encrypt(pkey, pbits, None, seed=4242)
+    pmodel = ps.new_model()
+    pbufs = ps.infer_buffers(n_p)
+    rates = {}
+    for mode in (False, True):
+        ts = []
+        for k in range(4):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            ps.infer(pmodel, prg, n_p, bufs=pbufs, packed=mode)
+            b.record()
+            torch.cuda.synchronize()
+            if k:
+                ts.append(a.elapsed_time(b))
+        rates["packed" if mode else "plain"] = n_p / (min(ts) / 1000.0)
+    psz = ps.sz
+    groups = min(pc.n_classes, 1 << psz["z"]) if psz["z"] <= psz["L"] else pc.n_classes
+    return {"workload": "cfg1", "inferences_per_s_plain": rates["plain"],
+            "inferences_per_s_packed": rates["packed"],
+            "vp_per_sample": {"plain": pc.n_classes * psz["k0"], "packed": groups * psz["k0"]}}
 
 
 # per-request sample caps of the serving mix: what the footprint rule leaves
@@ -758,7 +860,7 @@ def serve_leg(args, local):
 
     from paper_2403_20190_gb300.serve import ResidentModel, Server, latency_stats, poisson_stream
     from synthdata import get_config
-    cfgs = {nm: get_config(nm) for nm in ("cfg1", "cfg2", "cfg3", "cfg4")}
+    cfgs = {nm: get_config(nm) for nm in ALL_CONFIGS}
     geo = "auto" if args.geometry == "auto" else None
     models = {nm: ResidentModel(c, local, key_seed=c.key_seed, geometry=geo) for nm, c in cfgs.items()}
     reqs = poisson_stream(cfgs, n_requests=args.serve_requests, rate=200.0, seed=2024,
@@ -780,9 +882,9 @@ def serve_leg(args, local):
            "batched": latency_stats(batched), "batched_without_packing": latency_stats(batched_plain),
            "one_at_a_time": latency_stats(alone),
            "mix": {nm: sum(1 for r in reqs if r.cfg_name == nm) for nm in cfgs},
-           "policy": "2 streams, shortest expected batch first with aging 1.0, device arena, inference "
-                     "with horizontal packing where the tree layout allows (cfg1, cfg3); the one-at-a-time "
-                     "baseline runs the plain path",
+           "policy": "2 streams, shortest expected batch first with aging 1.0, device arena, at most one "
+                     "training batch in flight per model, inference with horizontal packing where the tree "
+                     "layout allows (cfg1, cfg3); the one-at-a-time baseline runs the plain path",
            "calibrated_ms_per_sample": {f"{k[0]}/{k[1]}": round(v * 1e3, 3) for k, v in costs.items()},
            "max_samples_per_request": SERVE_MAX}
     del models, arena
