@@ -644,7 +644,7 @@ def gpu_arm(args, ws, rank, local, pg):
         e0.record(stream)
         ksk = sess.ksk_gen(key, cfg.key_seed + 1, stream=stream)
         e1.record(stream)
-        pscr = sess.words(B.hw_pack_scratch_words(sess.ctx), zero=False)
+        pscr = sess.words(B.hw_pack_scratch_words(sess.ctx, bsz), zero=False)
         sess.pack_responses(ksk, resp, bsz, scratch=pscr, stream=stream)  # warm-up
         torch.cuda.synchronize()
         t_pack = []
@@ -656,7 +656,7 @@ def gpu_arm(args, ws, rank, local, pg):
             torch.cuda.synchronize()
             t_pack.append(a.elapsed_time(b))
         keyswitch = {"pack_ms_per_step": min(t_pack), "ksk_gen_ms_once": e0.elapsed_time(e1),
-                     "ksk_bytes": B.hw_ksk_words(sess.ctx) * 8,
+                     "ksk_bytes": B.hw_ksk_words(sess.ctx) * 8, "pack_scratch_bytes": pscr.numel() * 8,
                      "response_bytes_per_sample": {"lwe": sz["resp_words"] * 8, "packed": sz["rlwe_words"] * 8},
                      "share_of_infer": min(t_pack) / ph["infer"]}
         del ksk, pscr
@@ -851,9 +851,9 @@ SERVE_MAX = {"cfg1": 256, "cfg2": 16, "cfg3": 2, "cfg4": 1}
 
 
 def serve_leg(args, local):
-    """Poisson stream (200 requests/s, seeded) of train and infer requests over
+    """Seeded Poisson streams (200 requests/s) of train and infer requests over
     the four workloads, served with continuous batching and, for comparison,
-    one request at a time; latency is arrival to completion."""
+    one request at a time; latency is arrival to completion.  Three seeds."""
     import copy
 
     import torch
@@ -863,30 +863,43 @@ def serve_leg(args, local):
     cfgs = {nm: get_config(nm) for nm in ALL_CONFIGS}
     geo = "auto" if args.geometry == "auto" else None
     models = {nm: ResidentModel(c, local, key_seed=c.key_seed, geometry=geo) for nm, c in cfgs.items()}
-    reqs = poisson_stream(cfgs, n_requests=args.serve_requests, rate=200.0, seed=2024,
-                          max_samples=SERVE_MAX)
     from paper_2403_20190_gb300.arena import DeviceArena
     budget = 120 << 30
-    arena = DeviceArena(budget, torch.device("cuda", local))  # shared by both modes
-    warm = copy.deepcopy(reqs[:4])
+    arena = DeviceArena(budget, torch.device("cuda", local))  # shared by every mode
+    modes = {
+        "batched": dict(n_streams=1, packed_infer=True, policy="fifo"),
+        "batched_without_packing": dict(n_streams=1, packed_infer=False, policy="fifo"),
+        "batched_sjf_2_streams": dict(n_streams=2, packed_infer=True, policy="sjf"),
+    }
+    warm = poisson_stream(cfgs, n_requests=4, rate=200.0, seed=1, max_samples=SERVE_MAX)
     Server(models, arena=arena).run(warm, realtime=False)
-    base = copy.deepcopy(reqs)
-    srv = Server(models, n_streams=2, arena=arena, packed_infer=True)
-    costs = srv.calibrate()  # startup, outside the timed runs
-    batched = srv.run(copy.deepcopy(reqs), realtime=True)
-    srv_plain = Server(models, n_streams=2, arena=arena, packed_infer=False)
-    srv_plain.calibrate()
-    batched_plain = srv_plain.run(copy.deepcopy(reqs), realtime=True)
-    alone = Server(models, arena=arena, packed_infer=False).run_one_at_a_time(base)
-    out = {"requests": len(reqs), "rate_per_s": 200.0, "hbm_budget_gb": budget / 2**30,
-           "batched": latency_stats(batched), "batched_without_packing": latency_stats(batched_plain),
-           "one_at_a_time": latency_stats(alone),
-           "mix": {nm: sum(1 for r in reqs if r.cfg_name == nm) for nm in cfgs},
-           "policy": "2 streams, shortest expected batch first with aging 1.0, device arena, at most one "
-                     "training batch in flight per model, inference with horizontal packing where the tree "
-                     "layout allows (cfg1, cfg3); the one-at-a-time baseline runs the plain path",
+    runs = {m: [] for m in list(modes) + ["one_at_a_time"]}
+    costs = None
+    for seed in (2024, 2025, 2026):
+        reqs = poisson_stream(cfgs, n_requests=args.serve_requests, rate=200.0, seed=seed,
+                              max_samples=SERVE_MAX)
+        for m, kw in modes.items():
+            srv = Server(models, arena=arena, **kw)
+            c = srv.calibrate()  # startup, outside the timed runs
+            costs = costs or c
+            runs[m].append(latency_stats(srv.run(copy.deepcopy(reqs), realtime=True)))
+        runs["one_at_a_time"].append(latency_stats(
+            Server(models, arena=arena, packed_infer=False).run_one_at_a_time(copy.deepcopy(reqs))))
+
+    def summary(rs):
+        keys = ("samples_per_s", "p50_ms", "p99_ms")
+        out = {k: statistics.mean(r[k] for r in rs) for k in keys}
+        out["runs"] = rs
+        return out
+    out = {"requests": args.serve_requests, "rate_per_s": 200.0, "hbm_budget_gb": budget / 2**30,
+           "seeds": [2024, 2025, 2026], **{m: summary(rs) for m, rs in runs.items()},
+           "policy": "batched: one stream, groups launched oldest request first, every pending request of "
+                     "the same (workload, kind) joins its group (up to 256 samples), device arena, at most "
+                     "one training batch in flight per model, inference with horizontal packing where the "
+                     "tree layout allows (cfg1, cfg3); the one-at-a-time baseline runs the plain path",
            "calibrated_ms_per_sample": {f"{k[0]}/{k[1]}": round(v * 1e3, 3) for k, v in costs.items()},
            "max_samples_per_request": SERVE_MAX}
+    out["batched_vs_one_at_a_time"] = out["batched"]["samples_per_s"] / out["one_at_a_time"]["samples_per_s"]
     del models, arena
     torch.cuda.empty_cache()
     return out

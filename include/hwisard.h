@@ -180,7 +180,8 @@ int hw_get_sizes(const hw_ctx* ctx, hw_sizes* out);
  * address bit i, the encrypted bit slot it reads (-1: constant 0). */
 int hw_get_ram_slots(const hw_ctx* ctx, int32_t* ram_slot_host, size_t n);
 
-/* Scratch words hw_train_accumulate / hw_infer need for a batch of n samples. */
+/* Scratch words hw_train_accumulate / hw_infer need for a batch of n samples
+ * (per resident block of the persistent kernels; neither grows with n). */
 size_t hw_train_scratch_words(const hw_ctx* ctx, size_t n);
 size_t hw_infer_scratch_words(const hw_ctx* ctx, size_t n);
 
@@ -208,8 +209,13 @@ int hw_encrypt_sample(hw_ctx* ctx, const uint64_t* key_dev, const uint8_t* bits_
 /* Homomorphic training (Algorithm 6): for each sample and RAM j, the Inverse
  * Vertical Packing (Algorithm 5) of b = [label bits, tuple bits of RAM j] and
  * the trivial RLWE (0, Delta) is added into H[j] (mod q_i).  model_dev:
- * model_words device words, updated in place.  scratch_dev: at least
- * hw_train_scratch_words(ctx, n) device words. */
+ * model_words device words, updated in place: each (sample, RAM) item adds
+ * its stored ciphertexts with 64-bit atomic adds (exact integer sums, so the
+ * result does not depend on the order the items finish in), then one pass
+ * reduces H mod q_i; batches larger than 2^64 / max q_i - 2 samples are
+ * split into such passes.  No other work may read or write the model while
+ * the call runs.  scratch_dev: at least hw_train_scratch_words(ctx, n)
+ * device words. */
 int hw_train_accumulate(hw_ctx* ctx, uint64_t* model_dev, const uint64_t* rgsw_dev, size_t n,
                         uint64_t* scratch_dev, size_t scratch_words, void* stream);
 
@@ -352,11 +358,14 @@ int hw_infer_static_scratch(hw_ctx* ctx, const uint64_t* model_dev, const uint64
  * D_{x,rho}(X) = sum_i Dec_rho(a_{i,x}) X^i (the RGSW gadget).
  * resp_dev: n * resp_words (as hw_infer writes them); packed_dev: n *
  * rlwe_words, canonical RLWEs (decrypt with HW_DEC_RLWE: coefficient i is
- * u_i); scratch_dev: hw_pack_scratch_words(ctx) words, reused per sample.
+ * u_i); scratch_dev: scratch_words device words, at least
+ * hw_pack_scratch_words(ctx, 1); hw_pack_responses packs as many samples per
+ * pass as the scratch holds (hw_pack_scratch_words(ctx, n): all n in one
+ * pass, four launches), so a larger scratch means fewer, fuller launches.
  * HW_EINVAL when l * k0 > N. */
 size_t hw_ksk_words(const hw_ctx* ctx);
 int hw_ksk_gen(hw_ctx* ctx, const uint64_t* key_dev, uint64_t seed, uint64_t* ksk_dev, void* stream);
-size_t hw_pack_scratch_words(const hw_ctx* ctx);
+size_t hw_pack_scratch_words(const hw_ctx* ctx, size_t n);
 int hw_pack_responses(hw_ctx* ctx, const uint64_t* ksk_dev, const uint64_t* resp_dev, size_t n,
                       uint64_t* packed_dev, uint64_t* scratch_dev, size_t scratch_words, void* stream);
 

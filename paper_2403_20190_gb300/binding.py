@@ -95,7 +95,7 @@ _SIGS = {
     "hw_infer_plain": (ctypes.c_int, [_VP, _VP, _VP, _SZ, _VP, _VP, _VP, _SZ, _VP]),
     "hw_ksk_words": (_SZ, [_VP]),
     "hw_ksk_gen": (ctypes.c_int, [_VP, _VP, _U64, _VP, _VP]),
-    "hw_pack_scratch_words": (_SZ, [_VP]),
+    "hw_pack_scratch_words": (_SZ, [_VP, _SZ]),
     "hw_pack_responses": (ctypes.c_int, [_VP, _VP, _VP, _SZ, _VP, _VP, _SZ, _VP]),
     "hw_count_classes": (ctypes.c_int, [_VP, _VP, _VP, _SZ, _VP, _SZ, _VP]),
     "hw_pdact_balanced": (ctypes.c_int, [_VP, _VP, _VP, _SZ, _VP, _VP, _VP]),
@@ -357,8 +357,8 @@ def hw_ksk_gen(ctx, key, seed, ksk, stream=None):
     _check(load().hw_ksk_gen(ctx.handle, _ptr(key), seed, _ptr(ksk), _stream(stream)), "hw_ksk_gen")
 
 
-def hw_pack_scratch_words(ctx) -> int:
-    return int(load().hw_pack_scratch_words(ctx.handle))
+def hw_pack_scratch_words(ctx, n=1) -> int:
+    return int(load().hw_pack_scratch_words(ctx.handle, n))
 
 
 def hw_pack_responses(ctx, ksk, resp, n, packed, scratch, stream=None):

@@ -714,12 +714,23 @@ int hw_ctx_fail(int code, const char* msg) { return fail(code, "%s", msg); }
 extern "C" const char* hw_last_error(void) { return g_last_error.c_str(); }
 
 // Persistent-grid scratch per block: two accumulators and, unless it lives in
-// shared memory, one evaluation-form buffer (inference), plus the evaluation
-// forms of the k1 tree slots (training).
+// shared memory, one evaluation-form buffer (inference), plus the k1 tree
+// slots and their evaluation forms (training; the items add their slots into
+// the model themselves, so nothing grows with the batch).
 extern "C" size_t hw_train_scratch_words(const hw_ctx* c, size_t n) {
     if (!c) return 0;
-    return n * c->sz.model_words +
-           (size_t)c->li.ext_grid * (c->li.ext->scratch_rlwe + c->sz.k1) * c->sz.rlwe_words;
+    (void)n;
+    return (size_t)c->li.ext_grid * (c->li.ext->scratch_rlwe + 2 * (size_t)c->sz.k1) * c->sz.rlwe_words;
+}
+
+// Training samples per IVP launch: the model's words grow by < q_i per
+// sample between reductions and must stay below 2^64.
+static size_t train_chunk(const hw_ctx* c) {
+    u64 qmax = 0;
+    for (int i = 0; i < c->sz.r; i++) qmax = c->sz.q[i] > qmax ? c->sz.q[i] : qmax;
+    const u64 lim = (~(u64)0) / qmax - 1;  // (lim + 1) q <= 2^64 - 1
+    const size_t per_launch = (size_t)0x7fffffff / (size_t)c->sz.k0;  // items fit an int
+    return lim < per_launch ? (size_t)lim : per_launch;
 }
 
 extern "C" size_t hw_infer_scratch_words(const hw_ctx* c, size_t n) {
@@ -765,12 +776,14 @@ extern "C" int hw_train_accumulate(hw_ctx* c, uint64_t* model, const uint64_t* r
     size_t need = hw_train_scratch_words(c, n);
     if (scratch_words < need)
         return fail(HW_ENOMEM, "hw_train_accumulate: scratch has %zu words, needs %zu", scratch_words, need);
-    int grid = c->li.ext_grid;
-    u64* out = scratch;
-    u64* acc = scratch + n * c->sz.model_words;
+    const int grid = c->li.ext_grid;
     cudaStream_t st = (cudaStream_t)stream;
-    CUDA_TRY(launch_ivp_train(c->li, rgsw, n, out, acc, grid, st));
-    CUDA_TRY(launch_accumulate(c->li, model, out, n, st));
+    const size_t chunk = train_chunk(c);
+    for (size_t s0 = 0; s0 < n; s0 += chunk) {
+        const size_t m = n - s0 < chunk ? n - s0 : chunk;
+        CUDA_TRY(launch_ivp_train(c->li, rgsw + s0 * c->sz.sample_words, m, model, scratch, grid, st));
+        CUDA_TRY(launch_model_reduce(c->li, model, st));
+    }
     return HW_OK;
 }
 
@@ -897,7 +910,9 @@ extern "C" int hw_ksk_gen(hw_ctx* c, const uint64_t* key, uint64_t seed, uint64_
     return HW_OK;
 }
 
-extern "C" size_t hw_pack_scratch_words(const hw_ctx* c) { return c ? hw_pack_scratch_words_li(c->li) : 0; }
+extern "C" size_t hw_pack_scratch_words(const hw_ctx* c, size_t n) {
+    return c ? hw_pack_scratch_words_li(c->li, n) : 0;
+}
 
 extern "C" int hw_pack_responses(hw_ctx* c, const uint64_t* ksk, const uint64_t* resp, size_t n,
                                  uint64_t* packed, uint64_t* scratch, size_t scratch_words, void* stream) {
@@ -907,10 +922,10 @@ extern "C" int hw_pack_responses(hw_ctx* c, const uint64_t* ksk, const uint64_t*
     if ((size_t)c->sz.k0 * c->prm.n_classes > (size_t)c->sz.n)
         return fail(HW_EINVAL, "hw_pack_responses: %d responses per sample exceed N = %d",
                     c->sz.k0 * c->prm.n_classes, c->sz.n);
-    const size_t need = hw_pack_scratch_words_li(c->li);
+    const size_t need = hw_pack_scratch_words_li(c->li, 1);
     if (scratch_words < need)
-        return fail(HW_ENOMEM, "hw_pack_responses: scratch needs %zu words, got %zu", need, scratch_words);
-    CUDA_TRY(launch_pack(c->li, ksk, resp, n, packed, scratch, (cudaStream_t)stream));
+        return fail(HW_ENOMEM, "hw_pack_responses: scratch needs at least %zu words, got %zu", need, scratch_words);
+    CUDA_TRY(launch_pack(c->li, ksk, resp, n, packed, scratch, scratch_words, (cudaStream_t)stream));
     return HW_OK;
 }
 

@@ -135,14 +135,17 @@ __global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP>::T, ExtCfg<LOGN, LOGE, 
 // z..L+a-1 with an encrypted control C_t: acc <- acc + C_t [x] (acc X^{2^(t-z)}
 // - acc) (BlindRotate with weights -2^k); then the CDEMUX tree over bits
 // 0..z-1, level i splitting L_j into (L_j - C_i [x] L_j, C_i [x] L_j).
-// Outputs: out[item][slot] for every stored ciphertext index.
-// Per-block scratch: two accumulators, their evaluation forms, and the
-// evaluation forms of the k1 tree slots.
+// Outputs: the item's k1 stored ciphertexts are added into H[j] with 64-bit
+// atomic adds of the residues, unreduced (exact integer sums: the order in
+// which the batch's items arrive does not change them); the caller reduces
+// H mod q_i afterwards and keeps (n + 1) q_i < 2^64.
+// Per-block scratch: two accumulators, their evaluation form (outside mode
+// 1), the evaluation forms of the k1 tree slots and the k1 tree slots.
 // ---------------------------------------------------------------------------
 template <int LOGN, int LOGE, int NP, int SM>
 __global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP, SM>::T, ExtCfg<LOGN, LOGE, NP, SM>::MINB)
     k_ivp_train(const DevCtx* __restrict__ Cp, const u64* __restrict__ rgsw, int n_items,
-                u64* __restrict__ out, u64* __restrict__ scratch) {
+                u64* __restrict__ model, u64* __restrict__ scratch) {
     using X = ExtCfg<LOGN, LOGE, NP, SM>;
     extern __shared__ u64 smem[];
     Xchg xc{smem, SM ? smem : smem + NP * X::PADDED, X::PADDED, 0};
@@ -151,18 +154,18 @@ __global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP, SM>::T, ExtCfg<LOGN, LO
     const int tid = threadIdx.x, T = blockDim.x;
     const size_t rl = C.rlwe_words;
     constexpr int NB = SM == 1 ? 2 : 3;  // per-block RLWE buffers besides the tree
-    u64* blk = scratch + (size_t)blockIdx.x * (NB + C.k1) * rl;
+    u64* blk = scratch + (size_t)blockIdx.x * (NB + 2 * C.k1) * rl;
     u64* acc[2] = {blk, blk + rl};
     // one evaluation-form buffer (in shared memory in mode 1), updated in
     // place: the external product reads each thread's own words of a prime
     // before it writes them
     u64* accn = SM == 1 ? smem + NP * X::PADDED : blk + 2 * rl;
     u64* tn = blk + NB * rl;  // evaluation forms of the tree slots
+    u64* Lout = tn + (size_t)C.k1 * rl;  // the tree slots (the item's outputs)
     const int kbits = C.L + C.a;
     for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
         const int i = item / C.k0, j = item % C.k0;
         const u64* sample = rgsw + (size_t)i * C.sample_words;
-        u64* Lout = out + (size_t)item * C.k1 * rl;
         // last encrypted rotation bit: its CMUX writes straight into slot 0
         int last = -1;
         for (int t = C.z; t < kbits; t++)
@@ -220,6 +223,11 @@ __global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP, SM>::T, ExtCfg<LOGN, LO
             }
             __syncthreads();
         }
+        // the item's stored ciphertexts into H[j] (the last CMUX or gate
+        // ended with a barrier, so Lout is complete)
+        unsigned long long* Hj = (unsigned long long*)(model + (size_t)j * C.k1 * rl);
+        for (size_t w = tid; w < (size_t)C.k1 * rl; w += T) atomicAdd(Hj + w, (unsigned long long)Lout[w]);
+        __syncthreads();  // Lout is read before the next item rewrites it
     }
 }
 
@@ -695,8 +703,9 @@ struct ExtVariant {
     static constexpr int SCRATCH_RLWE = SM == 1 ? 2 : 3;  // per-block RLWE buffers (inference)
     static cudaError_t ivp(const LaunchInfo& li, const uint64_t* rgsw, int items, uint64_t* out,
                            uint64_t* acc, int grid, cudaStream_t st) {
-        // per-block scratch: two accumulators, (their evaluation form,) the tree slots
-        Launch L(li, grid, st, acc, (size_t)grid * (SCRATCH_RLWE + li.k1) * li.rlwe_words * sizeof(u64));
+        // per-block scratch: two accumulators, (their evaluation form,) the tree
+        // slots' evaluation forms and the tree slots
+        Launch L(li, grid, st, acc, (size_t)grid * (SCRATCH_RLWE + 2 * li.k1) * li.rlwe_words * sizeof(u64));
         return cudaLaunchKernelEx(&L.cfg, k_ivp_train<LOGN, LOGE, NP, SM>, li.dctx, (const u64*)rgsw, items,
                                   (u64*)out, (u64*)acc);
     }

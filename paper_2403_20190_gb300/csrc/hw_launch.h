@@ -22,7 +22,7 @@ struct ExtOps {
     cudaError_t (*encrypt)(const LaunchInfo&, const uint64_t* key, const uint8_t* bits,
                            const uint32_t* labels, int slot0, int n_enc, unsigned blocks,
                            uint64_t seed, uint64_t first, uint64_t* out, cudaStream_t);
-    cudaError_t (*ivp)(const LaunchInfo&, const uint64_t* rgsw, int items, uint64_t* out,
+    cudaError_t (*ivp)(const LaunchInfo&, const uint64_t* rgsw, int items, uint64_t* model,
                        uint64_t* acc, int grid, cudaStream_t);
     cudaError_t (*vp)(const LaunchInfo&, const uint64_t* model, const uint64_t* rgsw, int items,
                       uint64_t* resp, uint64_t* acc, int grid, int packed, cudaStream_t);
@@ -70,10 +70,11 @@ cudaError_t launch_encode(const LaunchInfo& li, const uint8_t* values, size_t n,
 cudaError_t launch_encrypt(const LaunchInfo& li, const uint64_t* key, const uint8_t* bits,
                            const uint32_t* labels, size_t n, uint64_t seed, uint64_t first,
                            uint64_t* out, cudaStream_t st);
-cudaError_t launch_ivp_train(const LaunchInfo& li, const uint64_t* rgsw, size_t n, uint64_t* out,
+// IVP training adds into the model unreduced; launch_model_reduce brings it
+// back below q_i (at most HW_TRAIN_MAX_BATCH(q) samples in between).
+cudaError_t launch_ivp_train(const LaunchInfo& li, const uint64_t* rgsw, size_t n, uint64_t* model,
                              uint64_t* acc, int grid, cudaStream_t st);
-cudaError_t launch_accumulate(const LaunchInfo& li, uint64_t* model, const uint64_t* out, size_t n,
-                              cudaStream_t st);
+cudaError_t launch_model_reduce(const LaunchInfo& li, uint64_t* model, cudaStream_t st);
 cudaError_t launch_vp_infer(const LaunchInfo& li, const uint64_t* model, const uint64_t* rgsw,
                             size_t n, uint64_t* resp, uint64_t* acc, int grid, cudaStream_t st,
                             int packed = 0);
@@ -106,11 +107,11 @@ cudaError_t launch_import_rgsw(const LaunchInfo& li, const uint64_t* in, size_t 
 cudaError_t launch_ntt_batch(const LaunchInfo& li, uint64_t* poly, size_t count, int inverse,
                              cudaStream_t st);
 // PackingKeySwitching (k_pack.cu).
-size_t hw_pack_scratch_words_li(const LaunchInfo& li);
+size_t hw_pack_scratch_words_li(const LaunchInfo& li, size_t group);
 cudaError_t launch_ksk_gen(const LaunchInfo& li, const uint64_t* key, uint64_t seed, uint64_t* ksk,
                            cudaStream_t st);
 cudaError_t launch_pack(const LaunchInfo& li, const uint64_t* ksk, const uint64_t* resp, size_t n,
-                        uint64_t* packed, uint64_t* scratch, cudaStream_t st);
+                        uint64_t* packed, uint64_t* scratch, size_t scratch_words, cudaStream_t st);
 cudaError_t hw_pack_kernels_init(const LaunchInfo& li);
 
 // Shared-memory attributes of the context's kernels (its ring size, its

@@ -56,33 +56,42 @@ __global__ void __launch_bounds__(Geo<LOGN>::T)
     }
 }
 
-// One sample's responses (k LWEs of r*(N+1) words) to A[j][x][i] = a_{i,x}
-// at prime j (0 for i >= k), by 32 x 32 tiles through shared memory.
-__global__ void k_pack_transpose(const DevCtx* __restrict__ Cp, const u64* __restrict__ resp, int k,
+// The responses of a group of samples (k LWEs of r*(N+1) words each) to
+// A[s][j][x][i] = a_{i,x} of sample s at prime j, i < kp (kp = k rounded up
+// to 32; 0 for i >= k), by 32 x 32 tiles through shared memory.  Grid z runs
+// over (sample, prime).
+__global__ void k_pack_transpose(const DevCtx* __restrict__ Cp, const u64* __restrict__ resp, int k, int kp,
                                  u64* __restrict__ A) {
     __shared__ u64 tile[32][33];
     const DevCtx& C = *Cp;
     const int N = C.n;
     const size_t lw = C.lwe_words;
-    const int x0 = blockIdx.x * 32, i0 = blockIdx.y * 32, j = blockIdx.z;
+    const int x0 = blockIdx.x * 32, i0 = blockIdx.y * 32;
+    const int j = blockIdx.z % C.r;
+    const size_t smp = blockIdx.z / C.r;
+    const u64* rs = resp + smp * (size_t)k * lw;
+    u64* As = A + smp * (size_t)C.r * N * kp;
     const int tx = threadIdx.x, ty = threadIdx.y;
     for (int iy = ty; iy < 32; iy += blockDim.y) {
         const int i = i0 + iy;
-        tile[iy][tx] = i < k ? resp[(size_t)i * lw + (size_t)j * (N + 1) + x0 + tx] : 0;
+        tile[iy][tx] = i < k ? rs[(size_t)i * lw + (size_t)j * (N + 1) + x0 + tx] : 0;
     }
     __syncthreads();
     for (int xy = ty; xy < 32; xy += blockDim.y)
-        A[((size_t)j * N + x0 + xy) * N + i0 + tx] = tile[tx][xy];
+        As[((size_t)j * N + x0 + xy) * kp + i0 + tx] = tile[tx][xy];
 }
 
-// B[j][i] = b_i at prime j (0 for i >= k).
-__global__ void k_pack_b(const DevCtx* __restrict__ Cp, const u64* __restrict__ resp, int k,
+// B[s][j][i] = b_i of sample s at prime j (0 for i >= k).
+__global__ void k_pack_b(const DevCtx* __restrict__ Cp, const u64* __restrict__ resp, int k, int n_smp,
                          u64* __restrict__ B) {
     const DevCtx& C = *Cp;
     const int N = C.n;
-    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < C.r * N; idx += gridDim.x * blockDim.x) {
-        const int j = idx / N, i = idx % N;
-        B[idx] = i < k ? resp[(size_t)i * C.lwe_words + (size_t)j * (N + 1) + N] : 0;
+    const size_t total = (size_t)n_smp * C.r * N;
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const size_t smp = idx / ((size_t)C.r * N);
+        const int j = (int)((idx / N) % C.r), i = (int)(idx % N);
+        B[idx] = i < k ? resp[(smp * k + i) * C.lwe_words + (size_t)j * (N + 1) + N] : 0;
     }
 }
 
@@ -90,19 +99,23 @@ __global__ void k_pack_b(const DevCtx* __restrict__ Cp, const u64* __restrict__ 
 // sum KS_{x,rho} * D_{x,rho} in evaluation form (both components).
 template <int LOGN>
 __global__ void __launch_bounds__(Geo<LOGN>::T)
-    k_pack_mac(const DevCtx* __restrict__ Cp, const u64* __restrict__ ksk, const u64* __restrict__ A,
-               u64* __restrict__ partial) {
+    k_pack_mac(const DevCtx* __restrict__ Cp, const u64* __restrict__ ksk, const u64* __restrict__ A, int kp,
+               int chunks, u64* __restrict__ partial) {
     extern __shared__ u64 smem[];
     constexpr int N = Ring<LOGN>::N, T = Ring<LOGN>::T;
     Xchg xc{smem, smem + Ring<LOGN>::PADDED, Ring<LOGN>::PADDED, 0};
     const DevCtx& C = *Cp;
     const int tid = threadIdx.x, r = C.r;
-    const int ch = blockIdx.x / r, j = (int)(blockIdx.x % r);
+    const int j = (int)(blockIdx.x % r);
+    const int ch = (int)((blockIdx.x / r) % chunks);
+    const size_t smp = blockIdx.x / ((size_t)r * chunks);
+    A += smp * (size_t)r * N * kp;
+    partial += smp * (size_t)chunks * 2 * r * N;
     const PrimeConst P = C.P[j];
     const u64 q = P.q;
     const size_t rl = C.rlwe_words;
     const int pairs = N * C.dnum;
-    const int per = (pairs + HW_PACK_CHUNKS - 1) / HW_PACK_CHUNKS;
+    const int per = (pairs + chunks - 1) / chunks;
     const int p0 = ch * per, p1 = p0 + per < pairs ? p0 + per : pairs;
     u64 acc[2][16];
 #pragma unroll
@@ -111,11 +124,13 @@ __global__ void __launch_bounds__(Geo<LOGN>::T)
         const int x = pr / C.dnum, rho = pr % C.dnum;
         const int gi = rho / C.dpp, gk = rho % C.dpp;
         const u64 qi = C.P[gi].q;
-        const u64* Arow = A + ((size_t)gi * N + x) * N;
+        const u64* Arow = A + ((size_t)gi * N + x) * kp;
         u64 v[16];
 #pragma unroll
-        for (int kk = 0; kk < 16; kk++)
-            v[kk] = lift_small(gadget_digit(centre(Arow[tid + kk * T], qi), gk, C.dpp, C.log_beta), q);
+        for (int kk = 0; kk < 16; kk++) {
+            const int i = tid + kk * T;
+            v[kk] = i < kp ? lift_small(gadget_digit(centre(Arow[i], qi), gk, C.dpp, C.log_beta), q) : 0;
+        }
         ntt_fwd1<LOGN>(v, xc, C, j);
         const u64* ka = ksk + (size_t)pr * rl + (size_t)(0 * r + j) * N + tid;
         const u64* kb = ksk + (size_t)pr * rl + (size_t)(1 * r + j) * N + tid;
@@ -137,20 +152,24 @@ __global__ void __launch_bounds__(Geo<LOGN>::T)
 template <int LOGN>
 __global__ void __launch_bounds__(Geo<LOGN>::T)
     k_pack_finish(const DevCtx* __restrict__ Cp, const u64* __restrict__ partial, const u64* __restrict__ B,
-                  u64* __restrict__ out) {
+                  int chunks, u64* __restrict__ out) {
     extern __shared__ u64 smem[];
     constexpr int N = Ring<LOGN>::N, T = Ring<LOGN>::T;
     Xchg xc{smem, smem + Ring<LOGN>::PADDED, Ring<LOGN>::PADDED, 0};
     const DevCtx& C = *Cp;
     const int tid = threadIdx.x, r = C.r;
-    const int comp = blockIdx.x / r, j = (int)(blockIdx.x % r);
+    const int j = (int)(blockIdx.x % r), comp = (int)((blockIdx.x / r) % 2);
+    const size_t smp = blockIdx.x / ((size_t)2 * r);
+    partial += smp * (size_t)chunks * 2 * r * N;
+    B += smp * (size_t)r * N;
+    out += smp * C.rlwe_words;
     const PrimeConst P = C.P[j];
     const u64 q = P.q;
     u64 v[16];
 #pragma unroll
     for (int e = 0; e < 16; e++) {
         u64 s = 0;
-        for (int ch = 0; ch < HW_PACK_CHUNKS; ch++)
+        for (int ch = 0; ch < chunks; ch++)
             s = add_mod(s, partial[(((size_t)ch * 2 + comp) * r + j) * N + e * T + tid], q);
         v[e] = shoup_mul_lazy(s, C.n_inv[j], C.n_inv_s[j], q);
     }
@@ -173,9 +192,22 @@ __global__ void __launch_bounds__(Geo<LOGN>::T)
             return cudaErrorInvalidValue; \
     }
 
-size_t hw_pack_scratch_words_li(const LaunchInfo& li) {
+// A pass packs a group of S samples: per sample the transposed masks
+// (r * N * kp words, kp = k rounded up to 32) and the b values (r * N), and
+// the group's partial sums (chunks(S) * 2 * r * N words per sample), with
+// chunks(S) picked so that the group's multiply-accumulate grid runs about
+// eight blocks per SM.
+static int pack_chunks(const LaunchInfo& li, size_t group) {
+    const size_t want = (8 * (size_t)li.sm_count + group * li.r - 1) / (group * li.r);
+    return want < 1 ? 1 : (want > HW_PACK_CHUNKS ? HW_PACK_CHUNKS : (int)want);
+}
+
+static size_t pack_kp(const LaunchInfo& li) { return ((size_t)li.n_classes * li.k0 + 31) / 32 * 32; }
+
+size_t hw_pack_scratch_words_li(const LaunchInfo& li, size_t group) {
+    if (group < 1) group = 1;
     const size_t N = (size_t)li.n, r = (size_t)li.r;
-    return r * N * N + r * N + (size_t)HW_PACK_CHUNKS * 2 * r * N;
+    return group * (r * N * pack_kp(li) + r * N + (size_t)pack_chunks(li, group) * 2 * r * N);
 }
 
 cudaError_t launch_ksk_gen(const LaunchInfo& li, const uint64_t* key, uint64_t seed, uint64_t* ksk,
@@ -192,21 +224,31 @@ cudaError_t launch_ksk_gen(const LaunchInfo& li, const uint64_t* key, uint64_t s
 }
 
 cudaError_t launch_pack(const LaunchInfo& li, const uint64_t* ksk, const uint64_t* resp, size_t n,
-                        uint64_t* packed, uint64_t* scratch, cudaStream_t st) {
+                        uint64_t* packed, uint64_t* scratch, size_t scratch_words, cudaStream_t st) {
     const int N = li.n, r = li.r;
     const int k = li.n_classes * li.k0;
-    u64* A = scratch;
-    u64* Bv = A + (size_t)r * N * N;
-    u64* partial = Bv + (size_t)r * N;
-    for (size_t s = 0; s < n; s++) {
-        const u64* rs = resp + s * (size_t)k * li.lwe_words;
-        u64* out = packed + s * li.rlwe_words;
-        k_pack_transpose<<<dim3(N / 32, N / 32, r), dim3(32, 8), 0, st>>>(li.dctx, rs, k, A);
-        k_pack_b<<<(unsigned)((r * N + 255) / 256), 256, 0, st>>>(li.dctx, rs, k, Bv);
-#define B(L)                                                                                          \
-    case L:                                                                                           \
-        k_pack_mac<L><<<HW_PACK_CHUNKS * r, Geo<L>::T, Geo<L>::XCHG_BYTES, st>>>(li.dctx, ksk, A, partial); \
-        k_pack_finish<L><<<2 * r, Geo<L>::T, Geo<L>::XCHG_BYTES, st>>>(li.dctx, partial, Bv, out);        \
+    const int kp = (int)pack_kp(li);
+    // the largest group the scratch holds (the caller checked one sample fits)
+    size_t group = n;
+    while (group > 1 && hw_pack_scratch_words_li(li, group) > scratch_words) group--;
+    for (size_t s0 = 0; s0 < n; s0 += group) {
+        const size_t S = n - s0 < group ? n - s0 : group;
+        const int chunks = pack_chunks(li, S);
+        u64* A = scratch;
+        u64* Bv = A + S * (size_t)r * N * kp;
+        u64* partial = Bv + S * (size_t)r * N;
+        const u64* rs = resp + s0 * (size_t)k * li.lwe_words;
+        u64* out = packed + s0 * li.rlwe_words;
+        k_pack_transpose<<<dim3(N / 32, kp / 32, (unsigned)(r * S)), dim3(32, 8), 0, st>>>(li.dctx, rs, k, kp, A);
+        size_t bb = (S * r * N + 255) / 256;
+        if (bb > (size_t)li.sm_count * 32) bb = (size_t)li.sm_count * 32;
+        k_pack_b<<<(unsigned)bb, 256, 0, st>>>(li.dctx, rs, k, (int)S, Bv);
+#define B(L)                                                                                            \
+    case L:                                                                                             \
+        k_pack_mac<L><<<(unsigned)(S * chunks * r), Geo<L>::T, Geo<L>::XCHG_BYTES, st>>>(li.dctx, ksk, A, kp,  \
+                                                                                       chunks, partial); \
+        k_pack_finish<L><<<(unsigned)(S * 2 * r), Geo<L>::T, Geo<L>::XCHG_BYTES, st>>>(li.dctx, partial, Bv,  \
+                                                                                     chunks, out);     \
         break;
         HW_PACK_DISPATCH(li.log_n, B)
 #undef B

@@ -8,18 +8,15 @@
 
 #include <vector>
 
-// H[j][t] += sum over the batch of out[i][j][t] (mod q), one word per thread.
-__global__ void k_accumulate(const DevCtx* __restrict__ Cp, u64* __restrict__ model,
-                             const u64* __restrict__ out, int n) {
+// H mod q_i after a training batch's atomic additions (words below
+// (n + 1) q_i < 2^64), one word per thread.
+__global__ void k_model_reduce(const DevCtx* __restrict__ Cp, u64* __restrict__ model) {
     const DevCtx& C = *Cp;
     const size_t total = C.model_words;
     for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (size_t)gridDim.x * blockDim.x) {
         const int p = (int)(((idx % C.rlwe_words) / C.n) % C.r);
-        const u64 q = C.P[p].q;
-        u64 s = model[idx];
-        for (int i = 0; i < n; i++) s = add_mod(s, out[(size_t)i * total + idx], q);
-        model[idx] = s;
+        model[idx] = reduce64(model[idx], C.P[p]);
     }
 }
 
@@ -116,12 +113,11 @@ cudaError_t launch_ivp_train(const LaunchInfo& li, const uint64_t* rgsw, size_t 
     return e;
 }
 
-cudaError_t launch_accumulate(const LaunchInfo& li, uint64_t* model, const uint64_t* out, size_t n,
-                              cudaStream_t st) {
+cudaError_t launch_model_reduce(const LaunchInfo& li, uint64_t* model, cudaStream_t st) {
     int threads = 256;
     size_t blocks = (li.model_words + threads - 1) / threads;
     if (blocks > (size_t)li.sm_count * 64) blocks = (size_t)li.sm_count * 64;
-    k_accumulate<<<(unsigned)blocks, threads, 0, st>>>(li.dctx, model, out, (int)n);
+    k_model_reduce<<<(unsigned)blocks, threads, 0, st>>>(li.dctx, model);
     (*li.launches)++;
     return cudaGetLastError();
 }

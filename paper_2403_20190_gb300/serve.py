@@ -17,9 +17,13 @@ Memory: every batch takes one chunk of a device arena allocated up front
 (arena.py) and carves its buffers from it, so admission by footprint is
 admission by placement and the loop never calls the CUDA allocator.
 
-Order: among pending requests the server launches the group with the least
-expected GPU time, less the age of its oldest request (shortest expected
-batch first with aging, so no request waits forever).  Expected times are
+Order: policy "fifo" (the default) launches the group whose oldest request
+arrived first: every request of the same (configuration, kind) that is
+pending by then joins it, so a backlog turns into few large batches and no
+request is overtaken by later ones (the tail latency stays that of arrival
+order).  Policy "sjf" launches the group with the least expected GPU time,
+less the age of its oldest request (shortest expected batch first with
+aging, so no request waits forever).  Expected times are
 per-sample costs per (configuration, kind): calibrate() times one
 single-sample batch of each alone, and batches that ran with nothing else
 on the GPU refine them (a batch that overlapped others is slowed by them
@@ -125,7 +129,7 @@ class _Batch:
 class Server:
     def __init__(self, models: dict, hbm_budget_bytes: int = None, n_streams: int = 2,
                  max_batch_samples: int = 256, keep_responses: bool = False, arena=None,
-                 aging: float = 1.0, packed_infer: bool = False):
+                 aging: float = 1.0, packed_infer: bool = False, policy: str = "fifo"):
         """models: name -> ResidentModel.  The arena (or a new one of
         hbm_budget_bytes on the models' device) holds every batch in flight.
         packed_infer answers inference with horizontal packing
@@ -142,6 +146,9 @@ class Server:
         self.keep_responses = keep_responses
         self.aging = aging
         self.packed_infer = packed_infer
+        if policy not in ("fifo", "sjf"):
+            raise ValueError(f"unknown policy {policy!r}")
+        self.policy = policy
         self.cost = {}  # (cfg name, kind) -> smoothed GPU seconds per sample
 
     @property
@@ -259,7 +266,10 @@ class Server:
                 for (nm, kind), (group, n) in self._groups(pending, training).items():
                     rm = self.models[nm]
                     oldest = min(r.t_arrive for r in group)
-                    score = self.expected(rm, kind, n) - self.aging * (now - oldest)
+                    if self.policy == "fifo":
+                        score = oldest
+                    else:
+                        score = self.expected(rm, kind, n) - self.aging * (now - oldest)
                     ranked.append((score, oldest, nm, kind, group))
                 ranked.sort(key=lambda x: (x[0], x[1]))
                 placed = None

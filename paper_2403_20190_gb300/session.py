@@ -130,7 +130,7 @@ class Session:
     def pack_responses(self, ksk, resp, n, scratch=None, stream=None):
         """One RLWE per test sample: coefficient c * k0 + j is u[c][j]."""
         if scratch is None:
-            scratch = self.words(B.hw_pack_scratch_words(self.ctx), zero=False)
+            scratch = self.words(B.hw_pack_scratch_words(self.ctx, n), zero=False)
         packed = self.words(int(n) * self.sz["rlwe_words"], zero=False)
         B.hw_pack_responses(self.ctx, ksk, resp, n, packed, scratch, stream)
         return packed

@@ -56,3 +56,23 @@ def test_cfg2_packed_rlwe_decrypts_to_the_responses():
     # everything above the l * k0 packed slots decrypts to 0
     full = s.decrypt_rlwe(R["key"], packed, 2).view(2, -1)
     assert not full[:, cfg.n_classes * s.sz["k0"]:].any()
+
+
+@pytest.mark.parametrize("name", ["zL", "zgtL"])
+def test_grouped_passes_equal_one_pass(name):
+    """A scratch for one sample packs sample by sample, one for all samples in
+    one pass, one for two samples in passes of two and a ragged last pass:
+    the packed RLWEs are the same bits."""
+    from paper_2403_20190_gb300 import binding as B
+    cfg = tiny_cfg(name)
+    R = run_pipeline(cfg, 7, 5)
+    s = R["sess"]
+    ksk = s.ksk_gen(R["key"], 11)
+    outs = []
+    for group in (1, 2, 5):
+        scr = s.words(B.hw_pack_scratch_words(s.ctx, group), zero=False)
+        outs.append(s.pack_responses(ksk, R["resp"], 5, scratch=scr))
+    torch.cuda.synchronize()
+    assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
+    with pytest.raises(B.HwError):
+        s.pack_responses(ksk, R["resp"], 5, scratch=s.words(B.hw_pack_scratch_words(s.ctx, 1) - 1))
