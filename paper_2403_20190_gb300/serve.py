@@ -196,13 +196,20 @@ class Server:
 
     def _retire(self, b, now):
         if b.kind == "infer":
-            lab = b.bufs["labels_out"].cpu().numpy()
             off = 0
             for r in b.reqs:
-                r.labels_out = lab[off:off + r.n].copy()
                 if self.keep_responses:
                     rw = b.rm.sess.sz["resp_words"]
                     r.resp = b.bufs["resp"][off * rw:(off + r.n) * rw].clone()
+                off += r.n
+            # a blocking copy on the same stream: the clones above have run
+            # before the chunk goes back to the arena (the next batch may
+            # overwrite it from another stream at once)
+            lab = b.bufs["labels_out"].cpu().numpy()
+            torch.cuda.current_stream().synchronize()
+            off = 0
+            for r in b.reqs:
+                r.labels_out = lab[off:off + r.n].copy()
                 off += r.n
         for r in b.reqs:
             r.t_done = now
