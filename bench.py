@@ -478,7 +478,7 @@ class Workload:
         keys = ["encrypt_train", "train", "encrypt_test", "infer", "decrypt_pdact"]
         return {kn: evs[a].elapsed_time(evs[b]) for a, b, kn in zip(names[:-1], names[1:], keys)}
 
-    def rooflines(self, ph, local):
+    def rooflines(self, ph, local, ceiling=None):
         """Roofline of the VP kernel (the dominant one: its graph's average
         duration over the timed steps) and of the IVP kernel (the training
         call of the phase breakdown), against the integer-multiply peak."""
@@ -503,6 +503,12 @@ class Workload:
               * self.bsz, "launch_ms": vp_ms, "peak_kind": peak_kind,
               "work": f"{alg['ext_infer_per_sample']} external products x {alg['per_ext_modmul']} modular "
                       f"products per test sample, {self.bsz} test samples per launch"}
+        if ceiling:
+            # the measured issue ceiling of the butterflies this context runs
+            # (register-only loops, hw_butterfly_rates), beside the derived peak
+            ct, gs = ("ct32", "gs32") if word_bits == 32 else ("ct64", "gs64")
+            vp["butterfly_ceiling"] = {"ct_t_per_s": ceiling[ct] / 1e3, "gs_t_per_s": ceiling[gs] / 1e3,
+                                       "source": "hw_butterfly_rates, measured in this run"}
         train_modmul = alg["ext_train_per_sample"] * self.bsz * alg["per_ext_modmul"]
         ivp_achieved = train_modmul / (ph["train"] / 1000.0)
         ivp = {"bound": "alu", "kernel": "k_ivp_train + k_accumulate", "achieved": ivp_achieved / 1e12,
@@ -539,9 +545,9 @@ class Workload:
                 "polys": count, "n": nn, "prime_bits": self.cfg.prime_bits, "ms_per_launch": t * 1000.0,
                 "variant": f"radix {1 << g['ntt_loge']}, {32 * g['ntt_limbs']}-bit words"}
 
-    def summary(self, elapsed_ms, steps, ws, local, with_ntt=True):
+    def summary(self, elapsed_ms, steps, ws, local, with_ntt=True, ceiling=None):
         ph = self.phases(1000 + steps)
-        vp, ivp, _ = self.rooflines(ph, local)
+        vp, ivp, _ = self.rooflines(ph, local, ceiling)
         out = {"workload": workload_name(self.cfg), "batch": self.bsz, "steps": steps,
                "samples_per_s": 2 * self.bsz * steps * ws / (elapsed_ms / 1000.0),
                "ms_per_step": elapsed_ms / steps,
@@ -582,6 +588,7 @@ def gpu_arm(args, ws, rank, local, pg):
         for nm in sorted(others - {args.config}):
             tuned_geometry(get_config(nm), local)
     geo = "auto" if args.geometry == "auto" else None
+    ceiling = B.hw_butterfly_rates(local)  # before any context holds the GPU
     bsz = args.batch or DEFAULT_BATCH.get(args.config, 16)
     w = Workload(args.config, local, bsz, geometry if geometry is not None else None, rank)
     cfg, sess, sz, st, stream = w.cfg, w.sess, w.sz, w.st, w.stream
@@ -613,7 +620,7 @@ def gpu_arm(args, ws, rank, local, pg):
     total_samples = 2 * bsz * args.steps * ws
     value = total_samples / (elapsed_ms / 1000.0)
     ph = w.phases(args.warmup + args.steps)
-    roofline, roofline_ivp, alg = w.rooflines(ph, local)
+    roofline, roofline_ivp, alg = w.rooflines(ph, local, ceiling)
     healthy("the timed steps")
 
     key, model = w.key, w.model
@@ -773,7 +780,8 @@ def gpu_arm(args, ws, rank, local, pg):
         pw = Workload(nm, local, DEFAULT_BATCH[nm], geo, rank)
         pw.warm(1)
         pms = pw.timed(1, args.per_config_steps, barrier)
-        per_config[nm], _ = pw.summary(pms, args.per_config_steps, ws, local, with_ntt=not args.no_ntt)
+        per_config[nm], _ = pw.summary(pms, args.per_config_steps, ws, local, with_ntt=not args.no_ntt,
+                                       ceiling=ceiling)
         del pw
         torch.cuda.synchronize()
         torch.cuda.empty_cache()

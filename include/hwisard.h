@@ -410,6 +410,14 @@ int hw_import_rgsw(hw_ctx* ctx, const uint64_t* canonical_dev, size_t count, uin
 int hw_ntt_forward(hw_ctx* ctx, uint64_t* poly_dev, size_t count, void* stream);
 int hw_ntt_inverse(hw_ctx* ctx, uint64_t* poly_dev, size_t count, void* stream);
 
+/* Integer-issue ceiling of the library's butterfly forms on `cuda_device`
+ * (no counterpart in the paper: the measured denominator beside the
+ * derived multiply-count peak).  Register-only loops, one 512-thread block
+ * per SM; out_host[0..3] = G butterflies/s of the 64-bit lazy Cooley-Tukey,
+ * the 64-bit Harvey Gentleman-Sande, and their 32-bit forms.  Synchronous;
+ * takes about a second of the whole GPU. */
+int hw_butterfly_rates(int cuda_device, double* out_host);
+
 /* Number of kernel launches the library has issued since the context was
  * created (all calls). */
 uint64_t hw_launch_count(const hw_ctx* ctx);

@@ -108,6 +108,7 @@ _SIGS = {
     "hw_model_header_check": (ctypes.c_int, [ctypes.POINTER(HwParams), _VP, _SZ, ctypes.POINTER(_U64)]),
     "hw_ntt_forward": (ctypes.c_int, [_VP, _VP, _SZ, _VP]),
     "hw_ntt_inverse": (ctypes.c_int, [_VP, _VP, _SZ, _VP]),
+    "hw_butterfly_rates": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "hw_launch_count": (_U64, [_VP]),
     "hw_last_error": (ctypes.c_char_p, []),
 }
@@ -435,6 +436,13 @@ def hw_ntt_forward(ctx, poly, count, stream=None):
 
 def hw_ntt_inverse(ctx, poly, count, stream=None):
     _check(load().hw_ntt_inverse(ctx.handle, _ptr(poly), count, _stream(stream)), "hw_ntt_inverse")
+
+
+def hw_butterfly_rates(device: int = 0) -> dict:
+    """Measured G butterflies/s of the library's butterfly forms (register-only)."""
+    out = (ctypes.c_double * 4)()
+    _check(load().hw_butterfly_rates(device, out), "hw_butterfly_rates")
+    return {"ct64": out[0], "gs64": out[1], "ct32": out[2], "gs32": out[3]}
 
 
 def hw_launch_count(ctx) -> int:

@@ -70,7 +70,43 @@ __global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP>::T, ExtCfg<LOGN, LOGE, 
             A[2 * c0 + 1] = add_mod(shoup_mul(w.v[2], P.r2, mr2_s, q), shoup_mul(w.v[3], mr, mr_s, q), q);
         }
         __syncthreads();
-        // a and e transformed together (NP == 2) or one after the other
+        const u64 gM = (bit && j == gi) ? to_mont(C.gconst[rho], P) : 0;
+        const u64* sM = key + (size_t)(r + j) * N;
+        u64* da = dst_row + (size_t)(0 * r + j) * N;
+        u64* db = dst_row + (size_t)(1 * r + j) * N;
+        bool ext64 = true;
+        if constexpr (LOGN <= 11) ext64 = !C.ext32;
+        if (NP == 1 && ext64) {
+            // one polynomial in registers at a time: a is transformed and
+            // written, a s waits in A (each thread's own slots), then e
+            u64 w[1][E];
+#pragma unroll
+            for (int kk = 0; kk < E; kk++) w[0][kk] = A[tid + kk * T];
+            ntt_fwd<LOGN, LOGE, 1>(w, xc, C, j);
+            __syncthreads();  // every thread has read its part of A
+#pragma unroll
+            for (int e = 0; e < E; e++) {
+                const int pos = e * T + tid;  // evaluation position E*tid + e, thread-major
+                const u64 aM = reduce_full(w[0][e], P);
+                A[pos] = mont_mul(aM, sM[pos], P);  // REDC(aR * sR) = a s R
+                // the evaluation form of the constant polynomial g is g everywhere
+                da[pos] = row < C.dnum ? aM : add_mod(aM, gM, q);
+            }
+#pragma unroll
+            for (int kk = 0; kk < E; kk++) {
+                const int x = tid + kk * T;
+                w[0][kk] = shoup_mul(from_signed((int64_t)ebuf[x], q), mr, mr_s, q);  // e R
+            }
+            ntt_fwd<LOGN, LOGE, 1>(w, xc, C, j);
+#pragma unroll
+            for (int e = 0; e < E; e++) {
+                const int pos = e * T + tid;
+                const u64 bM = add_mod(A[pos], reduce_full(w[0][e], P), q);
+                db[pos] = row < C.dnum ? add_mod(bM, gM, q) : bM;
+            }
+            continue;
+        }
+        // a and e transformed together (NP == 2), or the 32-bit transform
         u64 v[2][E];
 #pragma unroll
         for (int kk = 0; kk < E; kk++) {
@@ -108,10 +144,6 @@ __global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP>::T, ExtCfg<LOGN, LOGE, 
                 ntt_fwd<LOGN, LOGE, 1>(reinterpret_cast<u64(&)[1][E]>(v[1]), xc, C, j);
             }
         }
-        const u64 gM = (bit && j == gi) ? to_mont(C.gconst[rho], P) : 0;
-        const u64* sM = key + (size_t)(r + j) * N;
-        u64* da = dst_row + (size_t)(0 * r + j) * N;
-        u64* db = dst_row + (size_t)(1 * r + j) * N;
 #pragma unroll
         for (int e = 0; e < E; e++) {
             const int pos = e * T + tid;  // evaluation position E*tid + e, thread-major
