@@ -122,7 +122,10 @@ typedef struct hw_geometry {
                                   memory beside one exchange buffer (instead of two): 0 nothing;
                                   1 the accumulator's evaluation form (2*r*N words; HW_EINVAL
                                   where it does not fit); 2 the accumulator polynomials of the
-                                  prime being processed (2*N words, off the registers) */
+                                  prime being processed (2*N words, off the registers);
+                                  3 two exchange buffers plus the first of those two
+                                  accumulator polynomials (N words; the second stays in
+                                  registers) */
     int32_t l2_persist;        /* 1: the training / inference kernels mark their per-block
                                   accumulators persisting in L2 (an access-policy window on each
                                   launch and a persisting set-aside of this process's context,

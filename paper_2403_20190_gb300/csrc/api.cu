@@ -177,7 +177,7 @@ static int resolve_geometry(const hw_params* p, const hw_geometry* g, hw_geometr
     if (G.ext_np == 0) G.ext_np = default_ext_np(log_n);
     if (G.ntt_loge == 0) G.ntt_loge = 4;
     if (G.ntt_limbs == 0) G.ntt_limbs = small_q ? 1 : 2;
-    if (G.ext_smem < 0 || G.ext_smem > 2) return fail(HW_EINVAL, "ext_smem must be 0, 1 or 2");
+    if (G.ext_smem < 0 || G.ext_smem > 3) return fail(HW_EINVAL, "ext_smem must be 0, 1, 2 or 3");
     const ExtOps* ops = hw_ext_find(log_n, G.ext_loge, G.ext_np, G.ext_smem);
     if (!ops)
         return fail(HW_EINVAL,

@@ -180,8 +180,9 @@ __global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP, SM>::T, ExtCfg<LOGN, LO
                 u64* __restrict__ model, u64* __restrict__ scratch) {
     using X = ExtCfg<LOGN, LOGE, NP, SM>;
     extern __shared__ u64 smem[];
-    Xchg xc{smem, SM ? smem : smem + NP * X::PADDED, X::PADDED, 0};
+    Xchg xc{smem, (SM == 1 || SM == 2) ? smem : smem + NP * X::PADDED, X::PADDED, 0};
     if (SM == 2) xc.accs = smem + NP * X::PADDED;
+    if (SM == 3) xc.accs = smem + 2 * NP * X::PADDED;
     const DevCtx& C = *Cp;
     const int tid = threadIdx.x, T = blockDim.x;
     const size_t rl = C.rlwe_words;
@@ -222,7 +223,7 @@ __global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP, SM>::T, ExtCfg<LOGN, LO
             int nslot = -1;  // the next encrypted control (rotation bit or first tree gate)
             for (int t2 = t + 1; t2 < kbits && nslot < 0; t2++) nslot = bit_slot(C, j, t2);
             if (nslot < 0 && C.n_gates > 0) nslot = bit_slot(C, j, C.gate_lvl[0]);
-            ext_product<LOGN, LOGE, NP, SM == 2>(
+            ext_product<LOGN, LOGE, NP, X::ACC>(
                 C, sample + (size_t)slot * C.rgsw_words, acc[cur], w, acc[cur], 0, EXT_ADD, dst, xc,
                 ExtNtt{accn, dstn, t - C.z, 0,
                        nslot >= 0 ? sample + (size_t)nslot * C.rgsw_words : nullptr, 1});
@@ -244,7 +245,7 @@ __global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP, SM>::T, ExtCfg<LOGN, LO
                 continue;
             }
             const int nslot = g + 1 < C.n_gates ? bit_slot(C, j, C.gate_lvl[g + 1]) : -1;
-            ext_product<LOGN, LOGE, NP, SM == 2>(
+            ext_product<LOGN, LOGE, NP, X::ACC>(
                 C, sample + (size_t)slot * C.rgsw_words, lo, 0, nullptr, 0, EXT_PLAIN, hi, xc,
                 ExtNtt{lon, hin, -1, 0, nslot >= 0 ? sample + (size_t)nslot * C.rgsw_words : nullptr,
                        1});
@@ -296,8 +297,9 @@ __global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP, SM>::T, ExtCfg<LOGN, LO
                u64* __restrict__ scratch) {
     using X = ExtCfg<LOGN, LOGE, NP, SM>;
     extern __shared__ u64 smem[];
-    Xchg xc{smem, SM ? smem : smem + NP * X::PADDED, X::PADDED, 0};
+    Xchg xc{smem, (SM == 1 || SM == 2) ? smem : smem + NP * X::PADDED, X::PADDED, 0};
     if (SM == 2) xc.accs = smem + NP * X::PADDED;
+    if (SM == 3) xc.accs = smem + 2 * NP * X::PADDED;
     const DevCtx& C = *Cp;
     const int tid = threadIdx.x, T = blockDim.x;
     const size_t rl = C.rlwe_words;
@@ -340,7 +342,7 @@ __global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP, SM>::T, ExtCfg<LOGN, LO
             if (slot < 0) {
                 src = lo;
             } else {
-                ext_product<LOGN, LOGE, NP, SM == 2>(C, sample + (size_t)slot * C.rgsw_words, hi, 0, lo,
+                ext_product<LOGN, LOGE, NP, X::ACC>(C, sample + (size_t)slot * C.rgsw_words, hi, 0, lo,
                                                   0, EXT_ADD, acc[0], xc,
                                                   ExtNtt{nullptr, nullptr, -1, 0, nullptr, 0});
                 src = acc[0];
@@ -390,16 +392,16 @@ __global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP, SM>::T, ExtCfg<LOGN, LO
             const ExtNtt nt{srcn, t == last ? nullptr : accn, t - C.z, 1,
                             nslot >= 0 ? sample + (size_t)nslot * C.rgsw_words : nullptr, 0};
             if (PK && t == last) {
-                ext_product<LOGN, LOGE, NP, SM == 2>(C, sample + (size_t)slot * C.rgsw_words, src, eA, src,
+                ext_product<LOGN, LOGE, NP, X::ACC>(C, sample + (size_t)slot * C.rgsw_words, src, eA, src,
                                                   e0, EXT_ADD, acc[cur ^ 1], xc, nt);
                 for (int cc = c, k = 0; cc < l; cc += 1 << C.z, k++)
                     extract_lwe_at(C, acc[cur ^ 1], k, lwe + (size_t)(cc - c) * class_stride);
                 __syncthreads();
             } else if (t == last) {
-                ext_product<LOGN, LOGE, NP, SM == 2>(C, sample + (size_t)slot * C.rgsw_words, src, eA, src,
+                ext_product<LOGN, LOGE, NP, X::ACC>(C, sample + (size_t)slot * C.rgsw_words, src, eA, src,
                                                   e0, EXT_LWE, lwe, xc, nt);
             } else {
-                ext_product<LOGN, LOGE, NP, SM == 2>(C, sample + (size_t)slot * C.rgsw_words, src, eA, src,
+                ext_product<LOGN, LOGE, NP, X::ACC>(C, sample + (size_t)slot * C.rgsw_words, src, eA, src,
                                                   e0, EXT_ADD, acc[cur ^ 1], xc, nt);
                 src = acc[cur ^ 1];
                 srcn = accn;
@@ -423,8 +425,9 @@ __global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP, SM>::T, ExtCfg<LOGN, LO
                     u64* __restrict__ out, u64* __restrict__ scratch) {
     using X = ExtCfg<LOGN, LOGE, NP, SM>;
     extern __shared__ u64 smem[];
-    Xchg xc{smem, SM ? smem : smem + NP * X::PADDED, X::PADDED, 0};
+    Xchg xc{smem, (SM == 1 || SM == 2) ? smem : smem + NP * X::PADDED, X::PADDED, 0};
     if (SM == 2) xc.accs = smem + NP * X::PADDED;
+    if (SM == 3) xc.accs = smem + 2 * NP * X::PADDED;
     const DevCtx& C = *Cp;
     const int tid = threadIdx.x, T = blockDim.x;
     const size_t rl = C.rlwe_words;
@@ -444,7 +447,7 @@ __global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP, SM>::T, ExtCfg<LOGN, LO
         int cur = 0;
         for (int t = 0; t < C.L; t++) {
             const bool last = t == C.L - 1;
-            ext_product<LOGN, LOGE, NP, SM == 2>(
+            ext_product<LOGN, LOGE, NP, X::ACC>(
                 C, sample + (size_t)t * C.rgsw_words, acc[cur], 1 << t, acc[cur], 0, EXT_ADD,
                 last ? res : acc[cur ^ 1], xc,
                 ExtNtt{accn, last ? nullptr : accn, t, 0,
@@ -504,8 +507,9 @@ __global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP, SM>::T, ExtCfg<LOGN, LO
     constexpr int N = Ring<LOGN>::N, E = 1 << LOGE, T = X::T;
     constexpr int NPI = NP < 2 ? NP : 2;
     extern __shared__ u64 smem[];
-    Xchg xc{smem, SM ? smem : smem + NP * X::PADDED, X::PADDED, 0};
+    Xchg xc{smem, (SM == 1 || SM == 2) ? smem : smem + NP * X::PADDED, X::PADDED, 0};
     if (SM == 2) xc.accs = smem + NP * X::PADDED;
+    if (SM == 3) xc.accs = smem + 2 * NP * X::PADDED;
     const DevCtx& C = *Cp;
     const int tid = threadIdx.x, r = C.r, l = C.n_classes;
     const size_t rl = C.rlwe_words;
@@ -537,7 +541,7 @@ __global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP, SM>::T, ExtCfg<LOGN, LO
             int nslot = -1;
             for (int t2 = t + 1; t2 < kbits && nslot < 0; t2++) nslot = bit_slot(C, j, t2);
             if (nslot < 0 && zt > 0) nslot = bit_slot(C, j, C.L);
-            ext_product<LOGN, LOGE, NP, SM == 2>(
+            ext_product<LOGN, LOGE, NP, X::ACC>(
                 C, sample + (size_t)slot * C.rgsw_words, acc[cur], 2 * N - (1 << k), acc[cur], 0, EXT_ADD,
                 acc[cur ^ 1], xc,
                 ExtNtt{accn, accn, k, 1, nslot >= 0 ? sample + (size_t)nslot * C.rgsw_words : nullptr, 1});
@@ -650,7 +654,7 @@ __global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP, SM>::T, ExtCfg<LOGN, LO
                     extract_lwe_at(C, acc[0], 0, lwe);
                     __syncthreads();
                 } else {
-                    ext_product<LOGN, LOGE, NP, SM == 2>(C, sample + (size_t)tslot * C.rgsw_words, acc[1], 0,
+                    ext_product<LOGN, LOGE, NP, X::ACC>(C, sample + (size_t)tslot * C.rgsw_words, acc[1], 0,
                                                       acc[0], 0, EXT_LWE, lwe, xc,
                                                       ExtNtt{nullptr, nullptr, -1, 0, nullptr, 0});
                 }

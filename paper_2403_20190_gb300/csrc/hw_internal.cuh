@@ -591,25 +591,22 @@ struct ExtNtt {
 // recovers the evaluation form of its base from the diagonal digit's
 // transform (times (Psi^(+-2^t) - 1)^-1) so that dst_ntt can still be written.
 // The external product's two accumulator polynomials at one prime: E words
-// per thread each, in registers, or (AS) in thread-private shared-memory
-// slots (oc*E + e)*T + tid, which frees 2E 64-bit registers.
-template <int E, int T, bool AS>
+// per thread each, in registers (MODE 0), in thread-private shared-memory
+// slots (oc*E + e)*T + tid (MODE 1, frees 2E 64-bit registers), or
+// component 0 in such slots and component 1 in registers (MODE 2, frees E).
+template <int E, int T, int MODE>
 struct Acc {
-    u64 r[AS ? 1 : 2][AS ? 1 : E];
+    u64 r[MODE == 1 ? 1 : (MODE == 2 ? 1 : 2)][MODE == 1 ? 1 : E];
     u64* s;
-    __device__ __forceinline__ explicit Acc(u64* base) : s(AS ? base + threadIdx.x : nullptr) {}
-    __device__ __forceinline__ u64 get(int oc, int e) const {
-        if constexpr (AS) return s[(oc * E + e) * T];
+    __device__ __forceinline__ explicit Acc(u64* base) : s(MODE ? base + threadIdx.x : nullptr) {}
+    __device__ __forceinline__ u64& at(int oc, int e) {
+        if constexpr (MODE == 1) return s[(oc * E + e) * T];
+        else if constexpr (MODE == 2) return oc == 0 ? s[e * T] : r[0][e];
         else return r[oc][e];
     }
-    __device__ __forceinline__ void set(int oc, int e, u64 v) {
-        if constexpr (AS) s[(oc * E + e) * T] = v;
-        else r[oc][e] = v;
-    }
-    __device__ __forceinline__ void add(int oc, int e, u64 v) {
-        if constexpr (AS) s[(oc * E + e) * T] += v;
-        else r[oc][e] += v;
-    }
+    __device__ __forceinline__ u64 get(int oc, int e) { return at(oc, e); }
+    __device__ __forceinline__ void set(int oc, int e, u64 v) { at(oc, e) = v; }
+    __device__ __forceinline__ void add(int oc, int e, u64 v) { at(oc, e) += v; }
 };
 
 // The external product in 32-bit words, for contexts whose primes are below
@@ -635,7 +632,7 @@ __device__ __noinline__ void ext_product32(const DevCtx& C, const u64* __restric
         const PrimeConst Pj = C.P[j];
         const u64 qj = Pj.q;
         const u32 q32 = (u32)qj, q2 = 2 * q32;
-        Acc<E, T, AS != 0> acc(xc.accs);
+        Acc<E, T, AS> acc(xc.accs);
 #pragma unroll
         for (int e = 0; e < E; e++) {
             acc.set(0, e, 0);
@@ -764,7 +761,7 @@ __device__ __noinline__ void ext_product(const DevCtx& C, const u64* __restrict_
         const ulonglong2* rtab =
             cmux_rot ? C.rot_tab + (((size_t)j * 2 + nt.rot_sign) * C.log_n + nt.rot_t) * N + tid
                      : nullptr;
-        Acc<E, T, AS != 0> acc(xc.accs);
+        Acc<E, T, AS> acc(xc.accs);
 #pragma unroll
         for (int e = 0; e < E; e++) {
             acc.set(0, e, 0);
@@ -918,8 +915,12 @@ struct ExtCfg {
     // shared-memory mode SM: 0 = two exchange sets; 1 = one set, the rest
     // holds the accumulator's evaluation form (2*r*N words, added at launch);
     // 2 = one set plus the two accumulator polynomials of one prime (2*N words)
-    static constexpr size_t XCHG_BYTES = (SM ? 1 : 2) * (size_t)NP * PADDED * sizeof(u64);
-    static constexpr size_t ACC_BYTES = SM == 2 ? 2 * (size_t)Ring<LOGN>::N * sizeof(u64) : 0;
+    // 3 = two exchange sets plus accumulator component 0 (N words; component 1
+    // stays in registers)
+    static constexpr int ACC = SM == 2 ? 1 : (SM == 3 ? 2 : 0);  // Acc mode of ext_product
+    static constexpr size_t XCHG_BYTES = (SM == 1 || SM == 2 ? 1 : 2) * (size_t)NP * PADDED * sizeof(u64);
+    static constexpr size_t ACC_BYTES =
+        (SM == 2 ? 2 : (SM == 3 ? 1 : 0)) * (size_t)Ring<LOGN>::N * sizeof(u64);
     static constexpr size_t FIXED_BYTES = XCHG_BYTES + ACC_BYTES;
     // blocks that can be resident per SM by shared memory (227 KiB, 1 KiB
     // reserved per block) and by a 512-thread target; the register cap the

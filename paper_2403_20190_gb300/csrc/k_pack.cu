@@ -117,9 +117,16 @@ __global__ void __launch_bounds__(Geo<LOGN>::T)
     const int pairs = N * C.dnum;
     const int per = (pairs + chunks - 1) / chunks;
     const int p0 = ch * per, p1 = p0 + per < pairs ? p0 + per : pairs;
+    // at N = 8192 the a component's accumulators live in the block's own
+    // shared-memory slots (registers would spill); elsewhere in registers
+    constexpr bool ACC_SMEM = LOGN >= 13;
     u64 acc[2][16];
+    u64* acc0 = smem + 2 * Ring<LOGN>::PADDED + tid;
 #pragma unroll
-    for (int e = 0; e < 16; e++) acc[0][e] = acc[1][e] = 0;
+    for (int e = 0; e < 16; e++) {
+        acc[0][e] = acc[1][e] = 0;
+        if (ACC_SMEM) acc0[e * T] = 0;
+    }
     for (int pr = p0; pr < p1; pr++) {
         const int x = pr / C.dnum, rho = pr % C.dnum;
         const int gi = rho / C.dpp, gk = rho % C.dpp;
@@ -137,7 +144,10 @@ __global__ void __launch_bounds__(Geo<LOGN>::T)
 #pragma unroll
         for (int e = 0; e < 16; e++) {
             const u64 d = v[e], wa = __ldg(ka + e * T), wb = __ldg(kb + e * T);
-            acc[0][e] = add_mod(acc[0][e], redc(__umul64hi(d, wa), d * wa, P), q);
+            if (ACC_SMEM)
+                acc0[e * T] = add_mod(acc0[e * T], redc(__umul64hi(d, wa), d * wa, P), q);
+            else
+                acc[0][e] = add_mod(acc[0][e], redc(__umul64hi(d, wa), d * wa, P), q);
             acc[1][e] = add_mod(acc[1][e], redc(__umul64hi(d, wb), d * wb, P), q);
         }
     }
@@ -145,7 +155,8 @@ __global__ void __launch_bounds__(Geo<LOGN>::T)
     for (int comp = 0; comp < 2; comp++)
 #pragma unroll
         for (int e = 0; e < 16; e++)
-            partial[(((size_t)ch * 2 + comp) * r + j) * N + e * T + tid] = acc[comp][e];
+            partial[(((size_t)ch * 2 + comp) * r + j) * N + e * T + tid] =
+                (ACC_SMEM && comp == 0) ? acc0[e * T] : acc[comp][e];
 }
 
 // Sum of the partials, inverse transform, and C = (-S_a, B - S_b).
@@ -185,6 +196,13 @@ __global__ void __launch_bounds__(Geo<LOGN>::T)
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
+// k_pack_mac's shared memory: the exchange buffers, plus one accumulator
+// component at N = 8192.
+template <int LOGN>
+constexpr size_t pack_mac_smem() {
+    return Geo<LOGN>::XCHG_BYTES + (LOGN >= 13 ? (size_t)Ring<LOGN>::N * sizeof(u64) : 0);
+}
+
 #define HW_PACK_DISPATCH(logn, BODY) \
     switch (logn) {                  \
         BODY(6) BODY(7) BODY(8) BODY(9) BODY(10) BODY(11) BODY(12) BODY(13) \
@@ -245,7 +263,7 @@ cudaError_t launch_pack(const LaunchInfo& li, const uint64_t* ksk, const uint64_
         k_pack_b<<<(unsigned)bb, 256, 0, st>>>(li.dctx, rs, k, (int)S, Bv);
 #define B(L)                                                                                            \
     case L:                                                                                             \
-        k_pack_mac<L><<<(unsigned)(S * chunks * r), Geo<L>::T, Geo<L>::XCHG_BYTES, st>>>(li.dctx, ksk, A, kp,  \
+        k_pack_mac<L><<<(unsigned)(S * chunks * r), Geo<L>::T, pack_mac_smem<L>(), st>>>(li.dctx, ksk, A, kp,  \
                                                                                        chunks, partial); \
         k_pack_finish<L><<<(unsigned)(S * 2 * r), Geo<L>::T, Geo<L>::XCHG_BYTES, st>>>(li.dctx, partial, Bv,  \
                                                                                      chunks, out);     \
@@ -266,7 +284,7 @@ cudaError_t hw_pack_kernels_init(const LaunchInfo& li) {
 #define X(L)                  \
     case L:                   \
         A(k_ksk_gen, L)       \
-        A(k_pack_mac, L)      \
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pack_mac<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pack_mac_smem<L>()); \
         A(k_pack_finish, L)   \
         break;
     switch (li.log_n) {

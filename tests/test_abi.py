@@ -80,14 +80,14 @@ def test_geometry_lists_need_no_gpu(lib):
     from paper_2403_20190_gb300 import binding
     from synthdata import get_config
     expect_default = {6: (3, 2, 0), 10: (3, 2, 0), 12: (3, 2, 0), 13: (3, 1, 0)}
-    for name, log_n, n_expect in (("cfg1", 6, 12), ("cfg1", 10, 9), ("cfg2", 12, 12), ("cfg3", 13, 4)):
+    for name, log_n, n_expect in (("cfg1", 6, 13), ("cfg1", 10, 9), ("cfg2", 12, 13), ("cfg3", 13, 6)):
         geos = binding.hw_list_geometries(get_config(name, log_n=log_n))
         assert len(geos) == n_expect
         key = [(g["ext_loge"], g["ext_np"], g["ext_smem"]) for g in geos]
         assert key[0] == expect_default[log_n]
         assert len(set(key)) == len(key)
         for loge, np_, ev in key:
-            assert loge in (2, 3, 4) and np_ in (1, 2) and ev in (0, 1, 2)
+            assert loge in (2, 3, 4) and np_ in (1, 2) and ev in (0, 1, 2, 3)
 
 
 def test_bad_geometries_rejected_before_cuda(lib):
@@ -95,7 +95,7 @@ def test_bad_geometries_rejected_before_cuda(lib):
     from synthdata import get_config
     cases = [(get_config("cfg3"), dict(ext_loge=4, ext_np=2)),   # not built at N = 8192
              (get_config("cfg3"), dict(ext_loge=3, ext_np=1, ext_smem=1)),  # not built at N = 8192
-             (get_config("cfg2"), dict(ext_smem=3)),
+             (get_config("cfg2"), dict(ext_smem=4)),
              (get_config("cfg2", n_primes=3), dict(ext_loge=3, ext_np=2, ext_smem=1)),  # 192 KiB form: no room
              (get_config("cfg2"), dict(ext_loge=5)),
              (get_config("cfg2"), dict(ntt_loge=5)),

@@ -21,10 +21,10 @@ def geometries(cfg):
 
 
 @pytest.mark.parametrize("name", list(TINY))
-@pytest.mark.parametrize("k", range(12))
+@pytest.mark.parametrize("k", range(13))
 def test_tiny_rings_every_geometry(name, k):
     geos = geometries(tiny_cfg(name))
-    assert len(geos) == 12
+    assert len(geos) == 13
     tiny_full_parity(name, geos[k])
 
 
