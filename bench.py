@@ -83,12 +83,9 @@ def parse():
 # arithmetic.  Filled per (workload, geometry) when a capture of the current
 # sources exists.
 PROFILED_VP_TRAFFIC = [
-    {"config": "cfg2", "ext_loge": 3, "ext_np": 2, "ext_smem": 1, "ext_blocks_per_sm": 1, "l2_persist": 0,
-     "bytes_per_test_sample": 2.1133e9,
-     "sha256": "1b1c5d9b6538dd97528c71efa032a025f17669d8cca0d819f28b729fc8fef19d"},
-    {"config": "cfg3", "ext_loge": 3, "ext_np": 1, "ext_smem": 0, "ext_blocks_per_sm": 1, "l2_persist": 0,
-     "bytes_per_test_sample": 1.05231e11,
-     "sha256": "1b1c5d9b6538dd97528c71efa032a025f17669d8cca0d819f28b729fc8fef19d"},
+    {"config": "cfg3", "ext_loge": 3, "ext_np": 1, "ext_smem": 3, "ext_blocks_per_sm": 1, "l2_persist": 0,
+     "bytes_per_test_sample": 8.13325e10,
+     "sha256": "fd40b0d3e4a11c82195baac36f780c73d5071a295f6e89570aed657085089c5a"},
 ]
 PROFILED_SOURCES = (("paper_2403_20190_gb300/csrc/hw_ext.cuh", "// Encrypted bit slot that drives",
                      "// EncRGSW."),
