@@ -542,6 +542,50 @@ class Workload:
                 "polys": count, "n": nn, "prime_bits": self.cfg.prime_bits, "ms_per_launch": t * 1000.0,
                 "variant": f"radix {1 << g['ntt_loge']}, {32 * g['ntt_limbs']}-bit words"}
 
+    def keyswitch(self, infer_ms, ceiling=None):
+        """PackingKeySwitching of the last test batch's responses: the key's
+        generation once, then the best of two packing passes.  Each sample
+        needs N * dnum * r forward transforms (one per key row and prime) and
+        2 r inverse ones; against the measured 64-bit butterfly rate that
+        sets a floor under the pass."""
+        import torch
+
+        from paper_2403_20190_gb300 import binding as B
+        sess, st, sz, stream, bsz = self.sess, self.st, self.sz, self.stream, self.bsz
+        resp = st.ibufs[0]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ksk = sess.ksk_gen(self.key, self.cfg.key_seed + 1, stream=stream)
+        e1.record(stream)
+        pscr = sess.words(B.hw_pack_scratch_words(sess.ctx, bsz), zero=False)
+        sess.pack_responses(ksk, resp, bsz, scratch=pscr, stream=stream)  # warm-up
+        torch.cuda.synchronize()
+        t_pack = []
+        for _ in range(2):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            sess.pack_responses(ksk, resp, bsz, scratch=pscr, stream=stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            t_pack.append(a.elapsed_time(b))
+        n, r, dnum = sz["n"], sz["r"], sz["dnum"]
+        log_n = n.bit_length() - 1
+        bfly = bsz * (n * dnum * r + 2 * r) * (n // 2) * log_n
+        best = min(t_pack)
+        out = {"workload": self.name, "batch": bsz, "pack_ms_per_step": best,
+               "ksk_gen_ms_once": e0.elapsed_time(e1),
+               "ksk_bytes": B.hw_ksk_words(sess.ctx) * 8, "pack_scratch_bytes": pscr.numel() * 8,
+               "response_bytes_per_sample": {"lwe": sz["resp_words"] * 8, "packed": sz["rlwe_words"] * 8},
+               "share_of_infer": best / infer_ms,
+               "transforms_per_sample": n * dnum * r + 2 * r,
+               "butterflies_per_s": bfly / (best * 1e-3)}
+        if ceiling:
+            floor_ms = bfly / (ceiling["ct64"] * 1e9) * 1e3
+            out["butterfly_frac"] = out["butterflies_per_s"] / (ceiling["ct64"] * 1e9)
+            out["share_of_infer_at_butterfly_ceiling"] = floor_ms / infer_ms
+        del ksk, pscr
+        return out
+
     def summary(self, elapsed_ms, steps, ws, local, with_ntt=True, ceiling=None):
         ph = self.phases(1000 + steps)
         vp, ivp, _ = self.rooflines(ph, local, ceiling)
@@ -648,29 +692,7 @@ def gpu_arm(args, ws, rank, local, pg):
 
     # PackingKeySwitching (Section 2.4): the test batch's responses packed
     # into one RLWE per sample (what Algorithm 7 returns for PD-act)
-    keyswitch = None
-    if not args.no_keyswitch:
-        resp = st.ibufs[0]
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        ksk = sess.ksk_gen(key, cfg.key_seed + 1, stream=stream)
-        e1.record(stream)
-        pscr = sess.words(B.hw_pack_scratch_words(sess.ctx, bsz), zero=False)
-        sess.pack_responses(ksk, resp, bsz, scratch=pscr, stream=stream)  # warm-up
-        torch.cuda.synchronize()
-        t_pack = []
-        for _ in range(2):
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            sess.pack_responses(ksk, resp, bsz, scratch=pscr, stream=stream)
-            b.record(stream)
-            torch.cuda.synchronize()
-            t_pack.append(a.elapsed_time(b))
-        keyswitch = {"pack_ms_per_step": min(t_pack), "ksk_gen_ms_once": e0.elapsed_time(e1),
-                     "ksk_bytes": B.hw_ksk_words(sess.ctx) * 8, "pack_scratch_bytes": pscr.numel() * 8,
-                     "response_bytes_per_sample": {"lwe": sz["resp_words"] * 8, "packed": sz["rlwe_words"] * 8},
-                     "share_of_infer": min(t_pack) / ph["infer"]}
-        del ksk, pscr
+    keyswitch = None if args.no_keyswitch else w.keyswitch(ph["infer"], ceiling)
     healthy("the key-switching leg")
 
     # inference against the model in clear (Section 3.6.2): the owner's
@@ -777,8 +799,10 @@ def gpu_arm(args, ws, rank, local, pg):
         pw = Workload(nm, local, DEFAULT_BATCH[nm], geo, rank)
         pw.warm(1)
         pms = pw.timed(1, args.per_config_steps, barrier)
-        per_config[nm], _ = pw.summary(pms, args.per_config_steps, ws, local, with_ntt=not args.no_ntt,
-                                       ceiling=ceiling)
+        per_config[nm], pph = pw.summary(pms, args.per_config_steps, ws, local, with_ntt=not args.no_ntt,
+                                         ceiling=ceiling)
+        if nm == "cfg2" and not args.no_keyswitch:
+            per_config[nm]["packing_keyswitch"] = pw.keyswitch(pph["infer"], ceiling)
         del pw
         torch.cuda.synchronize()
         torch.cuda.empty_cache()
