@@ -508,7 +508,7 @@ class Workload:
                                        "source": "hw_butterfly_rates, measured in this run"}
         train_modmul = alg["ext_train_per_sample"] * self.bsz * alg["per_ext_modmul"]
         ivp_achieved = train_modmul / (ph["train"] / 1000.0)
-        ivp = {"bound": "alu", "kernel": "k_ivp_train + k_accumulate", "achieved": ivp_achieved / 1e12,
+        ivp = {"bound": "alu", "kernel": "k_ivp_train + k_model_reduce", "achieved": ivp_achieved / 1e12,
                "peak": peak_modmul / 1e12, "unit": "T modmul/s", "frac": ivp_achieved / peak_modmul,
                "launch_ms": ph["train"],
                "work": f"{alg['ext_train_per_sample']} external products per training sample"}

@@ -343,11 +343,49 @@ long long or_gaussian(const or_ctx *c, u64 w) { return gaussian(c, w); }
 /* + k carries g = beta^k at prime i and 0 at the other primes (for     */
 /* beta = q_i this is the CRT idempotent, residue 1 at prime i).        */
 /* Rows 0..dnum-1 add m*g to b, rows dnum.. add m*g to a.               */
+/*                                                                      */
+/* The mask a ~ U(R_q) (Section 2.4 fixes no domain for it) is drawn    */
+/* by its values at the N roots of X^N + 1: the evaluation map is a     */
+/* bijection of R_q, so uniform values are a uniform a.  Sampling index */
+/* k is the value at zeta_k = psi_min^(2 brv(k) + 1), psi_min the       */
+/* smallest primitive 2N-th root of unity mod q and brv the log2(N)-bit */
+/* reversal; its word pair is that of coefficient k before.             */
 /* ------------------------------------------------------------------ */
+
+static int brv_int(int x, int log_n) {
+    int y = 0;
+    for (int b = 0; b < log_n; b++) y |= ((x >> b) & 1) << (log_n - 1 - b);
+    return y;
+}
+
+/* The odd exponent v with psi^v = psi_min: the odd powers of a primitive
+ * 2N-th root are all of them, so psi_min is the smallest of those. */
+static u64 min_root_exponent(u64 q, u64 psi, int n) {
+    u64 step = mulmod(psi, psi, q), x = psi, best = psi, v = 1;
+    for (u64 e = 1; e < 2 * (u64)n; e += 2) {
+        if (x < best) { best = x; v = e; }
+        x = mulmod(x, step, q);
+    }
+    return v;
+}
+
+/* a's coefficients from its values U[k] = a(zeta_k): zeta_k is this
+ * oracle's evaluation point psi^(2m+1) for m = (v (2 brv(k) + 1) mod 2N -
+ * 1) / 2, the slot m of its natural evaluation order; then the inverse
+ * transform. */
+static void mask_from_points(const or_ctx *c, int j, const u64 *U, u64 *a) {
+    int n = c->n, log_n = c->log_n;
+    u64 v = min_root_exponent(c->q[j], c->psi[j], n);
+    for (int k = 0; k < n; k++) {
+        u64 y = (v * (2 * (u64)brv_int(k, log_n) + 1)) % (2 * (u64)n);
+        a[(y - 1) / 2] = U[k];
+    }
+    or_ntt_inv(a, log_n, c->q[j], c->psi[j]);
+}
 void or_encrypt_rgsw(const or_ctx *c, const int8_t *s, u64 seed, u64 stream_idx, int bit,
                      int trivial, u64 *rgsw_ntt) {
     int n = c->n, r = c->r;
-    u64 *spoly = (u64 *)malloc(sizeof(u64) * n);
+    u64 *spoly = (u64 *)malloc(sizeof(u64) * n), *U = (u64 *)malloc(sizeof(u64) * n);
     u64 *a = (u64 *)malloc(sizeof(u64) * n), *b = (u64 *)malloc(sizeof(u64) * n);
     long long *e = (long long *)malloc(sizeof(long long) * n);
     size_t rlwe = or_rlwe_words(c);
@@ -365,8 +403,12 @@ void or_encrypt_rgsw(const or_ctx *c, const int8_t *s, u64 seed, u64 stream_idx,
                 u64 w[4];
                 draw(seed, TAG_RGSW_A, (u64)k >> 1, (u64)row * r + j, stream_idx, w);
                 u64 hi = w[2 * (k & 1)], lo = w[2 * (k & 1) + 1];
-                a[k] = trivial ? 0 : (u64)((((u128)hi << 64) | lo) % q);
+                U[k] = (u64)((((u128)hi << 64) | lo) % q);
             }
+            if (trivial)
+                memset(a, 0, sizeof(u64) * n);
+            else
+                mask_from_points(c, j, U, a);
             or_poly_mul(a, spoly, b, c->log_n, q, c->psi[j]);
             for (int k = 0; k < n; k++) b[k] = addmod(b[k], from_signed(e[k], q), q);
             if (bit && j == gi) {
@@ -382,7 +424,7 @@ void or_encrypt_rgsw(const or_ctx *c, const int8_t *s, u64 seed, u64 stream_idx,
             or_ntt_fwd(dst_b, c->log_n, q, c->psi[j]);
         }
     }
-    free(spoly); free(a); free(b); free(e);
+    free(spoly); free(U); free(a); free(b); free(e);
 }
 
 /* Coefficient form of an RGSW held in the oracle's evaluation order. */

@@ -381,6 +381,24 @@ extern "C" int hw_create_tuned(const hw_params* p, const hw_geometry* g, int cud
             return fail(HW_EINVAL, "no 2N-th root of unity");
         }
         u64 psi_inv = hinv(psi, q[i]);
+        // RGSW masks are drawn at the points psi_min^(2 brv(k) + 1), psi_min
+        // the smallest primitive 2N-th root: psi_min = psi^u for the odd u
+        // whose power is smallest, and position pos of this order (the point
+        // psi^(2 brv(pos) + 1)) is sampling point u^-1 (2 brv(pos) + 1) mod 2N
+        {
+            const u64 two_n = 2 * (u64)n, step = hmul(psi, psi, q[i]);
+            u64 x = psi, best = psi, u = 1;
+            for (u64 e = 1; e < two_n; e += 2) {
+                if (x < best) {
+                    best = x;
+                    u = e;
+                }
+                x = hmul(x, step, q[i]);
+            }
+            u64 uinv = 1;
+            while ((u * uinv) % two_n != 1) uinv += 2;
+            H.a_point_mul[i] = (uint32_t)uinv;
+        }
         for (int k = 0; k < n; k++) {
             int e = brv(k, log_n);
             u64 w = hpow(psi, (u64)e, q[i]), wi = hpow(psi_inv, (u64)e, q[i]);

@@ -21,9 +21,12 @@ __device__ __forceinline__ int bit_slot(const DevCtx& C, int j, int t) {
 // ---------------------------------------------------------------------------
 // EncRGSW.  One block per (sample, bit slot, row).  Row rho < dnum encrypts
 // (a, a*s + e + m*g_rho), row dnum+rho encrypts (a + m*g_rho, a*s + e); the
-// gadget value g_rho sits at prime rho/dpp only.  a is uniform per prime
-// (two 64-bit words -> 128-bit value mod q), e is one integer polynomial for
-// all primes.  Rows are stored in evaluation form, Montgomery representation.
+// gadget value g_rho sits at prime rho/dpp only.  a is uniform per prime and
+// drawn at its evaluation points (a uniform value at every root of X^N + 1
+// is a uniform a): sampling point k, the root psi_min^(2 brv(k) + 1), takes
+// two 64-bit words of block k >> 1 -> 128-bit value mod q, so a needs no
+// transform.  e is one integer polynomial for all primes, transformed per
+// prime.  Rows are stored in evaluation form, Montgomery representation.
 // ---------------------------------------------------------------------------
 template <int LOGN, int LOGE, int NP>
 __global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP>::T, ExtCfg<LOGN, LOGE, NP>::MINB)
@@ -58,105 +61,63 @@ __global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP>::T, ExtCfg<LOGN, LOGE, 
     for (int j = 0; j < r; j++) {
         const PrimeConst P = C.P[j];
         const u64 q = P.q;
-        __syncthreads();  // A is free; ebuf is complete
+        __syncthreads();  // ebuf is complete
         // the whole row is computed in Montgomery form (x R mod q, the form
         // it is stored in): a uniform draw hi*2^64 + lo gives
         // a R = hi (R^2 mod q) + lo (R mod q), two products by constants; the
         // transform is linear, so it keeps the form
         const u64 mr = C.mr[j], mr_s = C.mr_s[j], mr2_s = C.mr2_s[j];
-        for (int c0 = tid; c0 < N / 2; c0 += T) {
-            Philox4 w = hw_draw(seed, HW_TAG_RGSW_A, (u64)c0, (u64)(row * r + j), stream);
-            A[2 * c0] = add_mod(shoup_mul(w.v[0], P.r2, mr2_s, q), shoup_mul(w.v[1], mr, mr_s, q), q);
-            A[2 * c0 + 1] = add_mod(shoup_mul(w.v[2], P.r2, mr2_s, q), shoup_mul(w.v[3], mr, mr_s, q), q);
-        }
-        __syncthreads();
+        const uint32_t amul = C.a_point_mul[j];
         const u64 gM = (bit && j == gi) ? to_mont(C.gconst[rho], P) : 0;
         const u64* sM = key + (size_t)(r + j) * N;
         u64* da = dst_row + (size_t)(0 * r + j) * N;
         u64* db = dst_row + (size_t)(1 * r + j) * N;
-        bool ext64 = true;
-        if constexpr (LOGN <= 11) ext64 = !C.ext32;
-        if (NP == 1 && ext64) {
-            // one polynomial in registers at a time: a is transformed and
-            // written, a s waits in A (each thread's own slots), then e
-            u64 w[1][E];
+        // a at evaluation positions E*tid + e and E*tid + e + 1 (addresses
+        // e*T + tid, thread-major): their points differ by the factor -1, so
+        // their sampling points are k and k ^ 1, one Philox block.  a s
+        // waits in A (each thread's own addresses) while e is transformed
 #pragma unroll
-            for (int kk = 0; kk < E; kk++) w[0][kk] = A[tid + kk * T];
-            ntt_fwd<LOGN, LOGE, 1>(w, xc, C, j);
-            __syncthreads();  // every thread has read its part of A
-#pragma unroll
-            for (int e = 0; e < E; e++) {
-                const int pos = e * T + tid;  // evaluation position E*tid + e, thread-major
-                const u64 aM = reduce_full(w[0][e], P);
-                A[pos] = mont_mul(aM, sM[pos], P);  // REDC(aR * sR) = a s R
-                // the evaluation form of the constant polynomial g is g everywhere
-                da[pos] = row < C.dnum ? aM : add_mod(aM, gM, q);
-            }
-#pragma unroll
-            for (int kk = 0; kk < E; kk++) {
-                const int x = tid + kk * T;
-                w[0][kk] = shoup_mul(from_signed((int64_t)ebuf[x], q), mr, mr_s, q);  // e R
-            }
-            ntt_fwd<LOGN, LOGE, 1>(w, xc, C, j);
-#pragma unroll
-            for (int e = 0; e < E; e++) {
-                const int pos = e * T + tid;
-                const u64 bM = add_mod(A[pos], reduce_full(w[0][e], P), q);
-                db[pos] = row < C.dnum ? add_mod(bM, gM, q) : bM;
-            }
-            continue;
+        for (int e = 0; e < E; e += 2) {
+            const uint32_t pos = (uint32_t)(E * tid + e);
+            const uint32_t x = 2u * (__brev(pos) >> (32 - LOGN)) + 1u;
+            const uint32_t y = (amul * x) & (2u * N - 1u);
+            const uint32_t k = __brev(y >> 1) >> (32 - LOGN);
+            const Philox4 w = hw_draw(seed, HW_TAG_RGSW_A, (u64)(k >> 1), (u64)(row * r + j), stream);
+            const int h = 2 * (int)(k & 1u);
+            const u64 a0 = add_mod(shoup_mul(w.v[h], P.r2, mr2_s, q), shoup_mul(w.v[h + 1], mr, mr_s, q), q);
+            const u64 a1 =
+                add_mod(shoup_mul(w.v[2 - h], P.r2, mr2_s, q), shoup_mul(w.v[3 - h], mr, mr_s, q), q);
+            const int ad0 = e * T + tid, ad1 = (e + 1) * T + tid;
+            A[ad0] = mont_mul(a0, sM[ad0], P);  // REDC(aR * sR) = a s R
+            A[ad1] = mont_mul(a1, sM[ad1], P);
+            // the evaluation form of the constant polynomial g is g everywhere
+            da[ad0] = row < C.dnum ? a0 : add_mod(a0, gM, q);
+            da[ad1] = row < C.dnum ? a1 : add_mod(a1, gM, q);
         }
-        // a and e transformed together (NP == 2), or the 32-bit transform
-        u64 v[2][E];
+        u64 v[1][E];
 #pragma unroll
         for (int kk = 0; kk < E; kk++) {
             const int x = tid + kk * T;
-            v[0][kk] = A[x];
-            v[1][kk] = shoup_mul(from_signed((int64_t)ebuf[x], q), mr, mr_s, q);  // e R
+            v[0][kk] = shoup_mul(from_signed((int64_t)ebuf[x], q), mr, mr_s, q);  // e R
         }
         bool done = false;
         if constexpr (LOGN <= 11) {
             if (C.ext32) {  // primes below 2^30: the same transform in 32-bit words
-                u32 w[2][E];
+                u32 w[1][E];
 #pragma unroll
-                for (int pp = 0; pp < 2; pp++)
+                for (int kk = 0; kk < E; kk++) w[0][kk] = (u32)v[0][kk];
+                fwd_from32<LOGN, LOGE, 1, 0>(w, xc, C.tw32_fwd + (size_t)j * N, (u32)q, 2 * (u32)q);
 #pragma unroll
-                    for (int kk = 0; kk < E; kk++) w[pp][kk] = (u32)v[pp][kk];
-                const uint2* tw = C.tw32_fwd + (size_t)j * N;
-                if constexpr (NP == 2) {
-                    fwd_from32<LOGN, LOGE, 2, 0>(w, xc, tw, (u32)q, 2 * (u32)q);
-                } else {
-                    fwd_from32<LOGN, LOGE, 1, 0>(reinterpret_cast<u32(&)[1][E]>(w[0]), xc, tw, (u32)q, 2 * (u32)q);
-                    fwd_from32<LOGN, LOGE, 1, 0>(reinterpret_cast<u32(&)[1][E]>(w[1]), xc, tw, (u32)q, 2 * (u32)q);
-                }
-#pragma unroll
-                for (int pp = 0; pp < 2; pp++)
-#pragma unroll
-                    for (int e = 0; e < E; e++) v[pp][e] = w[pp][e];  // < 4q, reduced below
+                for (int e = 0; e < E; e++) v[0][e] = w[0][e];  // < 4q, reduced below
                 done = true;
             }
         }
-        if (!done) {
-            if constexpr (NP == 2) {
-                ntt_fwd<LOGN, LOGE, 2>(v, xc, C, j);
-            } else {
-                ntt_fwd<LOGN, LOGE, 1>(reinterpret_cast<u64(&)[1][E]>(v[0]), xc, C, j);
-                ntt_fwd<LOGN, LOGE, 1>(reinterpret_cast<u64(&)[1][E]>(v[1]), xc, C, j);
-            }
-        }
+        if (!done) ntt_fwd<LOGN, LOGE, 1>(v, xc, C, j);
 #pragma unroll
         for (int e = 0; e < E; e++) {
-            const int pos = e * T + tid;  // evaluation position E*tid + e, thread-major
-            u64 aM = reduce_full(v[0][e], P);
-            // REDC(aR * sR) = a s R
-            u64 bM = add_mod(mont_mul(aM, sM[pos], P), reduce_full(v[1][e], P), q);
-            // the evaluation form of the constant polynomial g is g everywhere
-            if (row < C.dnum)
-                bM = add_mod(bM, gM, q);
-            else
-                aM = add_mod(aM, gM, q);
-            da[pos] = aM;
-            db[pos] = bM;
+            const int ad = e * T + tid;
+            const u64 bM = add_mod(A[ad], reduce_full(v[0][e], P), q);
+            db[ad] = row < C.dnum ? add_mod(bM, gM, q) : bM;
         }
     }
 }

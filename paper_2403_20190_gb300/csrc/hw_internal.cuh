@@ -27,6 +27,9 @@ struct DevCtx {
     u64 n_inv[HW_MAXP], n_inv_s[HW_MAXP];  // N^-1 and its Shoup companion
     u64 mr[HW_MAXP], mr_s[HW_MAXP];        // R = 2^64 mod q_i and its Shoup companion
     u64 mr2_s[HW_MAXP];                    // Shoup companion of R^2 mod q_i (P[i].r2)
+    // u^-1 mod 2N for psi_min = psi^u: evaluation position pos holds RGSW
+    // mask sampling point brv((a_point_mul (2 brv(pos) + 1) mod 2N) >> 1)
+    uint32_t a_point_mul[HW_MAXP];
     u64 delta[HW_MAXP];                    // floor(Q/p) mod q_i
     u64 gconst[HW_MAX_DNUM];               // gadget value of row rho at its prime
     // decryption constants (Q < 2^(64*HW_LIMBS))

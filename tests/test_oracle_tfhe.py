@@ -111,6 +111,64 @@ def test_gadget_recomposition(case):
         assert total[k] % P.Q == X[k]
 
 
+def _philox_words(seed, tag, c0, c1, c2):
+    """Block (c0, c1, c2, 0) of Philox4x64-10 keyed (seed, tag), from numpy's
+    implementation (it increments its 256-bit counter before each block)."""
+    v = (c0 + (c1 << 64) + (c2 << 128) - 1) % (1 << 256)
+    ctr = [(v >> (64 * i)) & ((1 << 64) - 1) for i in range(4)]
+    return [int(w) for w in np.random.Philox(counter=np.array(ctr, dtype=np.uint64),
+                                              key=np.array([seed, tag], dtype=np.uint64)).random_raw(4)]
+
+
+def _smallest_primitive_root(q, n):
+    """min over the primitive 2N-th roots of unity mod q: the odd powers of
+    any one of them."""
+    x = 2
+    while True:
+        c = pow(x, (q - 1) // (2 * n), q)
+        if pow(c, n, q) == q - 1:
+            return min(pow(c, 2 * i + 1, q) for i in range(n))
+        x += 1
+
+
+def _brv(k, bits):
+    return int(format(k, f"0{bits}b")[::-1], 2) if bits else 0
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("bit", [0, 1])
+def test_rgsw_mask_values_at_the_roots(case, bit):
+    """Each row's mask a takes the uniform draw of sampling index k at
+    zeta_k = psi_min^(2 brv(k) + 1) (psi_min the smallest primitive 2N-th root
+    of unity): a evaluated there by Horner's rule (not a transform) equals
+    (hi 2^64 + lo) mod q of words 2(k&1), 2(k&1)+1 of the RGSW_A block
+    (k >> 1, row r + j, stream).  Rows dnum.. carry m g on a's constant
+    term, which adds m g at every point."""
+    o = make(case)
+    P = o.P
+    beta = 1 << o.cfg.log_beta if o.cfg.log_beta else None
+    s = o.keygen(5)
+    seed, stream = 9, 3
+    rows = o.export_rgsw(o.encrypt_bit(s, seed, stream, bit)).reshape(2 * P.dnum, 2, P.r, P.n)
+    for j in range(P.r):
+        q = P.q[j]
+        pmin = _smallest_primitive_root(q, P.n)
+        zeta = [pow(pmin, 2 * _brv(k, P.log_n) + 1, q) for k in range(P.n)]
+        for row in range(2 * P.dnum):
+            rho = row % P.dnum
+            i, kk = divmod(rho, P.dpp)
+            g = (beta ** kk if beta else 1) % q if j == i else 0
+            shift = bit * g if row >= P.dnum else 0
+            a = [int(v) for v in rows[row, 0, j]]
+            for k in range(P.n):
+                val = 0
+                for coef in reversed(a):
+                    val = (val * zeta[k] + coef) % q
+                w = _philox_words(seed, 2, k >> 1, row * P.r + j, stream)
+                u = ((w[2 * (k & 1)] << 64) | w[2 * (k & 1) + 1]) % q
+                assert val == (u + shift) % q, (row, j, k)
+
+
 @pytest.mark.parametrize("case", list(CASES))
 @pytest.mark.parametrize("bit", [0, 1])
 def test_rgsw_rows(case, bit):
