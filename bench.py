@@ -586,6 +586,32 @@ class Workload:
         del ksk, pscr
         return out
 
+    def packed_inference(self, infer_ms):
+        """Horizontal packing (Section 6) on the last test batch: the packed
+        VP against the plain one's phase time, and whether every packed
+        response decrypts to the plain path's counter."""
+        import torch
+        sess, st, sz, stream, bsz = self.sess, self.st, self.sz, self.stream, self.bsz
+        groups = min(self.cfg.n_classes, 1 << sz["z"]) if sz["z"] <= sz["L"] else self.cfg.n_classes
+        bufs = sess.infer_buffers(bsz)
+        sess.infer(self.model, st.rgsw_test, bsz, bufs=bufs, stream=stream, packed=True)  # warm-up
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(2):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            sess.infer(self.model, st.rgsw_test, bsz, bufs=bufs, stream=stream, packed=True)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        pc = sess.responses_counts(self.key, bufs[0], bsz, stream=stream)
+        same = (pc.reshape(-1) == st.counts[: pc.numel()]).float().mean().item()
+        del bufs
+        return {"workload": self.name, "batch": bsz, "inferences_per_s_plain": bsz / (infer_ms / 1000.0),
+                "inferences_per_s_packed": bsz / (min(ts) / 1000.0),
+                "vp_per_sample": {"plain": self.cfg.n_classes * sz["k0"], "packed": groups * sz["k0"]},
+                "responses_equal_to_plain_path": same}
+
     def summary(self, elapsed_ms, steps, ws, local, with_ntt=True, ceiling=None):
         ph = self.phases(1000 + steps)
         vp, ivp, _ = self.rooflines(ph, local, ceiling)
@@ -694,6 +720,10 @@ def gpu_arm(args, ws, rank, local, pg):
     # into one RLWE per sample (what Algorithm 7 returns for PD-act)
     keyswitch = None if args.no_keyswitch else w.keyswitch(ph["infer"], ceiling)
     healthy("the key-switching leg")
+    packed_main = None
+    if not args.no_packing and args.config != "cfg1":
+        packed_main = w.packed_inference(ph["infer"])
+    healthy("the packed-inference leg")
 
     # inference against the model in clear (Section 3.6.2): the owner's
     # decrypted counters as plaintext tables, one blind rotation per (sample,
@@ -791,6 +821,8 @@ def gpu_arm(args, ws, rank, local, pg):
     packing = None
     if not args.no_packing:
         packing = packing_leg(local, geo)
+        if packed_main is not None:
+            packing = {"cfg1": packing, args.config: packed_main}
 
     # the other workloads, shorter: the same step, its rooflines and the
     # batched NTT at its primes
