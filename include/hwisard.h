@@ -183,8 +183,13 @@ int hw_get_sizes(const hw_ctx* ctx, hw_sizes* out);
  * address bit i, the encrypted bit slot it reads (-1: constant 0). */
 int hw_get_ram_slots(const hw_ctx* ctx, int32_t* ram_slot_host, size_t n);
 
-/* Scratch words hw_train_accumulate / hw_infer need for a batch of n samples
- * (per resident block of the persistent kernels; neither grows with n). */
+/* Scratch words hw_train_accumulate / hw_infer need for a batch of n samples:
+ * buffers per resident block of the persistent kernels, and for hw_infer at
+ * n >= 2 one set of the first blind-rotation CMUX's digit transforms per
+ * (RAM, class) (2 dnum r N words each; its source is the stored ciphertext,
+ * shared by the batch; none when a CMUX-tree level is an encrypted bit or
+ * the external product runs in 32-bit words).  Neither grows further with n;
+ * hw_infer_packed and hw_infer_plain need no more than hw_infer. */
 size_t hw_train_scratch_words(const hw_ctx* ctx, size_t n);
 size_t hw_infer_scratch_words(const hw_ctx* ctx, size_t n);
 

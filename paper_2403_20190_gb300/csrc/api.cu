@@ -623,6 +623,7 @@ extern "C" int hw_create_tuned(const hw_params* p, const hw_geometry* g, int cud
     li.model_words = H.model_words;
     li.sm_count = sms;
     li.small_q = p->prime_bits <= 30 ? 1 : 0;
+    li.ext32 = H.ext32;
     li.launches = &c->launches;
     {
         int occ = li.ext->occupancy(li.ext_smem);
@@ -751,10 +752,17 @@ static size_t train_chunk(const hw_ctx* c) {
     return lim < per_launch ? (size_t)lim : per_launch;
 }
 
+// Inference scratch: the persistent blocks' accumulators, then (batches of
+// two or more samples) the first CMUX's digit transforms shared by the batch.
+static size_t infer_block_words(const hw_ctx* c) {
+    return (size_t)c->li.ext_grid * c->li.ext->scratch_rlwe * c->sz.rlwe_words;
+}
+
+static size_t infer_digit_words(const hw_ctx* c, size_t n) { return n >= 2 ? vp_digits_words(c->li) : 0; }
+
 extern "C" size_t hw_infer_scratch_words(const hw_ctx* c, size_t n) {
     if (!c) return 0;
-    (void)n;
-    return (size_t)c->li.ext_grid * c->li.ext->scratch_rlwe * c->sz.rlwe_words;
+    return infer_block_words(c) + infer_digit_words(c, n);
 }
 
 #define CHECK_CTX(c)                                                   \
@@ -816,7 +824,8 @@ extern "C" int hw_infer(hw_ctx* c, const uint64_t* model, const uint64_t* rgsw, 
         return fail(HW_ENOMEM, "hw_infer: scratch has %zu words, needs %zu", scratch_words, need);
     int grid = c->li.ext_grid;
     cudaStream_t st = (cudaStream_t)stream;
-    CUDA_TRY(launch_vp_infer(c->li, model, rgsw, n, resp, scratch, grid, st));
+    uint64_t* digits = infer_digit_words(c, n) ? scratch + infer_block_words(c) : nullptr;
+    CUDA_TRY(launch_vp_infer(c->li, model, rgsw, n, resp, scratch, grid, st, 0, digits));
     CUDA_TRY(launch_class_sums(c->li, resp, n, sums, st));
     return HW_OK;
 }
@@ -832,7 +841,8 @@ extern "C" int hw_infer_packed(hw_ctx* c, const uint64_t* model, const uint64_t*
     if (scratch_words < need)
         return fail(HW_ENOMEM, "hw_infer_packed: scratch has %zu words, needs %zu", scratch_words, need);
     cudaStream_t st = (cudaStream_t)stream;
-    CUDA_TRY(launch_vp_infer(c->li, model, rgsw, n, resp, scratch, c->li.ext_grid, st, 1));
+    uint64_t* digits = infer_digit_words(c, n) ? scratch + infer_block_words(c) : nullptr;
+    CUDA_TRY(launch_vp_infer(c->li, model, rgsw, n, resp, scratch, c->li.ext_grid, st, 1, digits));
     CUDA_TRY(launch_class_sums(c->li, resp, n, sums, st));
     return HW_OK;
 }
@@ -851,7 +861,7 @@ extern "C" int hw_infer_plain(hw_ctx* c, const uint64_t* plain, const uint64_t* 
     CHECK_CTX(c);
     if (n == 0) return HW_OK;
     if (!plain || !rgsw || !resp || !sums || !scratch) return fail(HW_EINVAL, "hw_infer_plain: null buffer");
-    size_t need = hw_infer_scratch_words(c, n);
+    size_t need = infer_block_words(c);
     if (scratch_words < need)
         return fail(HW_ENOMEM, "hw_infer_plain: scratch has %zu words, needs %zu", scratch_words, need);
     if (n * (size_t)c->sz.k0 > 0x7fffffff) return fail(HW_EINVAL, "hw_infer_plain: batch too large");

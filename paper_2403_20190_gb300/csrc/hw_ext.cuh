@@ -249,13 +249,16 @@ __device__ __forceinline__ void extract_lwe_at(const DevCtx& C, const u64* ct, i
 // is a CMUX(C, L_{v+n}, L_v); label bits among the rotation bits are a plain
 // rotation X^-(c >> z).  The encrypted address bits then blind-rotate with
 // weights +2^k (X^-2^k) and the last CMUX writes ExtractLWE(., 0) directly.
-// Per-block scratch: two accumulators and their evaluation forms.
+// Per-block scratch: two accumulators and their evaluation forms.  With
+// `digits` (from k_vp_digits, z <= L) the first CMUX of item (RAM j, class c)
+// takes its digits' transforms from digits + (j G + c) 2 dnum r N: its source
+// is the stored ciphertext, the same for every sample of the batch.
 // ---------------------------------------------------------------------------
 template <int LOGN, int LOGE, int NP, int SM, int PK>
 __global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP, SM>::T, ExtCfg<LOGN, LOGE, NP, SM>::MINB)
     k_vp_infer(const DevCtx* __restrict__ Cp, const u64* __restrict__ model,
                const u64* __restrict__ rgsw, int n_items, u64* __restrict__ resp,
-               u64* __restrict__ scratch) {
+               u64* __restrict__ scratch, const u64* __restrict__ digits) {
     using X = ExtCfg<LOGN, LOGE, NP, SM>;
     extern __shared__ u64 smem[];
     Xchg xc{smem, (SM == 1 || SM == 2) ? smem : smem + NP * X::PADDED, X::PADDED, 0};
@@ -340,6 +343,9 @@ __global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP, SM>::T, ExtCfg<LOGN, LO
             continue;
         }
         int cur = (src == acc[0]) ? 0 : 1;  // acc[cur ^ 1] is free
+        const u64* dg = (digits && C.z <= C.L)
+                            ? digits + ((size_t)j * G + c) * (size_t)(2 * C.dnum * C.r) * C.n
+                            : nullptr;
         for (int t = (C.z > C.L ? C.z : C.L); t < kbits; t++) {
             int slot = bit_slot(C, j, t);
             if (slot < 0) continue;
@@ -351,25 +357,60 @@ __global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP, SM>::T, ExtCfg<LOGN, LO
             if (c == 0)
                 for (int t2 = t + 1; t2 < kbits && nslot < 0; t2++) nslot = bit_slot(C, j, t2);
             const ExtNtt nt{srcn, t == last ? nullptr : accn, t - C.z, 1,
-                            nslot >= 0 ? sample + (size_t)nslot * C.rgsw_words : nullptr, 0};
+                            nslot >= 0 ? sample + (size_t)nslot * C.rgsw_words : nullptr, 0, dg};
+            const u64* ct = sample + (size_t)slot * C.rgsw_words;
+            const bool to_lwe = !PK && t == last;
+            u64* dst = to_lwe ? lwe : acc[cur ^ 1];
+            const int mode = to_lwe ? EXT_LWE : EXT_ADD;
+            if (dg)  // the first CMUX, its digit transforms given
+                ext_product<LOGN, LOGE, NP, X::ACC, true>(C, ct, src, eA, src, e0, mode, dst, xc, nt);
+            else
+                ext_product<LOGN, LOGE, NP, X::ACC>(C, ct, src, eA, src, e0, mode, dst, xc, nt);
+            dg = nullptr;
             if (PK && t == last) {
-                ext_product<LOGN, LOGE, NP, X::ACC>(C, sample + (size_t)slot * C.rgsw_words, src, eA, src,
-                                                  e0, EXT_ADD, acc[cur ^ 1], xc, nt);
                 for (int cc = c, k = 0; cc < l; cc += 1 << C.z, k++)
                     extract_lwe_at(C, acc[cur ^ 1], k, lwe + (size_t)(cc - c) * class_stride);
                 __syncthreads();
-            } else if (t == last) {
-                ext_product<LOGN, LOGE, NP, X::ACC>(C, sample + (size_t)slot * C.rgsw_words, src, eA, src,
-                                                  e0, EXT_LWE, lwe, xc, nt);
-            } else {
-                ext_product<LOGN, LOGE, NP, X::ACC>(C, sample + (size_t)slot * C.rgsw_words, src, eA, src,
-                                                  e0, EXT_ADD, acc[cur ^ 1], xc, nt);
+            } else if (t != last) {
                 src = acc[cur ^ 1];
                 srcn = accn;
                 cur ^= 1;
             }
             e0 = 0;
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The first CMUX's digit transforms of every (RAM j, class c) item of VP
+// (z <= L): its source is the stored ciphertext H[j][c mod 2^z] rotated by
+// the clear label bits, the same for every sample, so the 2 dnum r forward
+// transforms are computed once per batch; k_vp_infer reads them.  Item
+// j G + c (G classes, or groups with PK) writes digits + item 2 dnum r N.
+// ---------------------------------------------------------------------------
+template <int LOGN, int LOGE, int NP, int SM, int PK>
+__global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP, SM>::T, ExtCfg<LOGN, LOGE, NP, SM>::MINB)
+    k_vp_digits(const DevCtx* __restrict__ Cp, const u64* __restrict__ model, int n_items,
+                u64* __restrict__ digits) {
+    using X = ExtCfg<LOGN, LOGE, NP, SM>;
+    extern __shared__ u64 smem[];
+    Xchg xc{smem, (SM == 1 || SM == 2) ? smem : smem + NP * X::PADDED, X::PADDED, 0};
+    const DevCtx& C = *Cp;
+    const int two_n = 2 * C.n, l = C.n_classes, kbits = C.L + C.a;
+    const size_t rl = C.rlwe_words;
+    const int G = PK ? (l < (1 << C.z) ? l : (1 << C.z)) : l;
+    const size_t per = (size_t)2 * C.dnum * C.r * C.n;
+    for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+        const int c = item % G, j = item / G;
+        const u64* src = model + (size_t)j * C.k1 * rl + (size_t)C.slot_of[c & ((1 << C.z) - 1)] * rl;
+        const int R = PK ? 0 : c >> C.z;
+        const int e0 = (two_n - R) % two_n;
+        int t0 = -1;
+        for (int t = C.L; t < kbits && t0 < 0; t++)
+            if (bit_slot(C, j, t) >= 0) t0 = t;
+        if (t0 < 0) continue;  // nothing encrypted: VP extracts directly
+        const int eA = (e0 + two_n - (1 << (t0 - C.z))) % two_n;
+        ext_digits<LOGN, LOGE, NP>(C, src, eA, src, e0, xc, digits + (size_t)item * per);
     }
 }
 
@@ -648,6 +689,12 @@ struct ExtVariant {
             e = cudaFuncSetAttribute(k_vp_infer<LOGN, LOGE, NP, SM, 1>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_vp_digits<LOGN, LOGE, NP, SM, 0>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_vp_digits<LOGN, LOGE, NP, SM, 1>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k_count_classes<LOGN, LOGE, NP, SM>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e == cudaSuccess)
@@ -707,13 +754,23 @@ struct ExtVariant {
                                   (u64*)out, (u64*)acc);
     }
     static cudaError_t vp(const LaunchInfo& li, const uint64_t* model, const uint64_t* rgsw, int items,
-                          uint64_t* resp, uint64_t* acc, int grid, int packed, cudaStream_t st) {
+                          uint64_t* resp, uint64_t* acc, int grid, int packed, const uint64_t* digits,
+                          cudaStream_t st) {
         Launch L(li, grid, st, acc, (size_t)grid * SCRATCH_RLWE * li.rlwe_words * sizeof(u64));
         if (packed)
             return cudaLaunchKernelEx(&L.cfg, k_vp_infer<LOGN, LOGE, NP, SM, 1>, li.dctx, (const u64*)model,
-                                      (const u64*)rgsw, items, (u64*)resp, (u64*)acc);
+                                      (const u64*)rgsw, items, (u64*)resp, (u64*)acc, (const u64*)digits);
         return cudaLaunchKernelEx(&L.cfg, k_vp_infer<LOGN, LOGE, NP, SM, 0>, li.dctx, (const u64*)model,
-                                  (const u64*)rgsw, items, (u64*)resp, (u64*)acc);
+                                  (const u64*)rgsw, items, (u64*)resp, (u64*)acc, (const u64*)digits);
+    }
+    static cudaError_t vp_digits(const LaunchInfo& li, const uint64_t* model, int items, uint64_t* digits,
+                                 int grid, int packed, cudaStream_t st) {
+        Launch L(li, grid, st, nullptr, 0);
+        if (packed)
+            return cudaLaunchKernelEx(&L.cfg, k_vp_digits<LOGN, LOGE, NP, SM, 1>, li.dctx, (const u64*)model,
+                                      items, (u64*)digits);
+        return cudaLaunchKernelEx(&L.cfg, k_vp_digits<LOGN, LOGE, NP, SM, 0>, li.dctx, (const u64*)model,
+                                  items, (u64*)digits);
     }
     static cudaError_t vp_plain(const LaunchInfo& li, const uint64_t* plain, const uint64_t* rgsw, int items,
                                 uint64_t* resp, uint64_t* acc, int grid, cudaStream_t st) {
@@ -729,7 +786,7 @@ struct ExtVariant {
     }
     static ExtOps ops() {
         return ExtOps{LOGE, NP, SM, SCRATCH_RLWE, X::T, X::FIXED_BYTES, ENC_SMEM, &init, &occupancy,
-                      &encrypt, &ivp, &vp, &count, &vp_plain};
+                      &encrypt, &ivp, &vp, &count, &vp_plain, &vp_digits};
     }
 };
 

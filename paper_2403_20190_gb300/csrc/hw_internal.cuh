@@ -569,6 +569,10 @@ struct ExtNtt {
     int rot_sign;
     const u64* next_rgsw;  // RGSW of the next external product (L2 prefetch), or null
     int prefetch_cur;      // also prefetch this product's RGSW
+    // the forward transforms of all 2 dnum digits of D at every prime, as
+    // ext_digits writes them ([prime][digit][address]); read by the
+    // ext_product<..., DG = true> instances only
+    const u64* digits = nullptr;
 };
 
 // The external product C [x] D for one RLWE, computed by one thread block.
@@ -730,7 +734,7 @@ __device__ __noinline__ void ext_product32(const DevCtx& C, const u64* __restric
     __syncthreads();  // dst complete for the whole block
 }
 
-template <int LOGN, int LOGE, int NP, int AS = 0>
+template <int LOGN, int LOGE, int NP, int AS = 0, bool DG = false>
 __device__ __noinline__ void ext_product(const DevCtx& C, const u64* __restrict__ rgsw,
                                          const u64* srcA, int eA, const u64* srcB, int eB, int mode,
                                          u64* dst, Xchg& xc, ExtNtt nt) {
@@ -743,7 +747,7 @@ __device__ __noinline__ void ext_product(const DevCtx& C, const u64* __restrict_
     constexpr int N = Ring<LOGN, LOGE>::N, T = Ring<LOGN, LOGE>::T, E = 1 << LOGE;
     const int tid = threadIdx.x, r = C.r;
     const bool cmux_rot = nt.rot_t >= 0;
-    const bool diag_in = C.diag && nt.src_ntt &&
+    const bool diag_in = C.diag && nt.src_ntt && !DG &&
                          ((cmux_rot && eB == 0) || (!cmux_rot && srcB == nullptr && eA == 0));
     const bool derive_base = C.diag && !diag_in && cmux_rot && nt.dst_ntt && mode == EXT_ADD;
     // the output's evaluation form is written only when its base's is known:
@@ -791,7 +795,36 @@ __device__ __noinline__ void ext_product(const DevCtx& C, const u64* __restrict_
                 }
             }
         }
-        for (int u0 = 0; u0 < ndig; u0 += NP) {
+        if constexpr (DG) {
+            // the digits' transforms were computed beforehand (the source is
+            // shared by other items, DG instances only): only the MACs
+            const u64* dg = nt.digits + (size_t)j * ndig * N + tid;
+            for (int u = 0; u < ndig; u++) {
+                const int comp = u / C.dnum, rho = u % C.dnum;
+                const int row = comp == 1 ? rho : C.dnum + rho;
+                const u64* Ra = rgsw + ((size_t)(row * 2 + 0) * r + j) * N + tid;
+                const u64* Rb = rgsw + ((size_t)(row * 2 + 1) * r + j) * N + tid;
+                const u64* du = dg + (size_t)u * N;
+#pragma unroll
+                for (int e = 0; e < E; e++) {
+                    const u64 ra = ld_rgsw(Ra + e * T, rpol), rb = ld_rgsw(Rb + e * T, rpol);
+                    const u64 x = du[e * T];
+                    acc.add(0, e, redc_lazy(__umul64hi(x, ra), x * ra, qj, Pj.qneg));
+                    acc.add(1, e, redc_lazy(__umul64hi(x, rb), x * rb, qj, Pj.qneg));
+                }
+                if (derive_base && rho == j) {
+                    const ulonglong2* ri =
+                        C.rot_inv + (((size_t)j * 2 + nt.rot_sign) * C.log_n + nt.rot_t) * N + tid;
+                    u64* bn = nt.dst_ntt + ((size_t)comp * r + j) * N + tid;
+#pragma unroll
+                    for (int e = 0; e < E; e++) {
+                        const ulonglong2 w = __ldg(ri + e * T);
+                        bn[e * T] = shoup_mul_lazy(du[e * T], w.x, w.y, qj);
+                    }
+                }
+            }
+        }
+        for (int u0 = 0; u0 < (DG ? 0 : ndig); u0 += NP) {
             u64 v[NP][E];
             int comps[NP], rhos[NP];
 #pragma unroll
@@ -905,6 +938,50 @@ __device__ __noinline__ void ext_product(const DevCtx& C, const u64* __restrict_
         }
     }
     __syncthreads();  // dst complete for the whole block
+}
+
+// The forward transforms ext_product computes for D = srcA X^eA - srcB X^eB
+// before its MACs (no evaluation form of the source given): the 2 dnum
+// gadget digits lifted to every prime j, written to
+// out[(j * 2 dnum + u) * N + address], u = comp * dnum + rho, the lazy values
+// of the transform as they are.  ext_product with ExtNtt::digits = out then
+// gives the same result as with the source.
+template <int LOGN, int LOGE, int NP>
+__device__ __noinline__ void ext_digits(const DevCtx& C, const u64* srcA, int eA, const u64* srcB, int eB,
+                                        Xchg& xc, u64* out) {
+    constexpr int N = Ring<LOGN, LOGE>::N, T = Ring<LOGN, LOGE>::T, E = 1 << LOGE;
+    const int tid = threadIdx.x, r = C.r;
+    const int ndig = 2 * C.dnum;
+    __syncthreads();  // exchange buffers are free
+    for (int j = 0; j < r; j++) {
+        const u64 qj = C.P[j].q;
+        for (int u0 = 0; u0 < ndig; u0 += NP) {
+            u64 v[NP][E];
+#pragma unroll
+            for (int pp = 0; pp < NP; pp++) {
+                const int u = u0 + pp;
+                const int comp = u / C.dnum, rho = u % C.dnum;
+                const int i = rho / C.dpp, k = rho % C.dpp;
+                const u64 qi = C.P[i].q;
+                const u64* pa = srcA + ((size_t)comp * r + i) * N;
+                const u64* pb = srcB ? srcB + ((size_t)comp * r + i) * N : nullptr;
+#pragma unroll
+                for (int kk = 0; kk < E; kk++) {
+                    const int x = tid + kk * T;
+                    u64 val = rot_read(pa, x, eA, N, qi);
+                    if (pb) val = sub_mod(val, rot_read(pb, x, eB, N, qi), qi);
+                    v[pp][kk] = lift_small(gadget_digit(centre(val, qi), k, C.dpp, C.log_beta), qj);
+                }
+            }
+            ntt_fwd<LOGN, LOGE, NP>(v, xc, C, j);
+#pragma unroll
+            for (int pp = 0; pp < NP; pp++) {
+                u64* o = out + ((size_t)j * ndig + u0 + pp) * N + tid;
+#pragma unroll
+                for (int e = 0; e < E; e++) o[e * T] = v[pp][e];
+            }
+        }
+    }
 }
 
 // Launch geometry of the external-product kernels: 2^LOGE residues per

@@ -25,11 +25,15 @@ struct ExtOps {
     cudaError_t (*ivp)(const LaunchInfo&, const uint64_t* rgsw, int items, uint64_t* model,
                        uint64_t* acc, int grid, cudaStream_t);
     cudaError_t (*vp)(const LaunchInfo&, const uint64_t* model, const uint64_t* rgsw, int items,
-                      uint64_t* resp, uint64_t* acc, int grid, int packed, cudaStream_t);
+                      uint64_t* resp, uint64_t* acc, int grid, int packed, const uint64_t* digits,
+                      cudaStream_t);
     cudaError_t (*count)(const LaunchInfo&, const uint64_t* rgsw, int items, uint64_t* out,
                          uint64_t* acc, int grid, cudaStream_t);
     cudaError_t (*vp_plain)(const LaunchInfo&, const uint64_t* plain, const uint64_t* rgsw, int items,
                             uint64_t* resp, uint64_t* acc, int grid, cudaStream_t);
+    // the first CMUX's digit transforms of every (RAM, class) item of VP
+    cudaError_t (*vp_digits)(const LaunchInfo&, const uint64_t* model, int items, uint64_t* digits, int grid,
+                             int packed, cudaStream_t);
 };
 
 struct LaunchInfo {
@@ -38,6 +42,7 @@ struct LaunchInfo {
     size_t rlwe_words, lwe_words, rgsw_words, sample_words, model_words;
     int sm_count;
     int small_q;  // every q_i < 2^30: the 32-bit transform tables exist
+    int ext32;    // the external product runs in 32-bit words
     const ExtOps* ext;  // the context's external-product geometry
     int ext_grid;       // persistent grid of the IVP / VP kernels
     size_t ext_smem;    // their dynamic shared memory per block
@@ -75,9 +80,12 @@ cudaError_t launch_encrypt(const LaunchInfo& li, const uint64_t* key, const uint
 cudaError_t launch_ivp_train(const LaunchInfo& li, const uint64_t* rgsw, size_t n, uint64_t* model,
                              uint64_t* acc, int grid, cudaStream_t st);
 cudaError_t launch_model_reduce(const LaunchInfo& li, uint64_t* model, cudaStream_t st);
+// With `digits` (vp_digits_words of them, z <= L) the first CMUX of every
+// item takes its digit transforms from there, computed once for the batch.
 cudaError_t launch_vp_infer(const LaunchInfo& li, const uint64_t* model, const uint64_t* rgsw,
                             size_t n, uint64_t* resp, uint64_t* acc, int grid, cudaStream_t st,
-                            int packed = 0);
+                            int packed = 0, uint64_t* digits = nullptr);
+size_t vp_digits_words(const LaunchInfo& li);
 // Unencrypted-model inference: the clear counters into plaintext tables, and
 // the responses against them.
 size_t hw_plain_words_li(const LaunchInfo& li);

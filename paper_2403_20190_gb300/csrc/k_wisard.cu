@@ -122,15 +122,32 @@ cudaError_t launch_model_reduce(const LaunchInfo& li, uint64_t* model, cudaStrea
     return cudaGetLastError();
 }
 
+// Words of the first CMUX's digit transforms: one set of 2 dnum r
+// polynomials per (RAM, class); none when a tree level is encrypted (the
+// first CMUX's source then depends on the sample) or for the 32-bit
+// external product.
+size_t vp_digits_words(const LaunchInfo& li) {
+    if (li.z > li.L || li.ext32) return 0;
+    return (size_t)li.k0 * li.n_classes * 2 * li.dnum * li.r * li.n;
+}
+
 cudaError_t launch_vp_infer(const LaunchInfo& li, const uint64_t* model, const uint64_t* rgsw,
                             size_t n, uint64_t* resp, uint64_t* acc, int grid, cudaStream_t st,
-                            int packed) {
+                            int packed, uint64_t* digits) {
     if (li.z > li.L) packed = 0;  // a tree level is an encrypted address bit: no packing
     const int groups = packed ? (li.n_classes < (1 << li.z) ? li.n_classes : (1 << li.z)) : li.n_classes;
     int items = (int)(n * li.k0 * groups);
     if (items == 0) return cudaSuccess;
+    if (vp_digits_words(li) == 0) digits = nullptr;
+    if (digits) {
+        const int d_items = li.k0 * groups;
+        const int d_grid = grid < d_items ? grid : d_items;
+        cudaError_t e = li.ext->vp_digits(li, model, d_items, digits, d_grid, packed, st);
+        (*li.launches)++;
+        if (e != cudaSuccess) return e;
+    }
     if (grid > items) grid = items;
-    cudaError_t e = li.ext->vp(li, model, rgsw, items, resp, acc, grid, packed, st);
+    cudaError_t e = li.ext->vp(li, model, rgsw, items, resp, acc, grid, packed, digits, st);
     (*li.launches)++;
     return e;
 }

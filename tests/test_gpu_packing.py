@@ -37,18 +37,20 @@ def test_tiny_packed_responses(name):
         assert torch.equal(resp, R["resp"])
 
 
-@pytest.mark.parametrize("name,rams", [("cfg1", [0, 17, 29]), ("cfg3", [5, 146])])
-def test_workload_packed_sampled(name, rams):
+@pytest.mark.parametrize("name,rams,n_test", [("cfg1", [0, 17, 29], 1), ("cfg3", [5, 146], 2)])
+def test_workload_packed_sampled(name, rams, n_test):
+    """Two cfg3 test samples: the batch path that transforms the first
+    CMUX's digits once for both."""
     cfg = get_config(name)
     o = Oracle(cfg)
     P = o.P
-    R = run_pipeline(cfg, 2, 1)
+    R = run_pipeline(cfg, 2, n_test)
     s = R["sess"]
-    resp, _ = s.infer(R["model"], R["trg"], 1, packed=True)
+    resp, _ = s.infer(R["model"], R["trg"], n_test, packed=True)
     torch.cuda.synchronize()
     sk = o.keygen(21)
     obits = wisard.encode(P, R["vals"])
     H = o.train(o.new_model(), sk, 31, obits, R["labels"], rams=rams)
     oresp, _ = o.infer_packed(H, sk, 41, wisard.encode(P, R["tvals"]), rams=rams)
-    gresp = u64(resp).reshape(1, cfg.n_classes, P.k0, -1)
+    gresp = u64(resp).reshape(n_test, cfg.n_classes, P.k0, -1)
     assert np.array_equal(gresp[:, :, rams], oresp)

@@ -196,7 +196,7 @@ def test_ntt_is_evaluation_at_odd_powers(name, ntt_loge, ntt_limbs):
 @pytest.mark.parametrize("name,n_train,n_test,rams", [
     ("cfg1", 6, 3, [0, 13, 29]),
     ("cfg2", 3, 2, [0, 77, 130]),
-    ("cfg3", 2, 1, [5, 146]),
+    ("cfg3", 2, 2, [5, 146]),
     ("cfg4", 2, 1, [0, 503]),
 ])
 def test_workload_parameters_sampled_parity(name, n_train, n_test, rams):
