@@ -185,11 +185,11 @@ int hw_get_ram_slots(const hw_ctx* ctx, int32_t* ram_slot_host, size_t n);
 
 /* Scratch words hw_train_accumulate / hw_infer need for a batch of n samples:
  * buffers per resident block of the persistent kernels, and for hw_infer at
- * n >= 2 one set of the first blind-rotation CMUX's digit transforms per
- * (RAM, class) (2 dnum r N words each; its source is the stored ciphertext,
- * shared by the batch; none when a CMUX-tree level is an encrypted bit or
- * the external product runs in 32-bit words).  Neither grows further with n;
- * hw_infer_packed and hw_infer_plain need no more than hw_infer. */
+ * n >= 2 one set of the first CMUX's digit transforms per (RAM, class)
+ * (2 dnum r N words each; that CMUX's source is made of stored ciphertexts
+ * only, shared by the batch; none when the external product runs in 32-bit
+ * words).  Neither grows further with n.  hw_infer_packed needs what
+ * hw_infer needs; hw_infer_plain needs hw_infer_scratch_words(ctx, 1). */
 size_t hw_train_scratch_words(const hw_ctx* ctx, size_t n);
 size_t hw_infer_scratch_words(const hw_ctx* ctx, size_t n);
 
@@ -265,7 +265,8 @@ int hw_infer_packed(hw_ctx* ctx, const uint64_t* model_dev, const uint64_t* rgsw
  * hw_plain_model_words(ctx) words of tables in the internal evaluation form
  * (valid for contexts of the same geometry).
  * hw_infer_plain: responses and sums laid out as hw_infer's (they decrypt to
- * the same counters; the ciphertexts differ); scratch as hw_infer. */
+ * the same counters; the ciphertexts differ); scratch of
+ * hw_infer_scratch_words(ctx, 1) words whatever n. */
 size_t hw_plain_model_words(const hw_ctx* ctx);
 int hw_plain_model_load(hw_ctx* ctx, const int64_t* counts_dev, uint64_t* plain_dev, void* stream);
 int hw_infer_plain(hw_ctx* ctx, const uint64_t* plain_dev, const uint64_t* rgsw_dev, size_t n,

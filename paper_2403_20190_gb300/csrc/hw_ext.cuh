@@ -250,9 +250,10 @@ __device__ __forceinline__ void extract_lwe_at(const DevCtx& C, const u64* ct, i
 // rotation X^-(c >> z).  The encrypted address bits then blind-rotate with
 // weights +2^k (X^-2^k) and the last CMUX writes ExtractLWE(., 0) directly.
 // Per-block scratch: two accumulators and their evaluation forms.  With
-// `digits` (from k_vp_digits, z <= L) the first CMUX of item (RAM j, class c)
-// takes its digits' transforms from digits + (j G + c) 2 dnum r N: its source
-// is the stored ciphertext, the same for every sample of the batch.
+// `digits` (from k_vp_digits) the first CMUX of item (RAM j, class c) --
+// the encrypted tree level's when z > L, else the first rotation's -- takes
+// its digits' transforms from digits + (j G + c) 2 dnum r N: its source is
+// made of stored ciphertexts only, the same for every sample of the batch.
 // ---------------------------------------------------------------------------
 template <int LOGN, int LOGE, int NP, int SM, int PK>
 __global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP, SM>::T, ExtCfg<LOGN, LOGE, NP, SM>::MINB)
@@ -305,6 +306,12 @@ __global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP, SM>::T, ExtCfg<LOGN, LO
             const int slot = bit_slot(C, j, C.z - 1);
             if (slot < 0) {
                 src = lo;
+            } else if (digits) {  // the digits of hi - lo, transformed once per batch
+                ext_product<LOGN, LOGE, NP, X::ACC, true>(
+                    C, sample + (size_t)slot * C.rgsw_words, hi, 0, lo, 0, EXT_ADD, acc[0], xc,
+                    ExtNtt{nullptr, nullptr, -1, 0, nullptr, 0,
+                           digits + ((size_t)j * G + c) * (size_t)(2 * C.dnum * C.r) * C.n});
+                src = acc[0];
             } else {
                 ext_product<LOGN, LOGE, NP, X::ACC>(C, sample + (size_t)slot * C.rgsw_words, hi, 0, lo,
                                                   0, EXT_ADD, acc[0], xc,
@@ -382,11 +389,13 @@ __global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP, SM>::T, ExtCfg<LOGN, LO
 }
 
 // ---------------------------------------------------------------------------
-// The first CMUX's digit transforms of every (RAM j, class c) item of VP
-// (z <= L): its source is the stored ciphertext H[j][c mod 2^z] rotated by
-// the clear label bits, the same for every sample, so the 2 dnum r forward
-// transforms are computed once per batch; k_vp_infer reads them.  Item
-// j G + c (G classes, or groups with PK) writes digits + item 2 dnum r N.
+// The first CMUX's digit transforms of every (RAM j, class c) item of VP:
+// its source is the stored ciphertext H[j][c mod 2^z] rotated by the clear
+// label bits (z <= L), or the difference of the two stored ciphertexts the
+// encrypted tree level selects between (z > L), the same for every sample,
+// so the 2 dnum r forward transforms are computed once per batch;
+// k_vp_infer reads them.  Item j G + c (G classes, or groups with PK)
+// writes digits + item 2 dnum r N.
 // ---------------------------------------------------------------------------
 template <int LOGN, int LOGE, int NP, int SM, int PK>
 __global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP, SM>::T, ExtCfg<LOGN, LOGE, NP, SM>::MINB)
@@ -402,6 +411,13 @@ __global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP, SM>::T, ExtCfg<LOGN, LO
     const size_t per = (size_t)2 * C.dnum * C.r * C.n;
     for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
         const int c = item % G, j = item / G;
+        if (C.z > C.L) {  // the encrypted tree level's CMUX: D = H[j][c + 2^(z-1)] - H[j][c]
+            if (bit_slot(C, j, C.z - 1) < 0) continue;  // a constant-0 bit: no CMUX
+            const u64* Hj = model + (size_t)j * C.k1 * rl;
+            ext_digits<LOGN, LOGE, NP>(C, Hj + (size_t)C.slot_of[c + (1 << (C.z - 1))] * rl, 0,
+                                       Hj + (size_t)C.slot_of[c] * rl, 0, xc, digits + (size_t)item * per);
+            continue;
+        }
         const u64* src = model + (size_t)j * C.k1 * rl + (size_t)C.slot_of[c & ((1 << C.z) - 1)] * rl;
         const int R = PK ? 0 : c >> C.z;
         const int e0 = (two_n - R) % two_n;

@@ -80,7 +80,7 @@ cudaError_t launch_encrypt(const LaunchInfo& li, const uint64_t* key, const uint
 cudaError_t launch_ivp_train(const LaunchInfo& li, const uint64_t* rgsw, size_t n, uint64_t* model,
                              uint64_t* acc, int grid, cudaStream_t st);
 cudaError_t launch_model_reduce(const LaunchInfo& li, uint64_t* model, cudaStream_t st);
-// With `digits` (vp_digits_words of them, z <= L) the first CMUX of every
+// With `digits` (vp_digits_words of them) the first CMUX of every
 // item takes its digit transforms from there, computed once for the batch.
 cudaError_t launch_vp_infer(const LaunchInfo& li, const uint64_t* model, const uint64_t* rgsw,
                             size_t n, uint64_t* resp, uint64_t* acc, int grid, cudaStream_t st,

@@ -123,11 +123,9 @@ cudaError_t launch_model_reduce(const LaunchInfo& li, uint64_t* model, cudaStrea
 }
 
 // Words of the first CMUX's digit transforms: one set of 2 dnum r
-// polynomials per (RAM, class); none when a tree level is encrypted (the
-// first CMUX's source then depends on the sample) or for the 32-bit
-// external product.
+// polynomials per (RAM, class); none for the 32-bit external product.
 size_t vp_digits_words(const LaunchInfo& li) {
-    if (li.z > li.L || li.ext32) return 0;
+    if (li.ext32) return 0;
     return (size_t)li.k0 * li.n_classes * 2 * li.dnum * li.r * li.n;
 }
 

@@ -197,7 +197,7 @@ def test_ntt_is_evaluation_at_odd_powers(name, ntt_loge, ntt_limbs):
     ("cfg1", 6, 3, [0, 13, 29]),
     ("cfg2", 3, 2, [0, 77, 130]),
     ("cfg3", 2, 2, [5, 146]),
-    ("cfg4", 2, 1, [0, 503]),
+    ("cfg4", 2, 2, [0, 503]),
 ])
 def test_workload_parameters_sampled_parity(name, n_train, n_test, rams):
     """Real ring sizes and primes: RGSW rows, trained model rows and

@@ -99,6 +99,8 @@ def test_plain_argument_checks():
     resp, sums, scratch = sess.infer_buffers(2)
     rg = sess.words(2 * sess.sz["sample_words"])
     B.hw_infer_plain(sess.ctx, plain, rg, 0, resp, sums, scratch)  # empty batch: nothing to do
+    # inference against a clear model needs the persistent blocks' buffers
+    # only (hw_infer's scratch for one sample)
     with pytest.raises(B.HwError):
-        B.hw_infer_plain(sess.ctx, plain, rg, 2, resp, sums, scratch[:-1])
+        B.hw_infer_plain(sess.ctx, plain, rg, 2, resp, sums, scratch[:B.hw_infer_scratch_words(sess.ctx, 1) - 1])
     assert B.hw_plain_model_words(sess.ctx) == cfg.n_classes * P.k0 * P.r * P.n
