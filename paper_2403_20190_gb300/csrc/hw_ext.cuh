@@ -371,6 +371,8 @@ __global__ void __launch_bounds__(ExtCfg<LOGN, LOGE, NP, SM>::T, ExtCfg<LOGN, LO
             const int mode = to_lwe ? EXT_LWE : EXT_ADD;
             if (dg)  // the first CMUX, its digit transforms given
                 ext_product<LOGN, LOGE, NP, X::ACC, true>(C, ct, src, eA, src, e0, mode, dst, xc, nt);
+            else if (to_lwe)  // the last CMUX, straight into ExtractLWE(., 0)
+                ext_product<LOGN, LOGE, NP, X::ACC, false, true>(C, ct, src, eA, src, e0, mode, dst, xc, nt);
             else
                 ext_product<LOGN, LOGE, NP, X::ACC>(C, ct, src, eA, src, e0, mode, dst, xc, nt);
             dg = nullptr;

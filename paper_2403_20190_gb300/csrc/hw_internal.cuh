@@ -734,7 +734,7 @@ __device__ __noinline__ void ext_product32(const DevCtx& C, const u64* __restric
     __syncthreads();  // dst complete for the whole block
 }
 
-template <int LOGN, int LOGE, int NP, int AS = 0, bool DG = false>
+template <int LOGN, int LOGE, int NP, int AS = 0, bool DG = false, bool B0 = false>
 __device__ __noinline__ void ext_product(const DevCtx& C, const u64* __restrict__ rgsw,
                                          const u64* srcA, int eA, const u64* srcB, int eB, int mode,
                                          u64* dst, Xchg& xc, ExtNtt nt) {
@@ -897,6 +897,33 @@ __device__ __noinline__ void ext_product(const DevCtx& C, const u64* __restrict_
         const u64 ninv = C.n_inv[j], ninv_s = C.n_inv_s[j];
         constexpr int NPI = NP < 2 ? NP : 2;  // the two output components
         for (int oc0 = 0; oc0 < 2; oc0 += NPI) {
+            if (B0 && NPI == 1 && oc0 == 1 && mode == EXT_LWE) {
+                // ExtractLWE keeps b_0 only: coefficient 0 of the inverse
+                // transform is the sum of the (N^-1-scaled) evaluations, so a
+                // block sum replaces the transform (B0 instances only: the
+                // others keep their register allocation)
+                u64 sum = 0;
+#pragma unroll
+                for (int e = 0; e < E; e++) {
+                    u64 x = shoup_mul_lazy(acc.get(1, e), ninv, ninv_s, qj);
+                    sum = add_mod(sum, x >= qj ? x - qj : x, qj);
+                }
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) sum = add_mod(sum, __shfl_down_sync(0xffffffffu, sum, off), qj);
+                u64* red = xc.next();
+                if (xc.b0 == xc.b1) __syncthreads();  // one buffer: the last exchange's reads are done
+                if ((tid & 31) == 0) red[tid >> 5] = sum;
+                __syncthreads();
+                if (tid < 32) {
+                    u64 t = tid < T / 32 ? red[tid] : 0;
+#pragma unroll
+                    for (int off = 16; off > 0; off >>= 1) t = add_mod(t, __shfl_down_sync(0xffffffffu, t, off), qj);
+                    if (tid == 0)
+                        dst[(size_t)j * (N + 1) + N] =
+                            add_mod(t, rot_read(srcB + ((size_t)r + j) * N, 0, eB, N, qj), qj);
+                }
+                continue;
+            }
             u64 v[NPI][E];
 #pragma unroll
             for (int pp = 0; pp < NPI; pp++)
