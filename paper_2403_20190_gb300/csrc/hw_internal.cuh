@@ -908,20 +908,29 @@ __device__ __noinline__ void ext_product(const DevCtx& C, const u64* __restrict_
                     u64 x = shoup_mul_lazy(acc.get(1, e), ninv, ninv_s, qj);
                     sum = add_mod(sum, x >= qj ? x - qj : x, qj);
                 }
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1) sum = add_mod(sum, __shfl_down_sync(0xffffffffu, sum, off), qj);
                 u64* red = xc.next();
                 if (xc.b0 == xc.b1) __syncthreads();  // one buffer: the last exchange's reads are done
-                if ((tid & 31) == 0) red[tid >> 5] = sum;
-                __syncthreads();
-                if (tid < 32) {
-                    u64 t = tid < T / 32 ? red[tid] : 0;
+                u64 t = 0;
+                if constexpr (T >= 32) {  // whole warps: shuffles, then one warp over the warps' sums
 #pragma unroll
-                    for (int off = 16; off > 0; off >>= 1) t = add_mod(t, __shfl_down_sync(0xffffffffu, t, off), qj);
+                    for (int off = 16; off > 0; off >>= 1)
+                        sum = add_mod(sum, __shfl_down_sync(0xffffffffu, sum, off), qj);
+                    if ((tid & 31) == 0) red[tid >> 5] = sum;
+                    __syncthreads();
+                    if (tid < 32) {
+                        t = tid < T / 32 ? red[tid] : 0;
+#pragma unroll
+                        for (int off = 16; off > 0; off >>= 1)
+                            t = add_mod(t, __shfl_down_sync(0xffffffffu, t, off), qj);
+                    }
+                } else {  // fewer threads than a warp (the smallest rings)
+                    red[tid] = sum;
+                    __syncthreads();
                     if (tid == 0)
-                        dst[(size_t)j * (N + 1) + N] =
-                            add_mod(t, rot_read(srcB + ((size_t)r + j) * N, 0, eB, N, qj), qj);
+                        for (int k = 0; k < T; k++) t = add_mod(t, red[k], qj);
                 }
+                if (tid == 0)
+                    dst[(size_t)j * (N + 1) + N] = add_mod(t, rot_read(srcB + ((size_t)r + j) * N, 0, eB, N, qj), qj);
                 continue;
             }
             u64 v[NPI][E];
