@@ -84,8 +84,8 @@ def parse():
 # sources exists.
 PROFILED_VP_TRAFFIC = [
     {"config": "cfg3", "ext_loge": 3, "ext_np": 1, "ext_smem": 3, "ext_blocks_per_sm": 1, "l2_persist": 0,
-     "bytes_per_test_sample": 8.13325e10,
-     "sha256": "fd40b0d3e4a11c82195baac36f780c73d5071a295f6e89570aed657085089c5a"},
+     "bytes_per_test_sample": 7.96436e10,
+     "sha256": "390053d8ae31d876b16edc9f70df0a9eef4c8f8f0ca4677abe20607d138753d7"},
 ]
 PROFILED_SOURCES = (("paper_2403_20190_gb300/csrc/hw_ext.cuh", "// Encrypted bit slot that drives",
                      "// EncRGSW."),
