@@ -42,6 +42,7 @@ extern "C" {
 #define HW_EINVAL (-1)    /* bad argument, size or parameter */
 #define HW_ENOMEM (-2)    /* a caller buffer is too small */
 #define HW_ECUDA (-3)     /* a CUDA call failed; see hw_last_error() */
+#define HW_ETIMEOUT (-4)  /* a bounded device-side wait ran out (see hw_check_context) */
 #define HW_EMISMATCH (-5) /* object made for other parameters */
 
 /* PD-act activations (Section 3.2): floor(log2(x+1)), min(floor(log2(x+1)),
@@ -141,9 +142,11 @@ int hw_create_tuned(const hw_params* params, const hw_geometry* geometry, int cu
 /* Self-check (no counterpart in the paper): HW_OK while the context's device
  * tables (transform, rotation and index tables and the device copy of the
  * context) are byte for byte what hw_create uploaded, HW_EMISMATCH if
- * anything has written into them since.  Synchronous; copies the tables
- * back (a few MB).  Lets a long-running caller detect a stray write before
- * it launches work on a damaged context. */
+ * anything has written into them since, HW_ETIMEOUT if a bounded wait of
+ * the batched transform ran out on this device since the library was
+ * loaded.  Synchronous; copies the tables back (a few MB).  Lets a
+ * long-running caller detect a stray write before it launches work on a
+ * damaged context. */
 int hw_check_context(const hw_ctx* ctx);
 /* The context's geometry with every default resolved. */
 int hw_get_geometry(const hw_ctx* ctx, hw_geometry* out);
@@ -415,7 +418,12 @@ int hw_import_rgsw(hw_ctx* ctx, const uint64_t* canonical_dev, size_t count, uin
 
 /* Batched forward / inverse negacyclic transform of count polynomials in
  * place, polynomial t using prime (t mod r).  The forward output is in the
- * library's evaluation order; inverse(forward(x)) = x. */
+ * library's evaluation order; inverse(forward(x)) = x.  With a 16-byte
+ * aligned poly_dev a persistent grid streams the polynomials through shared
+ * memory with bulk asynchronous copies (one in flight per block while it
+ * transforms the previous one); its waits are bounded, and one that runs
+ * out (not expected) stops the block and makes hw_check_context return
+ * HW_ETIMEOUT.  Other buffers take one block per polynomial. */
 int hw_ntt_forward(hw_ctx* ctx, uint64_t* poly_dev, size_t count, void* stream);
 int hw_ntt_inverse(hw_ctx* ctx, uint64_t* poly_dev, size_t count, void* stream);
 

@@ -20,6 +20,7 @@ HW_DEC_RLWE = 0
 HW_DEC_LWE = 1
 HW_DEC_MODEL = 2
 HW_EINVAL = -1
+HW_ETIMEOUT = -4
 HW_EMISMATCH = -5
 HW_MODEL_MAGIC = 0x3144524153495748
 HW_MODEL_VERSION = 1

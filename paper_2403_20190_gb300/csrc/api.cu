@@ -707,6 +707,9 @@ extern "C" int hw_check_context(const hw_ctx* c) {
     if (e != cudaSuccess) return fail(HW_ECUDA, "hw_check_context: copy failed: %s", cudaGetErrorString(e));
     if (fnv1a(img.data(), img.size()) != c->tables_hash)
         return fail(HW_EMISMATCH, "hw_check_context: the context's device tables changed since creation");
+    const unsigned to = ntt_wait_timeouts();
+    if (to == ~0u) return fail(HW_ECUDA, "hw_check_context: the transform's wait counter cannot be read");
+    if (to) return fail(HW_ETIMEOUT, "hw_check_context: %u bulk-copy waits of the batched transform ran out", to);
     return HW_OK;
 }
 

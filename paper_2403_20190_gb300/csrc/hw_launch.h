@@ -69,6 +69,7 @@ const ExtOps* hw_ext_table_12_p1(int* count);
 const ExtOps* hw_ext_table(int log_n, int* count);
 const ExtOps* hw_ext_find(int log_n, int loge, int np, int sm);
 
+unsigned ntt_wait_timeouts();
 cudaError_t launch_keygen(const LaunchInfo& li, uint64_t seed, uint64_t* key, cudaStream_t st);
 cudaError_t launch_encode(const LaunchInfo& li, const uint8_t* values, size_t n, uint8_t* bits,
                           cudaStream_t st);

@@ -145,6 +145,42 @@ def test_ntt_roundtrip_and_edge_values():
     assert np.array_equal(u64(dev).reshape(count, n), x)
 
 
+@pytest.mark.parametrize("name", ["cfg1", "cfg3"])
+def test_ntt_bulk_pipeline_equals_one_block_per_polynomial(name):
+    """The bulk-copy pipeline (16-byte aligned buffers: persistent blocks,
+    several polynomials each through two alternating stages) against the
+    one-block-per-polynomial form (the same data 8 bytes off that
+    alignment), both directions; cfg1 runs the 32-bit arithmetic, cfg3 the
+    64-bit one; the count leaves a ragged last round of the grid."""
+    from paper_2403_20190_gb300 import binding as B
+    cfg = get_config(name)
+    sess = session(cfg)
+    sz = sess.sz
+    n, r = sz["n"], sz["r"]
+    count = 3 * 152 * (6 if n <= 1024 else 1) + 5
+    rng = np.random.default_rng(7)
+    x = np.zeros((count, n), dtype=np.uint64)
+    for t in range(count):
+        x[t] = rng.integers(0, sz["q"][t % r], size=n, dtype=np.uint64)
+    flat = torch.from_numpy(x.reshape(-1).view(np.int64)).to(sess.device)
+    buf = torch.zeros(count * n + 2, dtype=torch.int64, device=sess.device)
+    aligned = buf[:count * n]
+    shifted = buf.new_zeros(count * n + 2)[1:1 + count * n]
+    assert aligned.data_ptr() % 16 == 0 and shifted.data_ptr() % 16 == 8
+    aligned.copy_(flat)
+    shifted.copy_(flat)
+    B.hw_ntt_forward(sess.ctx, aligned, count)
+    B.hw_ntt_forward(sess.ctx, shifted, count)
+    torch.cuda.synchronize()
+    assert torch.equal(aligned, shifted)
+    assert not torch.equal(aligned, flat)
+    B.hw_ntt_inverse(sess.ctx, aligned, count)
+    B.hw_ntt_inverse(sess.ctx, shifted, count)
+    torch.cuda.synchronize()
+    assert torch.equal(aligned, flat) and torch.equal(shifted, flat)
+    B.hw_check_context(sess.ctx)  # no bulk-copy wait ran out
+
+
 def _library_root(q, log_n):
     """The library's documented root choice: psi = x^((q-1)/2N) for the
     first odd x >= 3 with psi^N = -1."""
