@@ -418,12 +418,13 @@ int hw_import_rgsw(hw_ctx* ctx, const uint64_t* canonical_dev, size_t count, uin
 
 /* Batched forward / inverse negacyclic transform of count polynomials in
  * place, polynomial t using prime (t mod r).  The forward output is in the
- * library's evaluation order; inverse(forward(x)) = x.  With a 16-byte
- * aligned poly_dev a persistent grid streams the polynomials through shared
- * memory with bulk asynchronous copies (one in flight per block while it
- * transforms the previous one); its waits are bounded, and one that runs
- * out (not expected) stops the block and makes hw_check_context return
- * HW_ETIMEOUT.  Other buffers take one block per polynomial. */
+ * library's evaluation order; inverse(forward(x)) = x.  In 32-bit
+ * arithmetic (ntt_limbs = 1) with a 16-byte aligned poly_dev, a persistent
+ * grid streams the polynomials through shared memory with bulk asynchronous
+ * copies (one in flight per block while it transforms the previous one);
+ * its waits are bounded, and one that runs out (not expected) stops the
+ * block and makes hw_check_context return HW_ETIMEOUT.  Otherwise one
+ * block transforms one polynomial. */
 int hw_ntt_forward(hw_ctx* ctx, uint64_t* poly_dev, size_t count, void* stream);
 int hw_ntt_inverse(hw_ctx* ctx, uint64_t* poly_dev, size_t count, void* stream);
 

@@ -105,8 +105,9 @@ __global__ void __launch_bounds__(Ring<LOGN, LOGE>::T)
 }
 
 // ---------------------------------------------------------------------------
-// Bulk-asynchronous form of the same transforms (the default when the
-// buffer is 16-byte aligned): a persistent grid, each block streaming its
+// Bulk-asynchronous form of the same transforms (the default for the 32-bit
+// arithmetic when the buffer is 16-byte aligned): a persistent grid, each
+// block streaming its
 // polynomials through two shared-memory stages.  One thread issues the
 // bulk copy (cp.async.bulk) of polynomial k+1 into one stage, completing on
 // that stage's mbarrier, while the block transforms polynomial k in the
@@ -309,7 +310,12 @@ struct NttVariant {
     }
     static cudaError_t launch(const LaunchInfo& li, uint64_t* poly, size_t count, int inverse,
                               cudaStream_t st) {
-        if (((uintptr_t)poly & 15) == 0) {  // bulk copies need 16-byte aligned addresses
+        // the bulk pipeline for the 32-bit arithmetic, whose transform is
+        // bound by HBM; the 64-bit one is bound by integer issue and keeps
+        // more resident warps per SM with one block per polynomial (its two
+        // stages would cost it blocks); bulk copies need 16-byte aligned
+        // addresses
+        if (W32 && ((uintptr_t)poly & 15) == 0) {
             int occ = 0;
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_ntt_bulk<LOGN, LOGE, W32>, T,
                                                           NttBulkCfg<LOGN, LOGE>::SMEM);

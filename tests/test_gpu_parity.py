@@ -145,19 +145,21 @@ def test_ntt_roundtrip_and_edge_values():
     assert np.array_equal(u64(dev).reshape(count, n), x)
 
 
-@pytest.mark.parametrize("name", ["cfg1", "cfg3"])
-def test_ntt_bulk_pipeline_equals_one_block_per_polynomial(name):
-    """The bulk-copy pipeline (16-byte aligned buffers: persistent blocks,
-    several polynomials each through two alternating stages) against the
-    one-block-per-polynomial form (the same data 8 bytes off that
-    alignment), both directions; cfg1 runs the 32-bit arithmetic, cfg3 the
-    64-bit one; the count leaves a ragged last round of the grid."""
+@pytest.mark.parametrize("name,ntt_loge", [("cfg1", 4), ("cfg1", 3), ("z0", 4), ("z0", 3)])
+def test_ntt_bulk_pipeline_equals_one_block_per_polynomial(name, ntt_loge):
+    """The bulk-copy pipeline of the 32-bit transform (16-byte aligned
+    buffers: persistent blocks, several polynomials each through two
+    alternating stages) against the one-block-per-polynomial form (the same
+    data 8 bytes off that alignment), both directions, radix 16 and 8, on
+    cfg1's ring and on a 64-point ring (blocks smaller than a warp); the
+    count leaves a ragged last round of the grid."""
     from paper_2403_20190_gb300 import binding as B
-    cfg = get_config(name)
-    sess = session(cfg)
+    cfg = tiny_cfg(name) if name in TINY else get_config(name)
+    sess = session(cfg, dict(ntt_loge=ntt_loge, ntt_limbs=1))
+    assert (sess.geometry["ntt_loge"], sess.geometry["ntt_limbs"]) == (ntt_loge, 1)
     sz = sess.sz
     n, r = sz["n"], sz["r"]
-    count = 3 * 152 * (6 if n <= 1024 else 1) + 5
+    count = 3 * 152 * 32 + 5  # more than the persistent grid holds at once
     rng = np.random.default_rng(7)
     x = np.zeros((count, n), dtype=np.uint64)
     for t in range(count):
