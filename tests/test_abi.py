@@ -121,3 +121,13 @@ def test_buffer_arguments_must_be_tensors():
     assert binding._ptr(t).value == t.data_ptr()
     with pytest.raises(binding.HwError):
         binding._ptr(torch.zeros(4, 4)[:, 1])
+
+
+def test_binding_constants_match_the_header():
+    """The Python names of the header's error codes and decrypt kinds carry
+    the header's values."""
+    from paper_2403_20190_gb300 import binding
+    txt = open(os.path.join(ROOT, "include", "hwisard.h")).read()
+    defines = {m.group(1): int(m.group(2)) for m in re.finditer(r"#define (HW_[A-Z_]+) \(?(-?\d+)\)?", txt)}
+    for name in ("HW_EINVAL", "HW_ETIMEOUT", "HW_EMISMATCH", "HW_DEC_RLWE", "HW_DEC_LWE", "HW_DEC_MODEL"):
+        assert getattr(binding, name) == defines[name], name
