@@ -6,23 +6,33 @@
 //   D_{x,rho}(X) = sum_i Dec_rho(a_{i,x}) X^i.
 // Each D_{x,rho} is one transform per prime and a multiply-accumulate with
 // the key row in evaluation form; the key and every transform use the
-// 16-residues-per-thread geometry (thread-major evaluation layout).
+// 8-residues-per-thread geometry (PackGeo, thread-major evaluation layout).
 #include "cdt.cuh"
 #include "hw_internal.cuh"
 #include "hw_launch.h"
 
 #define HW_PACK_CHUNKS 256
 
+// The key-switching kernels' transform geometry: 8 residues per thread (N/8
+// threads), the widest blocks the transforms take, for latency hiding.
+template <int LOGN>
+struct PackGeo {
+    static constexpr int E = 8;
+    static constexpr int T = Ring<LOGN, 3>::T;
+    static constexpr int PD = Ring<LOGN, 3>::PADDED;
+    static constexpr size_t XCHG_BYTES = 2 * (size_t)PD * sizeof(u64);
+};
+
 // Key row (x, rho) at prime j: a from the KSK_A stream (two words per
 // coefficient), e from the KSK_E stream (one integer polynomial per row),
 // b = a s + e + s_x g_rho; stored in evaluation form, Montgomery
 // representation.  One block per (row, prime).
 template <int LOGN>
-__global__ void __launch_bounds__(Geo<LOGN>::T)
+__global__ void __launch_bounds__(PackGeo<LOGN>::T)
     k_ksk_gen(const DevCtx* __restrict__ Cp, const u64* __restrict__ key, u64 seed, u64* __restrict__ ksk) {
     extern __shared__ u64 smem[];
-    constexpr int N = Ring<LOGN>::N, T = Ring<LOGN>::T;
-    Xchg xc{smem, smem + Ring<LOGN>::PADDED, Ring<LOGN>::PADDED, 0};
+    constexpr int N = Ring<LOGN>::N, T = PackGeo<LOGN>::T, E = PackGeo<LOGN>::E, PD = PackGeo<LOGN>::PD;
+    Xchg xc{smem, smem + PD, PD, 0};
     const DevCtx& C = *Cp;
     const int tid = threadIdx.x, r = C.r;
     const size_t row = blockIdx.x / r;
@@ -30,30 +40,37 @@ __global__ void __launch_bounds__(Geo<LOGN>::T)
     const int x = (int)(row / C.dnum), rho = (int)(row % C.dnum);
     const PrimeConst P = C.P[j];
     const u64 q = P.q;
-    u64 va[16], ve[16];
-#pragma unroll
-    for (int kk = 0; kk < 16; kk++) {
-        const int k = tid + kk * T;
-        const Philox4 wa = hw_draw(seed, HW_TAG_KSK_A, (u64)(k >> 1), (u64)(row * r + j), 0);
-        va[kk] = reduce128(wa.v[2 * (k & 1)], wa.v[2 * (k & 1) + 1], P);
-        const Philox4 we = hw_draw(seed, HW_TAG_KSK_E, (u64)(k >> 2), (u64)row, 0);
-        ve[kk] = from_signed((int64_t)gaussian_from_word(we.v[k & 3]), q);
-    }
-    ntt_fwd1<LOGN>(va, xc, C, j);
-    ntt_fwd1<LOGN>(ve, xc, C, j);
     // the constant s_x g_rho, only at the gadget row's prime
     const u64 m = (j == rho / C.dpp) ? mont_mul(key[(size_t)j * N + x], to_mont(C.gconst[rho], P), P) : 0;
     const size_t rl = C.rlwe_words;
     u64* da = ksk + row * rl + (size_t)(0 * r + j) * N;
     u64* db = ksk + row * rl + (size_t)(1 * r + j) * N;
+    // a first: its row, and a s + s_x g_rho parked in the b row (each thread
+    // rewrites only its own words), then e; one polynomial in registers
+    u64 v[1][E];
 #pragma unroll
-    for (int e = 0; e < 16; e++) {
-        const u64 sM = key[(size_t)(r + j) * N + eval_addr(16 * tid + e, LOGN, C.ext_loge)];
-        const u64 a = reduce_full(va[e], P);
-        const u64 b = add_mod(add_mod(mont_mul(a, sM, P), reduce_full(ve[e], P), q), m, q);
-        da[e * T + tid] = to_mont(a, P);
-        db[e * T + tid] = to_mont(b, P);
+    for (int kk = 0; kk < E; kk++) {
+        const int k = tid + kk * T;
+        const Philox4 wa = hw_draw(seed, HW_TAG_KSK_A, (u64)(k >> 1), (u64)(row * r + j), 0);
+        v[0][kk] = reduce128(wa.v[2 * (k & 1)], wa.v[2 * (k & 1) + 1], P);
     }
+    ntt_fwd<LOGN, 3, 1>(v, xc, C, j);
+#pragma unroll
+    for (int e = 0; e < E; e++) {
+        const u64 sM = key[(size_t)(r + j) * N + eval_addr(E * tid + e, LOGN, C.ext_loge)];
+        const u64 a = reduce_full(v[0][e], P);
+        da[e * T + tid] = to_mont(a, P);
+        db[e * T + tid] = add_mod(mont_mul(a, sM, P), m, q);
+    }
+#pragma unroll
+    for (int kk = 0; kk < E; kk++) {
+        const int k = tid + kk * T;
+        const Philox4 we = hw_draw(seed, HW_TAG_KSK_E, (u64)(k >> 2), (u64)row, 0);
+        v[0][kk] = from_signed((int64_t)gaussian_from_word(we.v[k & 3]), q);
+    }
+    ntt_fwd<LOGN, 3, 1>(v, xc, C, j);
+#pragma unroll
+    for (int e = 0; e < E; e++) db[e * T + tid] = to_mont(add_mod(db[e * T + tid], reduce_full(v[0][e], P), q), P);
 }
 
 // The responses of a group of samples (k LWEs of r*(N+1) words each) to
@@ -98,12 +115,12 @@ __global__ void k_pack_b(const DevCtx* __restrict__ Cp, const u64* __restrict__ 
 // Partial sums over a chunk of (x, rho) pairs at prime j:
 // sum KS_{x,rho} * D_{x,rho} in evaluation form (both components).
 template <int LOGN>
-__global__ void __launch_bounds__(Geo<LOGN>::T)
+__global__ void __launch_bounds__(PackGeo<LOGN>::T)
     k_pack_mac(const DevCtx* __restrict__ Cp, const u64* __restrict__ ksk, const u64* __restrict__ A, int kp,
                int chunks, u64* __restrict__ partial) {
     extern __shared__ u64 smem[];
-    constexpr int N = Ring<LOGN>::N, T = Ring<LOGN>::T;
-    Xchg xc{smem, smem + Ring<LOGN>::PADDED, Ring<LOGN>::PADDED, 0};
+    constexpr int N = Ring<LOGN>::N, T = PackGeo<LOGN>::T, E = PackGeo<LOGN>::E, PD = PackGeo<LOGN>::PD;
+    Xchg xc{smem, smem + PD, PD, 0};
     const DevCtx& C = *Cp;
     const int tid = threadIdx.x, r = C.r;
     const int j = (int)(blockIdx.x % r);
@@ -120,10 +137,10 @@ __global__ void __launch_bounds__(Geo<LOGN>::T)
     // at N = 8192 the a component's accumulators live in the block's own
     // shared-memory slots (registers would spill); elsewhere in registers
     constexpr bool ACC_SMEM = LOGN >= 13;
-    u64 acc[2][16];
-    u64* acc0 = smem + 2 * Ring<LOGN>::PADDED + tid;
+    u64 acc[2][E];
+    u64* acc0 = smem + 2 * PD + tid;
 #pragma unroll
-    for (int e = 0; e < 16; e++) {
+    for (int e = 0; e < E; e++) {
         acc[0][e] = acc[1][e] = 0;
         if (ACC_SMEM) acc0[e * T] = 0;
     }
@@ -132,18 +149,18 @@ __global__ void __launch_bounds__(Geo<LOGN>::T)
         const int gi = rho / C.dpp, gk = rho % C.dpp;
         const u64 qi = C.P[gi].q;
         const u64* Arow = A + ((size_t)gi * N + x) * kp;
-        u64 v[16];
+        u64 v[1][E];
 #pragma unroll
-        for (int kk = 0; kk < 16; kk++) {
+        for (int kk = 0; kk < E; kk++) {
             const int i = tid + kk * T;
-            v[kk] = i < kp ? lift_small(gadget_digit(centre(Arow[i], qi), gk, C.dpp, C.log_beta), q) : 0;
+            v[0][kk] = i < kp ? lift_small(gadget_digit(centre(Arow[i], qi), gk, C.dpp, C.log_beta), q) : 0;
         }
-        ntt_fwd1<LOGN>(v, xc, C, j);
+        ntt_fwd<LOGN, 3, 1>(v, xc, C, j);
         const u64* ka = ksk + (size_t)pr * rl + (size_t)(0 * r + j) * N + tid;
         const u64* kb = ksk + (size_t)pr * rl + (size_t)(1 * r + j) * N + tid;
 #pragma unroll
-        for (int e = 0; e < 16; e++) {
-            const u64 d = v[e], wa = __ldg(ka + e * T), wb = __ldg(kb + e * T);
+        for (int e = 0; e < E; e++) {
+            const u64 d = v[0][e], wa = __ldg(ka + e * T), wb = __ldg(kb + e * T);
             if (ACC_SMEM)
                 acc0[e * T] = add_mod(acc0[e * T], redc(__umul64hi(d, wa), d * wa, P), q);
             else
@@ -154,19 +171,19 @@ __global__ void __launch_bounds__(Geo<LOGN>::T)
 #pragma unroll
     for (int comp = 0; comp < 2; comp++)
 #pragma unroll
-        for (int e = 0; e < 16; e++)
+        for (int e = 0; e < E; e++)
             partial[(((size_t)ch * 2 + comp) * r + j) * N + e * T + tid] =
                 (ACC_SMEM && comp == 0) ? acc0[e * T] : acc[comp][e];
 }
 
 // Sum of the partials, inverse transform, and C = (-S_a, B - S_b).
 template <int LOGN>
-__global__ void __launch_bounds__(Geo<LOGN>::T)
+__global__ void __launch_bounds__(PackGeo<LOGN>::T)
     k_pack_finish(const DevCtx* __restrict__ Cp, const u64* __restrict__ partial, const u64* __restrict__ B,
                   int chunks, u64* __restrict__ out) {
     extern __shared__ u64 smem[];
-    constexpr int N = Ring<LOGN>::N, T = Ring<LOGN>::T;
-    Xchg xc{smem, smem + Ring<LOGN>::PADDED, Ring<LOGN>::PADDED, 0};
+    constexpr int N = Ring<LOGN>::N, T = PackGeo<LOGN>::T, E = PackGeo<LOGN>::E, PD = PackGeo<LOGN>::PD;
+    Xchg xc{smem, smem + PD, PD, 0};
     const DevCtx& C = *Cp;
     const int tid = threadIdx.x, r = C.r;
     const int j = (int)(blockIdx.x % r), comp = (int)((blockIdx.x / r) % 2);
@@ -176,19 +193,19 @@ __global__ void __launch_bounds__(Geo<LOGN>::T)
     out += smp * C.rlwe_words;
     const PrimeConst P = C.P[j];
     const u64 q = P.q;
-    u64 v[16];
+    u64 v[1][E];
 #pragma unroll
-    for (int e = 0; e < 16; e++) {
+    for (int e = 0; e < E; e++) {
         u64 s = 0;
         for (int ch = 0; ch < chunks; ch++)
             s = add_mod(s, partial[(((size_t)ch * 2 + comp) * r + j) * N + e * T + tid], q);
-        v[e] = shoup_mul_lazy(s, C.n_inv[j], C.n_inv_s[j], q);
+        v[0][e] = shoup_mul_lazy(s, C.n_inv[j], C.n_inv_s[j], q);
     }
-    ntt_inv1<LOGN>(v, xc, C, j);
+    ntt_inv<LOGN, 3, 1>(v, xc, C, j);
 #pragma unroll
-    for (int kk = 0; kk < 16; kk++) {
+    for (int kk = 0; kk < E; kk++) {
         const int y = tid + kk * T;
-        const u64 val = v[kk] >= q ? v[kk] - q : v[kk];
+        const u64 val = v[0][kk] >= q ? v[0][kk] - q : v[0][kk];
         out[(size_t)(comp * r + j) * N + y] = comp == 0 ? neg_mod(val, q) : sub_mod(B[(size_t)j * N + y], val, q);
     }
 }
@@ -200,7 +217,7 @@ __global__ void __launch_bounds__(Geo<LOGN>::T)
 // component at N = 8192.
 template <int LOGN>
 constexpr size_t pack_mac_smem() {
-    return Geo<LOGN>::XCHG_BYTES + (LOGN >= 13 ? (size_t)Ring<LOGN>::N * sizeof(u64) : 0);
+    return PackGeo<LOGN>::XCHG_BYTES + (LOGN >= 13 ? (size_t)Ring<LOGN>::N * sizeof(u64) : 0);
 }
 
 #define HW_PACK_DISPATCH(logn, BODY) \
@@ -233,7 +250,7 @@ cudaError_t launch_ksk_gen(const LaunchInfo& li, const uint64_t* key, uint64_t s
     const size_t blocks = (size_t)li.n * li.dnum * li.r;
 #define B(L)                                                                                        \
     case L:                                                                                         \
-        k_ksk_gen<L><<<(unsigned)blocks, Geo<L>::T, Geo<L>::XCHG_BYTES, st>>>(li.dctx, key, seed, ksk); \
+        k_ksk_gen<L><<<(unsigned)blocks, PackGeo<L>::T, PackGeo<L>::XCHG_BYTES, st>>>(li.dctx, key, seed, ksk); \
         break;
     HW_PACK_DISPATCH(li.log_n, B)
 #undef B
@@ -263,9 +280,9 @@ cudaError_t launch_pack(const LaunchInfo& li, const uint64_t* ksk, const uint64_
         k_pack_b<<<(unsigned)bb, 256, 0, st>>>(li.dctx, rs, k, (int)S, Bv);
 #define B(L)                                                                                            \
     case L:                                                                                             \
-        k_pack_mac<L><<<(unsigned)(S * chunks * r), Geo<L>::T, pack_mac_smem<L>(), st>>>(li.dctx, ksk, A, kp,  \
+        k_pack_mac<L><<<(unsigned)(S * chunks * r), PackGeo<L>::T, pack_mac_smem<L>(), st>>>(li.dctx, ksk, A, kp, \
                                                                                        chunks, partial); \
-        k_pack_finish<L><<<(unsigned)(S * 2 * r), Geo<L>::T, Geo<L>::XCHG_BYTES, st>>>(li.dctx, partial, Bv,  \
+        k_pack_finish<L><<<(unsigned)(S * 2 * r), PackGeo<L>::T, PackGeo<L>::XCHG_BYTES, st>>>(li.dctx, partial, Bv, \
                                                                                      chunks, out);     \
         break;
         HW_PACK_DISPATCH(li.log_n, B)
@@ -280,7 +297,7 @@ cudaError_t launch_pack(const LaunchInfo& li, const uint64_t* ksk, const uint64_
 cudaError_t hw_pack_kernels_init(const LaunchInfo& li) {
     cudaError_t e = cudaSuccess;
 #define A(K, L) \
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(K<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Geo<L>::XCHG_BYTES);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(K<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PackGeo<L>::XCHG_BYTES);
 #define X(L)                  \
     case L:                   \
         A(k_ksk_gen, L)       \
