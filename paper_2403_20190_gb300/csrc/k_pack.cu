@@ -112,6 +112,35 @@ __global__ void k_pack_b(const DevCtx* __restrict__ Cp, const u64* __restrict__ 
     }
 }
 
+// ntt_fwd<LOGN, 3, 1> for a polynomial whose upper half is zero (D has k_p
+// <= N/2 coefficients) when the first round is the single stage 0
+// (LOGN mod 3 = 1): that stage pairs x_p with x_{p+N/2} = 0, so it leaves
+// x_p and writes x_p + 2q (the lazy form of x_p - w*0) without a multiply;
+// the exchange and the remaining rounds are ntt_fwd's.
+template <int LOGN>
+__device__ __forceinline__ void fwd_upper_zero(u64 (&v)[1][8], Xchg& xc, const DevCtx& C, int j) {
+    if constexpr (LOGN % 3 == 1) {
+        constexpr int G = 4, R2 = FwdR<LOGN, 3, 1>::R, G2 = 8 >> R2;
+        const u64 q = C.P[j].q, q2 = 2 * q;
+#pragma unroll
+        for (int gg = 0; gg < G; gg++) v[0][gg + G] = v[0][gg] + q2;
+        u64* sm = xc.next();
+        if (xc.b0 == xc.b1) __syncthreads();
+#pragma unroll
+        for (int gg = 0; gg < G; gg++)
+#pragma unroll
+            for (int e = 0; e < 2; e++) sm[padw<3>(fpos<LOGN, 3, 0, 1>(gg, e))] = v[0][gg + e * G];
+        __syncthreads();
+#pragma unroll
+        for (int gg = 0; gg < G2; gg++)
+#pragma unroll
+            for (int e = 0; e < (1 << R2); e++) v[0][gg + e * G2] = sm[padw<3>(fpos<LOGN, 3, 1, R2>(gg, e))];
+        fwd_from<LOGN, 3, 1, 1>(v, xc, C.tw_fwd + (size_t)j * Ring<LOGN>::N, q, q2);
+    } else {
+        ntt_fwd<LOGN, 3, 1>(v, xc, C, j);
+    }
+}
+
 // Partial sums over a chunk of (x, rho) pairs at prime j:
 // sum KS_{x,rho} * D_{x,rho} in evaluation form (both components).
 template <int LOGN>
@@ -155,7 +184,10 @@ __global__ void __launch_bounds__(PackGeo<LOGN>::T)
             const int i = tid + kk * T;
             v[0][kk] = i < kp ? lift_small(gadget_digit(centre(Arow[i], qi), gk, C.dpp, C.log_beta), q) : 0;
         }
-        ntt_fwd<LOGN, 3, 1>(v, xc, C, j);
+        if (LOGN % 3 == 1 && 2 * kp <= N)
+            fwd_upper_zero<LOGN>(v, xc, C, j);
+        else
+            ntt_fwd<LOGN, 3, 1>(v, xc, C, j);
         const u64* ka = ksk + (size_t)pr * rl + (size_t)(0 * r + j) * N + tid;
         const u64* kb = ksk + (size_t)pr * rl + (size_t)(1 * r + j) * N + tid;
 #pragma unroll
